@@ -1,0 +1,58 @@
+"""Host-side statistics for Monte Carlo time series.
+
+Integrated autocorrelation time by the Gamma method with automatic windowing
+(U. Wolff, "Monte Carlo errors with less errors", Comput. Phys. Commun. 156
+(2004) 143; window rule of Madras & Sokal, J. Stat. Phys. 50 (1988) 109 refined
+by Wolff's S parameter).  Convention: tau_int = 1/2 + sum_{t>=1} rho(t), so an
+uncorrelated series has tau_int = 1/2 and the error of the mean is
+sqrt(2 tau_int Gamma(0) / N).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def autocorrelation(series: np.ndarray, tmax: int) -> np.ndarray:
+    """Gamma(t) for t = 0..tmax, normalised by N - t, via FFT."""
+    a = np.asarray(series, dtype=np.float64)
+    n = a.size
+    d = a - a.mean()
+    nfft = 1 << (2 * n - 1).bit_length()
+    f = np.fft.rfft(d, nfft)
+    acf = np.fft.irfft(f * np.conj(f), nfft)[: tmax + 1]
+    return acf / (n - np.arange(tmax + 1))
+
+
+def tau_int(series, s_factor: float = 1.5):
+    """Returns (tau_int, its statistical error, window W, error of the mean)."""
+    a = np.asarray(series, dtype=np.float64)
+    n = a.size
+    if n < 4:
+        raise ValueError("series too short")
+    tmax = min(n // 2, 100000)
+    gamma = autocorrelation(a, tmax)
+    if gamma[0] <= 0.0:
+        return 0.5, 0.0, 0, 0.0
+    rho = gamma / gamma[0]
+    cum = 0.5 + np.cumsum(rho[1:])  # tau_int(W) for W = 1..tmax
+    window = tmax
+    for w in range(1, tmax + 1):
+        t = cum[w - 1]
+        if t <= 0.5:
+            tau_w = 1e-12
+        else:
+            tau_w = s_factor / math.log((2.0 * t + 1.0) / (2.0 * t - 1.0))
+        g = math.exp(-w / tau_w) - tau_w / math.sqrt(w * n)
+        if g < 0.0:
+            window = w
+            break
+    # bias correction of Gamma(0) and of the summed autocorrelation (Wolff, Eq. 49)
+    cf = gamma[0] + 2.0 * gamma[1: window + 1].sum()
+    cf *= 1.0 + (2.0 * window + 1.0) / n
+    g0 = gamma[0] + cf / n  # corrected variance estimate
+    tau = max(0.5 * cf / g0, 0.5)
+    dtau = tau * math.sqrt(2.0 * (2.0 * window + 1.0) / n)
+    err_mean = math.sqrt(max(cf, 0.0) / n)
+    return tau, dtau, window, err_mean

@@ -1,0 +1,13 @@
+"""Test configuration: registers the ``gpu`` marker and puts the repository
+root on ``sys.path`` so that ``oracle`` and the package import from source."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a GB300 (sm_103a) GPU and the built CUDA library")
+    config.addinivalue_line("markers", "slow: long statistical test")
