@@ -1,0 +1,171 @@
+/*
+ * su2.h -- C ABI of the GB300 (sm_103a) lattice SU(2) heat-bath library.
+ *
+ * Pure-gauge SU(2) on an Ns^3 x Nt periodic lattice with the Wilson action,
+ * updated by the checkerboard heat bath of Cardoso & Bicudo, "Lattice SU(2) on
+ * GPU's" (LAT2010):
+ *   Sec. 2  links are SU(2) elements U = a0 + i a.sigma stored as quaternions
+ *           (a0, a1, a2, a3), |a| = 1; each link is redrawn from
+ *           dP(U) ~ exp(beta/2 Tr(U V)) where V is the staple (sum of the six
+ *           three-link products around U); with k = sqrt(det V) and
+ *           U~ = V/k, a0 is drawn from sqrt(1-a0^2) exp(beta k a0), the vector
+ *           part uniformly on the sphere of radius sqrt(1-a0^2), and the new
+ *           link is U' = a U~^{-1}.
+ *   Sec. 4  one iteration (sweep) updates, for mu = 0..3 in order, first the
+ *           even then the odd sites; kernels for cold start, hot start,
+ *           heat bath, plaquette, Polyakov loop and the global sum.
+ *
+ * Conventions common to every call:
+ *   - Every call returns an su2_status; nothing is thrown across the ABI.
+ *     On SU2_E_CUDA the text of the CUDA error is kept per thread and is
+ *     returned by su2_last_error().
+ *   - Host buffers are owned by the caller.  Device memory of a lattice is
+ *     owned by the library (allocated through the hook of su2_set_allocator,
+ *     else cudaMallocAsync on the lattice's stream) and freed by su2_destroy.
+ *   - All device work of a lattice is ordered on the CUDA stream given to
+ *     su2_create (NULL = the legacy default stream).  Calls that return host
+ *     values (observables, links, statistics) synchronise that stream.
+ *   - A handle is not thread-safe: one thread at a time per handle.
+ *   - Directions: mu = 0,1,2 are x,y,z (extent Ns), mu = 3 is time (extent Nt).
+ *     Sites are numbered lexicographically, lex = ((t*Ns + z)*Ns + y)*Ns + x;
+ *     the parity of a site is (x+y+z+t) mod 2.
+ *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key = seed and
+ *     counter (even/odd site index, sweep, stream kind/parity/mu, block), so a
+ *     run is a pure function of (start, seed, beta, sweep count).
+ */
+#ifndef SU2_H
+#define SU2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SU2_ABI_VERSION 1
+
+typedef struct su2_lattice su2_lattice;
+
+typedef enum {
+    SU2_COLD = 0, /* all links = identity (Sec. 4, cold start)            */
+    SU2_HOT = 1   /* all links Haar-random on S^3 (Sec. 4, hot start)     */
+} su2_start;
+
+typedef enum {
+    SU2_OK = 0,
+    SU2_E_INVAL = 1,          /* bad argument (odd or < 2 extent, beta < 0 or not finite, NULL) */
+    SU2_E_NOMEM = 2,          /* device or host allocation failed                                */
+    SU2_E_CUDA = 3,           /* a CUDA call failed; see su2_last_error()                        */
+    SU2_E_SAMPLER = 4,        /* a heat-bath draw hit its trial cap (link left unchanged)        */
+    SU2_E_DEVICE_TIMEOUT = 5, /* a bounded device wait gave up                                   */
+    SU2_E_NUMERIC = 6,        /* non-finite value met                                            */
+    SU2_E_STATE = 7           /* call not valid in the handle's current state                    */
+} su2_status;
+
+/* Per-call statistics, filled by the sweep calls when the pointer is non-NULL. */
+typedef struct {
+    uint64_t sweeps;            /* sweeps performed by the call                               */
+    uint64_t link_updates;      /* 4 V per sweep                                              */
+    uint64_t trials[8];         /* heat-bath a0 trials of phase 2*mu + parity, summed over sweeps */
+    uint64_t sampler_failures;  /* links whose draw hit the trial cap                         */
+    uint32_t kernel_launches;   /* heat-bath phase launches (8 per sweep)                     */
+    uint32_t timed;             /* 1 if kernel_ms is valid (see su2_set_timing)               */
+    double kernel_ms;           /* summed device time of the heat-bath phase kernels          */
+} su2_stats;
+
+/* Resumable state: with the links (su2_get_links) it determines every later sweep. */
+typedef struct {
+    int32_t ns, nt;
+    double beta;
+    uint64_t seed;
+    uint32_t sweep; /* sweeps done so far: the counter word of the next sweep */
+} su2_state;
+
+/* Device allocation hook (e.g. a framework's caching allocator).  alloc
+ * returns device memory usable on `stream`, or NULL; free releases it. */
+typedef void *(*su2_alloc_fn)(size_t bytes, int device, void *stream, void *ctx);
+typedef void (*su2_free_fn)(void *ptr, size_t bytes, int device, void *stream, void *ctx);
+
+/* Installs (or, with both NULL, removes) the process-wide allocation hook used
+ * by lattices created afterwards.  Not thread-safe with concurrent su2_create. */
+su2_status su2_set_allocator(su2_alloc_fn alloc, su2_free_fn free_fn, void *ctx);
+
+/* Creates an Ns^3 x Nt lattice on the current CUDA device and initialises it
+ * with a cold or hot start (Sec. 4).  ns, nt even and >= 2 (checkerboard with
+ * periodic boundaries); beta finite and >= 0; 4 Ns^3 Nt < 2^31 links.
+ * cuda_stream: a cudaStream_t or NULL.  *out receives the handle. */
+su2_status su2_create(int ns, int nt, double beta, uint64_t seed, su2_start start, void *cuda_stream,
+                      su2_lattice **out);
+
+/* Frees the lattice's device memory (stream-ordered) and the handle.  NULL is a no-op. */
+su2_status su2_destroy(su2_lattice *lat);
+
+/* nsweeps >= 0 heat-bath sweeps (Sec. 2 update, Sec. 4 schedule: mu = 0..3,
+ * even then odd).  Asynchronous unless stats != NULL, in which case the call
+ * synchronises and fills *stats.  SU2_E_SAMPLER if any draw hit its cap. */
+su2_status su2_heatbath_sweep(su2_lattice *lat, int nsweeps, su2_stats *stats);
+
+/* One phase only: links U_mu(x) with parity(x) = parity, using the current
+ * sweep counter (which is not advanced).  For tests and diagnostics. */
+su2_status su2_heatbath_phase(su2_lattice *lat, int mu, int parity);
+
+/* Generation loop: nsweeps sweeps; after every `measure_every`-th sweep
+ * (0 = never) the plaquette and Polyakov loop are computed on the device and
+ * kept; after every `reunit_every`-th sweep (0 = never) the links are
+ * reunitarized.  plaq and poly (host, nullable) receive nsweeps/measure_every
+ * values each.  Synchronises once at the end. */
+su2_status su2_generate(su2_lattice *lat, int nsweeps, int measure_every, int reunit_every, double *plaq,
+                        double *poly, su2_stats *stats);
+
+/* a <- a / |a| for every link (the links drift from |a| = 1 by rounding). */
+su2_status su2_reunitarize(su2_lattice *lat);
+
+/* Mean plaquette (Sec. 4): (1/6V) sum_x sum_{mu<nu} (1/2) Tr U_mu(x) U_nu(x+mu)
+ * U_mu(x+nu)^dag U_nu(x)^dag; per-site values in binary32, global sum in
+ * binary64.  Synchronous. */
+su2_status su2_plaquette(su2_lattice *lat, double *out);
+
+/* Polyakov loop (Sec. 4): (1/Ns^3) sum over spatial sites of
+ * (1/2) Tr prod_{t=0}^{Nt-1} U_3(x, t), signed; binary32 products, binary64
+ * sum.  Synchronous. */
+su2_status su2_polyakov(su2_lattice *lat, double *out);
+
+/* Copies all links to / from a host buffer of 16 V floats laid out
+ * [lex site][mu][a0..a3].  Synchronous.  set_links does not reunitarize. */
+su2_status su2_get_links(su2_lattice *lat, float *host);
+su2_status su2_set_links(su2_lattice *lat, const float *host);
+
+/* Resumable state (sweep counter, seed, beta).  set_state requires matching extents. */
+su2_status su2_get_state(const su2_lattice *lat, su2_state *out);
+su2_status su2_set_state(su2_lattice *lat, const su2_state *in);
+su2_status su2_set_beta(su2_lattice *lat, double beta);
+
+/* Device view of the links: even/odd structure of arrays of float4,
+ * element (mu, parity, i) at index (2 mu + parity) (V/2) + i, where i = lex/2
+ * of a site of that parity.  The pointer stays owned by the lattice. */
+su2_status su2_device_links(su2_lattice *lat, void **ptr, size_t *bytes);
+
+/* When enabled, the sweep calls record CUDA events around each heat-bath
+ * phase kernel on the lattice's stream and report the summed device time in
+ * su2_stats.kernel_ms. */
+su2_status su2_set_timing(su2_lattice *lat, int enable);
+
+/* Self-tests of device building blocks (they launch kernels):
+ * su2_selftest_philox: n rows of host input ck[6 n] = (key0, key1, c0, c1, c2,
+ *   c3) -> out[4 n] Philox4x32-10 words.
+ * su2_selftest_math: which = 0 log, 1 exp, 2 sin/cos of 2 pi x; n inputs
+ *   x[n] -> y[n] (and y2[n] = cos for which = 2; else y2 may be NULL). */
+su2_status su2_selftest_philox(const uint32_t *ck, uint32_t *out, size_t n);
+su2_status su2_selftest_math(int which, const float *x, float *y, float *y2, size_t n);
+
+/* Human-readable status and the last CUDA error text of this thread. */
+const char *su2_status_str(su2_status s);
+const char *su2_last_error(void);
+int su2_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SU2_H */

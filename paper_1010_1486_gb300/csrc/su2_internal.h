@@ -1,0 +1,117 @@
+// su2_internal.h -- host-side state of a lattice handle and the launchers
+// shared between the translation units of libsu2.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/su2.h"
+#include "su2_device.cuh"
+
+namespace su2 {
+
+constexpr int kTrialSlots = 64;      // trial counters are spread over 64 slots per phase
+constexpr int kReduceThreads = 256;  // block size of the observable kernels
+constexpr int kHbThreads = 256;      // block size of the heat-bath phase kernel
+
+// Device scratch of a lattice, carved from one allocation.
+struct DeviceScratch {
+    double *partials = nullptr;             // per-block partial sums of a reduction
+    unsigned int *ticket = nullptr;         // last-block counter of a reduction
+    double *result = nullptr;               // [0] plaquette, [1] Polyakov (latest)
+    unsigned long long *trials = nullptr;   // [8][kTrialSlots]
+    unsigned int *flags = nullptr;          // [0] sampler cap hits, [1] other errors
+    double *history = nullptr;              // measurements of su2_generate: [2][history_cap]
+    int partials_cap = 0;
+    int history_cap = 0;
+};
+
+}  // namespace su2
+
+struct su2_lattice {
+    int ns = 0, nt = 0;
+    int64_t vol = 0;  // Ns^3 Nt
+    int vh = 0;       // vol / 2
+    double beta = 0.0;
+    uint64_t seed = 0;
+    uint32_t sweep = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+
+    void *block = nullptr;  // the single device allocation
+    size_t block_bytes = 0;
+    float4 *links = nullptr;  // 8 vh float4 (even/odd structure of arrays)
+    su2::DeviceScratch scratch;
+
+    void *staging = nullptr;  // lex-ordered copy for get/set_links (allocated on demand)
+    size_t staging_bytes = 0;
+
+    bool timing = false;
+    std::vector<cudaEvent_t> events;  // pairs around timed phase launches
+    size_t events_used = 0;
+};
+
+namespace su2 {
+
+// Error bookkeeping (per thread).
+void set_last_error(const std::string &msg);
+su2_status cuda_fail(cudaError_t e, const char *what);
+
+#define SU2_CUDA(call)                                                         \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess) return ::su2::cuda_fail(e_, #call);             \
+    } while (0)
+
+// Keeps the lattice's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) changed = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+inline Geom geom_of(const su2_lattice *lat)
+{
+    Geom g;
+    g.ns = lat->ns;
+    g.nt = lat->nt;
+    g.vh = lat->vh;
+    g.vs = lat->ns * lat->ns * lat->ns;
+    return g;
+}
+
+inline int grid_for(int64_t n, int threads, int64_t cap = 152 * 64)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+// Allocation through the installed hook (or cudaMallocAsync).
+void *device_alloc(size_t bytes, int device, cudaStream_t stream);
+void device_free(void *ptr, size_t bytes, int device, cudaStream_t stream);
+
+// Launchers (each enqueues on lat->stream and returns a status of the launch).
+su2_status launch_cold_start(su2_lattice *lat);
+su2_status launch_hot_start(su2_lattice *lat);
+su2_status launch_hb_phase(su2_lattice *lat, int mu, int parity, uint32_t sweep);
+su2_status launch_reunitarize(su2_lattice *lat);
+// Observables: write the value into *dst (device memory) without synchronising.
+su2_status launch_plaquette(su2_lattice *lat, double *dst);
+su2_status launch_polyakov(su2_lattice *lat, double *dst);
+su2_status launch_clear_counters(su2_lattice *lat);
+// Reads and clears the trial counters and flags (synchronises).
+su2_status collect_stats(su2_lattice *lat, su2_stats *stats, uint64_t sweeps);
+
+}  // namespace su2

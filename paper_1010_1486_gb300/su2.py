@@ -1,0 +1,274 @@
+"""Thin Python binding of the ``libsu2`` C ABI (``include/su2.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``libsu2.so``.  Functions carry the C names; a non-OK status raises
+:class:`SU2Error`.  If the library has not been built, importing this module
+raises ``ImportError`` -- there is no fallback of any kind.
+
+PyTorch supplies device memory and streams: :func:`use_torch_allocator`
+routes the library's device allocations through PyTorch's caching allocator,
+and ``stream`` arguments accept a ``torch.cuda.Stream`` or a raw handle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsu2.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "su2.h")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built; run __graft_entry__.build() (nvcc, sm_103a)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+SU2_COLD, SU2_HOT = 0, 1
+STATUS = {0: "SU2_OK", 1: "SU2_E_INVAL", 2: "SU2_E_NOMEM", 3: "SU2_E_CUDA", 4: "SU2_E_SAMPLER",
+          5: "SU2_E_DEVICE_TIMEOUT", 6: "SU2_E_NUMERIC", 7: "SU2_E_STATE"}
+
+
+class SU2Error(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        detail = _lib.su2_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({_lib.su2_status_str(status).decode()}) {detail}")
+
+
+class su2_stats(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_uint64), ("link_updates", ctypes.c_uint64),
+                ("trials", ctypes.c_uint64 * 8), ("sampler_failures", ctypes.c_uint64),
+                ("kernel_launches", ctypes.c_uint32), ("timed", ctypes.c_uint32),
+                ("kernel_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"sweeps": self.sweeps, "link_updates": self.link_updates, "trials": list(self.trials),
+                "sampler_failures": self.sampler_failures, "kernel_launches": self.kernel_launches,
+                "timed": bool(self.timed), "kernel_ms": self.kernel_ms}
+
+
+class su2_state(ctypes.Structure):
+    _fields_ = [("ns", ctypes.c_int32), ("nt", ctypes.c_int32), ("beta", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("sweep", ctypes.c_uint32)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
+
+_P = ctypes.c_void_p
+_i32, _u32, _u64, _f64 = ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double
+_SIGS = {
+    "su2_set_allocator": [ALLOC_FN, FREE_FN, _P],
+    "su2_create": [_i32, _i32, _f64, _u64, _i32, _P, ctypes.POINTER(_P)],
+    "su2_destroy": [_P],
+    "su2_heatbath_sweep": [_P, _i32, ctypes.POINTER(su2_stats)],
+    "su2_heatbath_phase": [_P, _i32, _i32],
+    "su2_generate": [_P, _i32, _i32, _i32, _P, _P, ctypes.POINTER(su2_stats)],
+    "su2_reunitarize": [_P],
+    "su2_plaquette": [_P, ctypes.POINTER(_f64)],
+    "su2_polyakov": [_P, ctypes.POINTER(_f64)],
+    "su2_get_links": [_P, _P],
+    "su2_set_links": [_P, _P],
+    "su2_get_state": [_P, ctypes.POINTER(su2_state)],
+    "su2_set_state": [_P, ctypes.POINTER(su2_state)],
+    "su2_set_beta": [_P, _f64],
+    "su2_device_links": [_P, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_size_t)],
+    "su2_set_timing": [_P, _i32],
+    "su2_selftest_philox": [_P, _P, ctypes.c_size_t],
+    "su2_selftest_math": [_i32, _P, _P, _P, ctypes.c_size_t],
+}
+for _name, _args in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = ctypes.c_int
+_lib.su2_status_str.argtypes = [ctypes.c_int]
+_lib.su2_status_str.restype = ctypes.c_char_p
+_lib.su2_last_error.argtypes = []
+_lib.su2_last_error.restype = ctypes.c_char_p
+_lib.su2_abi_version.argtypes = []
+_lib.su2_abi_version.restype = ctypes.c_int
+
+
+def declared_symbols() -> list[str]:
+    """Function names declared in include/su2.h."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w\s\*]*?\b(su2_\w+)\s*\(", text, flags=re.M)))
+
+
+def library():
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise SU2Error(status, where)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(getattr(stream, "cuda_stream"))
+
+
+def _host_ptr(a: np.ndarray) -> int:
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("host buffer must be C-contiguous")
+    return a.ctypes.data
+
+
+# --------------------------------------------------------------- allocator
+_torch_hooks = None
+
+
+def use_torch_allocator() -> None:
+    """Route device allocations through PyTorch's caching allocator."""
+    global _torch_hooks
+    import torch
+
+    def _alloc(nbytes, device, stream, ctx):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), device=int(device), stream=int(stream or 0)))
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, device, stream, ctx):
+        try:
+            torch.cuda.caching_allocator_delete(int(ptr))
+        except Exception:
+            pass
+
+    hooks = (ALLOC_FN(_alloc), FREE_FN(_free))
+    _check(_lib.su2_set_allocator(hooks[0], hooks[1], None), "su2_set_allocator")
+    _torch_hooks = hooks
+
+
+def use_default_allocator() -> None:
+    global _torch_hooks
+    _check(_lib.su2_set_allocator(ALLOC_FN(), FREE_FN(), None), "su2_set_allocator")
+    _torch_hooks = None
+
+
+# ------------------------------------------------------------------ C names
+def su2_create(ns: int, nt: int, beta: float, seed: int, start: int = SU2_HOT, stream=None) -> int:
+    h = _P()
+    _check(_lib.su2_create(ns, nt, float(beta), int(seed), int(start), _stream_handle(stream), ctypes.byref(h)),
+           "su2_create")
+    return h.value
+
+
+def su2_destroy(lat: int) -> None:
+    _check(_lib.su2_destroy(lat), "su2_destroy")
+
+
+def su2_heatbath_sweep(lat: int, nsweeps: int = 1, stats: bool = False):
+    st = su2_stats() if stats else None
+    _check(_lib.su2_heatbath_sweep(lat, nsweeps, ctypes.byref(st) if st is not None else None),
+           "su2_heatbath_sweep")
+    return st.as_dict() if st is not None else None
+
+
+def su2_heatbath_phase(lat: int, mu: int, parity: int) -> None:
+    _check(_lib.su2_heatbath_phase(lat, mu, parity), "su2_heatbath_phase")
+
+
+def su2_generate(lat: int, nsweeps: int, measure_every: int = 1, reunit_every: int = 0,
+                 plaq: np.ndarray | None = None, poly: np.ndarray | None = None):
+    """Returns (plaquettes, polyakov loops, stats dict).  plaq / poly may be
+    caller-provided float64 arrays (e.g. pinned host memory)."""
+    nmeas = nsweeps // measure_every if measure_every > 0 else 0
+    if plaq is None:
+        plaq = np.zeros(nmeas, dtype=np.float64)
+    if poly is None:
+        poly = np.zeros(nmeas, dtype=np.float64)
+    st = su2_stats()
+    _check(_lib.su2_generate(lat, nsweeps, measure_every, reunit_every, _host_ptr(plaq) if nmeas else None,
+                             _host_ptr(poly) if nmeas else None, ctypes.byref(st)), "su2_generate")
+    return plaq[:nmeas], poly[:nmeas], st.as_dict()
+
+
+def su2_reunitarize(lat: int) -> None:
+    _check(_lib.su2_reunitarize(lat), "su2_reunitarize")
+
+
+def su2_plaquette(lat: int) -> float:
+    out = _f64()
+    _check(_lib.su2_plaquette(lat, ctypes.byref(out)), "su2_plaquette")
+    return out.value
+
+
+def su2_polyakov(lat: int) -> float:
+    out = _f64()
+    _check(_lib.su2_polyakov(lat, ctypes.byref(out)), "su2_polyakov")
+    return out.value
+
+
+def su2_get_links(lat: int, ns: int, nt: int, out: np.ndarray | None = None) -> np.ndarray:
+    """Links as float32 [site, mu, 4] in lexicographic site order."""
+    if out is None:
+        out = np.empty((ns ** 3 * nt, 4, 4), dtype=np.float32)
+    _check(_lib.su2_get_links(lat, _host_ptr(out)), "su2_get_links")
+    return out
+
+
+def su2_set_links(lat: int, links: np.ndarray) -> None:
+    links = np.ascontiguousarray(links, dtype=np.float32)
+    _check(_lib.su2_set_links(lat, _host_ptr(links)), "su2_set_links")
+
+
+def su2_get_state(lat: int) -> dict:
+    s = su2_state()
+    _check(_lib.su2_get_state(lat, ctypes.byref(s)), "su2_get_state")
+    return {"ns": s.ns, "nt": s.nt, "beta": s.beta, "seed": s.seed, "sweep": s.sweep}
+
+
+def su2_set_state(lat: int, state: dict) -> None:
+    s = su2_state(state["ns"], state["nt"], state["beta"], state["seed"], state["sweep"])
+    _check(_lib.su2_set_state(lat, ctypes.byref(s)), "su2_set_state")
+
+
+def su2_set_beta(lat: int, beta: float) -> None:
+    _check(_lib.su2_set_beta(lat, float(beta)), "su2_set_beta")
+
+
+def su2_device_links(lat: int):
+    p = _P()
+    n = ctypes.c_size_t()
+    _check(_lib.su2_device_links(lat, ctypes.byref(p), ctypes.byref(n)), "su2_device_links")
+    return p.value, n.value
+
+
+def su2_set_timing(lat: int, enable: bool) -> None:
+    _check(_lib.su2_set_timing(lat, int(bool(enable))), "su2_set_timing")
+
+
+def su2_selftest_philox(ck: np.ndarray) -> np.ndarray:
+    ck = np.ascontiguousarray(ck, dtype=np.uint32).reshape(-1, 6)
+    out = np.zeros((ck.shape[0], 4), dtype=np.uint32)
+    _check(_lib.su2_selftest_philox(_host_ptr(ck), _host_ptr(out), ck.shape[0]), "su2_selftest_philox")
+    return out
+
+
+def su2_selftest_math(which: int, x: np.ndarray):
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.empty_like(x)
+    y2 = np.empty_like(x) if which == 2 else None
+    _check(_lib.su2_selftest_math(which, _host_ptr(x), _host_ptr(y), _host_ptr(y2) if y2 is not None else None,
+                                  x.size), "su2_selftest_math")
+    return (y, y2) if which == 2 else y
+
+
+def su2_status_str(status: int) -> str:
+    return _lib.su2_status_str(status).decode()
+
+
+def su2_last_error() -> str:
+    return _lib.su2_last_error().decode(errors="replace")
+
+
+def su2_abi_version() -> int:
+    return _lib.su2_abi_version()
