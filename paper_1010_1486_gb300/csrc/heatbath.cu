@@ -5,102 +5,301 @@
 // Its staple reads only links of the other three directions (both parities)
 // and U_mu of the opposite parity, none of which the phase writes, so every
 // thread works independently and the loads may use the read-only path.
+#include <algorithm>
 #include <cstdio>
+#include <cstdlib>
+#include <cstring>
 
 #include "su2_device.cuh"
 #include "su2_internal.h"
 
 namespace su2 {
 
-// Sums `value` over the block and adds it to one of kTrialSlots counters.
-__device__ __forceinline__ void block_add_trials(unsigned int value, unsigned long long *slot)
-{
-    __shared__ unsigned int warp_sums[32];
-    const unsigned int lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    const unsigned int w = __reduce_add_sync(0xffffffffu, value);
-    if (lane == 0) warp_sums[warp] = w;
-    __syncthreads();
-    if (warp == 0) {
-        const unsigned int nwarps = blockDim.x >> 5;
-        unsigned int v = lane < nwarps ? warp_sums[lane] : 0u;
-        v = __reduce_add_sync(0xffffffffu, v);
-        if (lane == 0 && v) atomicAdd(slot, (unsigned long long)v);
-    }
-}
-
 // Staple of U_mu(x) (Sec. 2):
 //   V = sum_{nu != mu} U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
 //                    + U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu)
 // nu ascending, forward term first, accumulated from zero.
-template <int MU>
-__device__ __forceinline__ float4 staple(const float4 *__restrict__ L, const Geom &g, const Coord &x, int eo,
-                                         int parity)
+struct HbParams {
+    float4 *links;
+    Geom g;
+    RoundKeys rk;
+    int parity;
+    float beta;
+    uint32_t sweep;
+    unsigned long long *trial_slots;
+    unsigned int *flags;
+};
+
+constexpr int kHbWarps = kHbThreads / 32;
+
+// Forward and backward staple terms of direction nu (Sec. 2), from the six
+// links they need: U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag and
+// U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu).
+struct NuLinks {
+    float4 nu_xp, mu_xn, nu_x, nu_xpm, mu_xm, nu_xm;
+};
+
+template <int MU, int NU>
+__device__ __forceinline__ NuLinks load_nu(const float4 *__restrict__ L, const Geom &g, const Coord &x, int lex_p,
+                                           int parity)
 {
+    constexpr int nu = NU;
     const int op = parity ^ 1;
-    const Coord xp = step(g, x, MU, +1);
-    const int e_xp = coord_to_eo(g, xp);
-    float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-#pragma unroll
-    for (int nu = 0; nu < 4; ++nu) {
-        if (nu == MU) continue;
-        const int e_xn = coord_to_eo(g, step(g, x, nu, +1));
-        const Coord xm = step(g, x, nu, -1);
-        const int e_xm = coord_to_eo(g, xm);
-        const int e_xpm = coord_to_eo(g, step(g, xp, nu, -1));
-        const float4 u_nu_xp = __ldg(L + link_index(g, nu, op, e_xp));
-        const float4 u_mu_xn = __ldg(L + link_index(g, MU, op, e_xn));
-        const float4 u_nu_x = __ldg(L + link_index(g, nu, parity, eo));
-        const float4 u_nu_xpm = __ldg(L + link_index(g, nu, parity, e_xpm));
-        const float4 u_mu_xm = __ldg(L + link_index(g, MU, op, e_xm));
-        const float4 u_nu_xm = __ldg(L + link_index(g, nu, op, e_xm));
-        const float4 fwd = qmul(qmul(u_nu_xp, qdag(u_mu_xn)), qdag(u_nu_x));
-        const float4 bwd = qmul(qmul(qdag(u_nu_xpm), qdag(u_mu_xm)), u_nu_xm);
-        v = qadd(v, fwd);
-        v = qadd(v, bwd);
-    }
-    return v;
+    NuLinks n;
+    const int e_xn = lex_fwd(g, x.lex, x.c[nu], nu) >> 1;
+    const int e_xm = lex_bwd(g, x.lex, x.c[nu], nu) >> 1;
+    const int e_xpm = lex_bwd(g, lex_p, x.c[nu], nu) >> 1;  // x + mu - nu keeps the nu coordinate of x
+    n.nu_xp = __ldg(L + link_index(g, nu, op, lex_p >> 1));
+    n.mu_xn = __ldg(L + link_index(g, MU, op, e_xn));
+    n.nu_x = __ldg(L + link_index(g, nu, parity, x.lex >> 1));
+    n.nu_xpm = __ldg(L + link_index(g, nu, parity, e_xpm));
+    n.mu_xm = __ldg(L + link_index(g, MU, op, e_xm));
+    n.nu_xm = __ldg(L + link_index(g, nu, op, e_xm));
+    return n;
 }
 
-template <int MU>
-__global__ void __launch_bounds__(kHbThreads) hb_phase_kernel(float4 *__restrict__ links, Geom g, int parity,
-                                                               float beta, uint32_t k0, uint32_t k1,
-                                                               uint32_t sweep,
-                                                               unsigned long long *__restrict__ trial_slots,
-                                                               unsigned int *__restrict__ flags)
+__device__ __forceinline__ float4 add_nu_terms(float4 v, const NuLinks &n)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned int trials = 0;
-    if (i < g.vh) {
-        const Coord x = eo_to_coord(g, i, parity);
-        const float4 v = staple<MU>(links, g, x, i, parity);
-        float4 out;
-        const int n = heatbath_draw(v, beta, k0, k1, (uint32_t)i, sweep, (uint32_t)parity, (uint32_t)MU, out);
-        if (n > 0) {
-            links[link_index(g, MU, parity, i)] = out;
-            trials = (unsigned int)n;
-        } else {
-            atomicAdd(&flags[0], 1u);  // trial cap: the link keeps its old value
-            trials = (unsigned int)kMaxTrials;
+    const float4 fwd = qmul(qmul(n.nu_xp, qdag(n.mu_xn)), qdag(n.nu_x));
+    const float4 bwd = qmul(qmul(qdag(n.nu_xpm), qdag(n.mu_xm)), n.nu_xm);
+    return qadd(qadd(v, fwd), bwd);
+}
+
+// One heat-bath phase (mu = MU, sites of parity p.parity).
+//
+// The V/2 sites are cut into rounds of 32 consecutive even/odd indices; warp
+// w takes rounds w, w + W, w + 2W, ... (W warps in the grid), so all warps
+// sweep the lattice together and neighbour links are re-read from L2.  Each
+// warp runs one loop whose iterations interleave three kinds of work:
+//   A  one third of the staple of its next round (the six links of one nu):
+//      the loads are issued first and used at the end of the iteration, so
+//      their latency hides behind B;  after the third part, U~^dag, beta k
+//      and exp(-2 beta k) of the 32 sites go into the warp's ring of R rounds;
+//   B  one Philox block (two Creutz trials) for the pending link each lane
+//      holds; a lane whose link is accepted takes the next pending link of the
+//      ring, so no lane idles while the slowest draw of its round finishes;
+//   C  once every link of the oldest round is accepted, the 32 lanes draw the
+//      directions and store U' = a U~^dag together (coalesced).
+// A link's random numbers depend only on its counter, never on the lane or
+// the iteration that handles it, so the phase computes exactly the
+// one-thread-per-link definition.  Every iteration advances A, B or C, and B
+// ends every link within kMaxTrials trials, so the loop terminates.
+template <int MU, int R>
+__global__ void __launch_bounds__(kHbThreads) hb_phase_kernel(const HbParams p)
+{
+    constexpr int Q = 32 * R;
+    __shared__ float4 s_ut[kHbWarps][Q];
+    __shared__ float s_bk[kHbWarps][Q];  // beta k; after acceptance a0 (NaN: trial cap hit)
+    __shared__ float s_e[kHbWarps][Q];
+    __shared__ int s_done[kHbWarps][R];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    float4 *const ut_q = s_ut[wib];
+    float *const bk_q = s_bk[wib];
+    float *const e_q = s_e[wib];
+    int *const done_q = s_done[wib];
+    const unsigned int lanes_below = (1u << lane) - 1u;
+    const int warp_global = blockIdx.x * kHbWarps + wib;
+    const int nwarps = gridDim.x * kHbWarps;
+    const int vh = p.g.vh;
+    const int rounds_total = (vh + 31) >> 5;
+    const int my_rounds = warp_global < rounds_total ? (rounds_total - warp_global + nwarps - 1) / nwarps : 0;
+    const uint32_t sw_creutz = stream_word(kCreutz, (uint32_t)p.parity, MU);
+    const uint32_t sw_dir = stream_word(kDirection, (uint32_t)p.parity, MU);
+
+    if (lane < R) done_q[lane] = 0;
+    unsigned int my_trials = 0;
+
+    int a = 0, sub = 0;  // A: rounds produced, part (0..2) of the next one
+    int f = 0;           // C: rounds finalised
+    int produced = 0;    // valid links produced so far (their sequence numbers are 0 .. produced-1)
+    int claim = 0;       // next sequence number to hand out
+    int item = -1;       // B: sequence number of this lane's pending link
+    int item_eo = 0;
+    uint32_t blk = 0;
+    float bk = 0.0f, e = 0.0f, ome = 1.0f;
+    bool haar = false;
+    Coord xa;            // A: site of this lane in round a
+    int lex_pa = 0;
+    float4 va = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+
+    while (true) {
+        __syncwarp();
+        // ---- C: finalise every complete round, oldest first
+        while (f < a) {
+            const int k = warp_global + f * nwarps;
+            const int rsize = min(32, vh - 32 * k);
+            if (done_q[f % R] < rsize) break;
+            if (lane < rsize) {
+                const int slot = (f % R) * 32 + lane;
+                const int eo = 32 * k + lane;
+                const float a0 = bk_q[slot];
+                if (a0 == a0) {
+                    const uint4 d = philox_rk(make_uint4((uint32_t)eo, p.sweep, sw_dir, 0u), p.rk);
+                    p.links[link_index(p.g, MU, p.parity, eo)] = direction_update(a0, ut_q[slot], d);
+                } else {
+                    atomicAdd(&p.flags[0], 1u);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) done_q[f % R] = 0;
+            __syncwarp();
+            ++f;
+        }
+        if (f == my_rounds) break;
+
+        // ---- hand pending links to idle lanes
+        {
+            const unsigned int need = __ballot_sync(0xffffffffu, item < 0);
+            const int avail = produced - claim;
+            if (item < 0) {
+                const int rank = __popc(need & lanes_below);
+                if (rank < avail) {
+                    item = claim + rank;
+                    const int slot = item % Q;
+                    const int k = warp_global + (item >> 5) * nwarps;
+                    item_eo = 32 * k + (item & 31);
+                    blk = 0;
+                    bk = bk_q[slot];
+                    e = e_q[slot];
+                    ome = __fsub_rn(1.0f, e);
+                    haar = bk < kHaarBelow;
+                }
+            }
+            claim += min(__popc(need), avail);
+        }
+
+        const bool do_a = a < my_rounds && a < f + R;
+        const int a_k = warp_global + a * nwarps;
+        const bool a_valid = do_a && 32 * a_k + lane < vh;
+        NuLinks nl;
+        // ---- A (issue): the six links of one nu for this lane's site of round a
+        if (a_valid) {
+            if (sub == 0) {
+                xa = eo_to_coord(p.g, 32 * a_k + lane, p.parity);
+                lex_pa = lex_fwd(p.g, xa.lex, xa.c[MU], MU);
+                va = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+            // the three directions nu != MU, ascending
+            if (sub == 0)
+                nl = load_nu<MU, (MU == 0 ? 1 : 0)>(p.links, p.g, xa, lex_pa, p.parity);
+            else if (sub == 1)
+                nl = load_nu<MU, (MU <= 1 ? 2 : 1)>(p.links, p.g, xa, lex_pa, p.parity);
+            else
+                nl = load_nu<MU, (MU <= 2 ? 3 : 2)>(p.links, p.g, xa, lex_pa, p.parity);
+        }
+
+        // ---- B: one Philox block (two trials) for the pending link
+        if (item >= 0) {
+            const uint4 w = philox_rk(make_uint4((uint32_t)item_eo, p.sweep, sw_creutz, blk), p.rk);
+            float cand;
+            uint32_t t = 0;
+            if (creutz_trial(uniform01(w.x), uniform01(w.y), bk, e, ome, haar, cand))
+                t = 2 * blk + 1;
+            else if (creutz_trial(uniform01(w.z), uniform01(w.w), bk, e, ome, haar, cand))
+                t = 2 * blk + 2;
+            bool finished = false;
+            if (t) {
+                my_trials += t;
+                finished = true;
+            } else if (++blk == (uint32_t)(kMaxTrials / 2)) {
+                cand = __int_as_float(0x7fc00000);  // NaN: trial cap hit, the link keeps its value
+                my_trials += kMaxTrials;
+                finished = true;
+            }
+            if (finished) {
+                bk_q[item % Q] = cand;
+                atomicAdd(&done_q[(item >> 5) % R], 1);
+                item = -1;
+            }
+        }
+
+        // ---- A (use): add the two staple terms of nu; after the third part park the site
+        if (do_a) {
+            if (a_valid) {
+                va = add_nu_terms(va, nl);
+                if (sub == 2) {
+                    const DrawSetup d = prepare_draw(va, p.beta);
+                    const int slot = (a % R) * 32 + lane;
+                    ut_q[slot] = d.ut;
+                    bk_q[slot] = d.bk;
+                    e_q[slot] = d.e;
+                }
+            }
+            if (++sub == 3) {
+                sub = 0;
+                produced += min(32, vh - 32 * a_k);
+                ++a;
+            }
         }
     }
-    block_add_trials(trials, &trial_slots[(2 * MU + parity) * kTrialSlots + (blockIdx.x & (kTrialSlots - 1))]);
+    const unsigned int wsum = __reduce_add_sync(0xffffffffu, my_trials);
+    if (lane == 0 && wsum)
+        atomicAdd(&p.trial_slots[(2 * MU + p.parity) * kTrialSlots + (warp_global & (kTrialSlots - 1))],
+                  (unsigned long long)wsum);
+}
+
+// Depth R of each warp's ring (rounds of 32 links in flight).  SU2_HB_QUEUE
+// = 2 | 4 | 8 overrides the default of 8 (tuning).
+static int queue_depth()
+{
+    static const int depth = [] {
+        const char *env = getenv("SU2_HB_QUEUE");
+        const int d = env ? atoi(env) : 8;
+        return (d == 2 || d == 4) ? d : 8;
+    }();
+    return depth;
+}
+
+template <int MU, int R>
+static cudaError_t launch_hb(const HbParams &p, int device, cudaStream_t stream)
+{
+    static int blocks_per_sm[64] = {};
+    static int num_sms[64] = {};
+    if (device < 0 || device >= 64) device = 0;
+    if (!blocks_per_sm[device]) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[device],
+                                                                      hb_phase_kernel<MU, R>, kHbThreads, 0);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&num_sms[device], cudaDevAttrMultiProcessorCount, device);
+        if (e != cudaSuccess) return e;
+        if (blocks_per_sm[device] < 1) blocks_per_sm[device] = 1;
+    }
+    const int rounds = (p.g.vh + 31) / 32;
+    const int want = (rounds + kHbWarps - 1) / kHbWarps;
+    const int grid = std::max(1, std::min(want, blocks_per_sm[device] * num_sms[device]));
+    hb_phase_kernel<MU, R><<<grid, kHbThreads, 0, stream>>>(p);
+    return cudaGetLastError();
 }
 
 su2_status launch_hb_phase(su2_lattice *lat, int mu, int parity, uint32_t sweep)
 {
-    const Geom g = geom_of(lat);
-    const int grid = (g.vh + kHbThreads - 1) / kHbThreads;
-    const float beta = (float)lat->beta;
-    const uint32_t k0 = (uint32_t)lat->seed, k1 = (uint32_t)(lat->seed >> 32);
-    unsigned long long *slots = lat->scratch.trials;
-    unsigned int *flags = lat->scratch.flags;
-    switch (mu) {
-    case 0: hb_phase_kernel<0><<<grid, kHbThreads, 0, lat->stream>>>(lat->links, g, parity, beta, k0, k1, sweep, slots, flags); break;
-    case 1: hb_phase_kernel<1><<<grid, kHbThreads, 0, lat->stream>>>(lat->links, g, parity, beta, k0, k1, sweep, slots, flags); break;
-    case 2: hb_phase_kernel<2><<<grid, kHbThreads, 0, lat->stream>>>(lat->links, g, parity, beta, k0, k1, sweep, slots, flags); break;
-    default: hb_phase_kernel<3><<<grid, kHbThreads, 0, lat->stream>>>(lat->links, g, parity, beta, k0, k1, sweep, slots, flags); break;
+    HbParams p;
+    p.links = lat->links;
+    p.g = geom_of(lat);
+    p.rk = make_round_keys(lat->seed);
+    p.parity = parity;
+    p.beta = (float)lat->beta;
+    p.sweep = sweep;
+    p.trial_slots = lat->scratch.trials;
+    p.flags = lat->scratch.flags;
+    const int R = queue_depth();
+    cudaError_t e;
+    switch (R * 4 + mu) {
+    case 8: e = launch_hb<0, 2>(p, lat->device, lat->stream); break;
+    case 9: e = launch_hb<1, 2>(p, lat->device, lat->stream); break;
+    case 10: e = launch_hb<2, 2>(p, lat->device, lat->stream); break;
+    case 11: e = launch_hb<3, 2>(p, lat->device, lat->stream); break;
+    case 16: e = launch_hb<0, 4>(p, lat->device, lat->stream); break;
+    case 17: e = launch_hb<1, 4>(p, lat->device, lat->stream); break;
+    case 18: e = launch_hb<2, 4>(p, lat->device, lat->stream); break;
+    case 19: e = launch_hb<3, 4>(p, lat->device, lat->stream); break;
+    case 32: e = launch_hb<0, 8>(p, lat->device, lat->stream); break;
+    case 33: e = launch_hb<1, 8>(p, lat->device, lat->stream); break;
+    case 34: e = launch_hb<2, 8>(p, lat->device, lat->stream); break;
+    default: e = launch_hb<3, 8>(p, lat->device, lat->stream); break;
     }
-    SU2_CUDA(cudaGetLastError());
+    SU2_CUDA(e);
     return SU2_OK;
 }
 

@@ -75,7 +75,7 @@ __global__ void cold_start_kernel(float4 *__restrict__ links, int64_t n)
 // (x1,x2) with s1 and (x3,x4) with s2, give (x1, x2, x3 f, x4 f),
 // f = sqrt((1-s1)/s2), uniform on S^3.  Candidate pair m uses words 2(m&1),
 // 2(m&1)+1 of hot-start block m>>1 of the link's counter.
-__global__ void hot_start_kernel(float4 *__restrict__ links, Geom g, uint32_t k0, uint32_t k1,
+__global__ void hot_start_kernel(float4 *__restrict__ links, Geom g, const RoundKeys rk,
                                  unsigned int *__restrict__ flags)
 {
     const int64_t n = 8 * (int64_t)g.vh;
@@ -88,7 +88,10 @@ __global__ void hot_start_kernel(float4 *__restrict__ links, Geom g, uint32_t k0
         int found = 0;
         uint4 w = make_uint4(0u, 0u, 0u, 0u);
         for (int m = 0; m < 64 && found < 2; ++m) {
-            if ((m & 1) == 0) w = draw(k0, k1, (uint32_t)eo, 0u, kHotStart, (uint32_t)parity, (uint32_t)mu, (uint32_t)(m >> 1));
+            if ((m & 1) == 0)
+                w = philox_rk(make_uint4((uint32_t)eo, 0u, stream_word(kHotStart, (uint32_t)parity, (uint32_t)mu),
+                                         (uint32_t)(m >> 1)),
+                              rk);
             const float x = __fsub_rn(__fmul_rn(2.0f, uniform01((m & 1) ? w.z : w.x)), 1.0f);
             const float y = __fsub_rn(__fmul_rn(2.0f, uniform01((m & 1) ? w.w : w.y)), 1.0f);
             const float s = __fmaf_rn(x, x, __fmul_rn(y, y));
@@ -157,8 +160,8 @@ su2_status launch_cold_start(su2_lattice *lat)
 su2_status launch_hot_start(su2_lattice *lat)
 {
     const int64_t n = 8 * (int64_t)lat->vh;
-    hot_start_kernel<<<grid_for(n, 256), 256, 0, lat->stream>>>(lat->links, geom_of(lat), (uint32_t)lat->seed,
-                                                                (uint32_t)(lat->seed >> 32), lat->scratch.flags);
+    hot_start_kernel<<<grid_for(n, 256), 256, 0, lat->stream>>>(lat->links, geom_of(lat),
+                                                                make_round_keys(lat->seed), lat->scratch.flags);
     SU2_CUDA(cudaGetLastError());
     return SU2_OK;
 }

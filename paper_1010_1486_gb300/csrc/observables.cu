@@ -66,7 +66,7 @@ __device__ __forceinline__ float site_plaquette(const float4 *__restrict__ L, co
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
         u[mu] = __ldg(L + link_index(g, mu, parity, eo));
-        e_fwd[mu] = coord_to_eo(g, step(g, x, mu, +1));
+        e_fwd[mu] = lex_fwd(g, x.lex, x.c[mu], mu) >> 1;
     }
     float sum = 0.0f;
 #pragma unroll

@@ -11,7 +11,7 @@ __global__ void philox_selftest_kernel(const uint32_t *__restrict__ ck, uint32_t
 {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const uint32_t *r = ck + 6 * i;
-        const uint4 w = philox4x32_10(make_uint4(r[2], r[3], r[4], r[5]), r[0], r[1]);
+        const uint4 w = philox_rk(make_uint4(r[2], r[3], r[4], r[5]), make_round_keys(r[0], r[1]));
         out[4 * i + 0] = w.x;
         out[4 * i + 1] = w.y;
         out[4 * i + 2] = w.z;

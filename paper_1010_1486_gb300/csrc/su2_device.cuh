@@ -15,10 +15,30 @@
 namespace su2 {
 
 // ---------------------------------------------------------------- Philox
-// Philox4x32-10: ten rounds; each round multiplies words 0 and 2 by the two
-// round constants (full 64-bit products), xors the high halves with words
-// 1, 3 and the key, and the key advances by the two Weyl constants.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+// Philox4x32-10: ten rounds; each multiplies words 0 and 2 by the two round
+// constants (full 64-bit products) and xors the high halves with words 1, 3
+// and the round key; the key advances by the two Weyl constants per round.
+// Round keys (k0 + r W0, k1 + r W1), r = 0..9, are computed once and passed
+// by value, so in a kernel parameter they are read from the constant bank.
+struct RoundKeys {
+    uint32_t k0[10], k1[10];
+};
+
+__host__ __device__ inline RoundKeys make_round_keys(uint32_t a, uint32_t b)
+{
+    RoundKeys rk;
+    for (int r = 0; r < 10; ++r) {
+        rk.k0[r] = a;
+        rk.k1[r] = b;
+        a += 0x9E3779B9u;
+        b += 0xBB67AE85u;
+    }
+    return rk;
+}
+
+inline RoundKeys make_round_keys(uint64_t seed) { return make_round_keys((uint32_t)seed, (uint32_t)(seed >> 32)); }
+
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const RoundKeys &rk)
 {
 #pragma unroll
     for (int round = 0; round < 10; ++round) {
@@ -26,9 +46,7 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
         const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
         const uint32_t lo1 = 0xCD9E8D57u * c.z;
         const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
+        c = make_uint4(hi1 ^ c.y ^ rk.k0[round], lo1, hi0 ^ c.w ^ rk.k1[round], lo0);
     }
     return c;
 }
@@ -39,13 +57,12 @@ __device__ __forceinline__ float uniform01(uint32_t w)
     return __fmul_rn(__uint2float_rn((w >> 8) + 1u), 5.9604644775390625e-8f);
 }
 
-// Stream kinds of the counter word c2 = (kind << 3) | (parity << 2) | mu.
+// Counter of a draw: (even/odd site index, sweep, (kind << 3) | (parity << 2) | mu, block).
 enum StreamKind : uint32_t { kCreutz = 0, kDirection = 1, kHotStart = 2, kLearned = 3 };
 
-__device__ __forceinline__ uint4 draw(uint32_t k0, uint32_t k1, uint32_t eo, uint32_t sweep, uint32_t kind,
-                                      uint32_t parity, uint32_t mu, uint32_t block)
+__device__ __forceinline__ uint32_t stream_word(uint32_t kind, uint32_t parity, uint32_t mu)
 {
-    return philox4x32_10(make_uint4(eo, sweep, (kind << 3) | (parity << 2) | mu, block), k0, k1);
+    return (kind << 3) | (parity << 2) | mu;
 }
 
 // ------------------------------------------------------ elementary functions
@@ -161,57 +178,55 @@ __device__ __forceinline__ float qnorm2(float4 a) { return chain4(a.x, a.x, a.y,
 
 // ------------------------------------------------------------ heat bath
 constexpr int kMaxTrials = 4096;
+constexpr float kHaarBelow = 1e-6f;  // beta k below this: a0 from the Haar marginal
+constexpr float kExpCutoff = 43.0f;  // beta k above this: exp(-2 beta k) taken as 0
 
-// Heat-bath draw of one link from its staple v (Sec. 2).
-//   k = |v| = sqrt(det V), U~^dag = v^dag / k
-//   a0 ~ sqrt(1 - a0^2) exp(beta k a0): Creutz's method -- a0 = 1 + ln(x)/(beta k),
-//     x uniform in [exp(-2 beta k), 1], kept iff r2^2 <= 1 - a0^2; trial t uses
-//     words 2(t&1), 2(t&1)+1 of Creutz block t>>1.  beta k < 1e-6: a0 = 2 r1 - 1
-//     with the same test (the Haar marginal); beta k > 43: exp(-2 beta k) -> 0.
-//   direction: c = 2 u0 - 1, phi = 2 pi u1 from direction block 0;
-//   a = (a0, r s cos phi, r s sin phi, r c), r = sqrt(1-a0^2), s = sqrt(1-c^2);
-//   U' = a U~^dag.
-// Returns the trial count (>= 1) or 0 if kMaxTrials trials were rejected.
-__device__ __forceinline__ int heatbath_draw(float4 v, float beta, uint32_t k0, uint32_t k1, uint32_t eo,
-                                             uint32_t sweep, uint32_t parity, uint32_t mu, float4 &out)
+// Normalised staple (Sec. 2): k = |v| = sqrt(det V), U~^dag = v^dag / k
+// (identity if k = 0), bk = beta k, e = exp(-2 beta k) (0 when beta k > 43 or
+// on the Haar branch).
+struct DrawSetup {
+    float4 ut;
+    float bk;
+    float e;
+};
+
+__device__ __forceinline__ DrawSetup prepare_draw(float4 v, float beta)
 {
+    DrawSetup d;
     const float k = __fsqrt_rn(qnorm2(v));
-    float4 ut = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+    d.ut = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
     if (k > 0.0f) {
         const float inv_k = __fdiv_rn(1.0f, k);
-        ut = make_float4(__fmul_rn(v.x, inv_k), __fmul_rn(-v.y, inv_k), __fmul_rn(-v.z, inv_k),
-                         __fmul_rn(-v.w, inv_k));
+        d.ut = make_float4(__fmul_rn(v.x, inv_k), __fmul_rn(-v.y, inv_k), __fmul_rn(-v.z, inv_k),
+                           __fmul_rn(-v.w, inv_k));
     }
-    const float bk = __fmul_rn(beta, k);
-    const bool haar = bk < 1e-6f;
-    float e = 0.0f;
-    if (!haar && bk <= 43.0f) e = exp_series(__fmul_rn(-2.0f, bk));
-    const float one_minus_e = __fsub_rn(1.0f, e);
+    d.bk = __fmul_rn(beta, k);
+    d.e = 0.0f;
+    if (!(d.bk < kHaarBelow) && d.bk <= kExpCutoff) d.e = exp_series(__fmul_rn(-2.0f, d.bk));
+    return d;
+}
 
-    float a0 = 0.0f;
-    int trials = 0;
-    uint4 w = make_uint4(0u, 0u, 0u, 0u);
-    for (int t = 0; t < kMaxTrials; ++t) {
-        if ((t & 1) == 0) w = draw(k0, k1, eo, sweep, kCreutz, parity, mu, (uint32_t)(t >> 1));
-        const float r1 = uniform01((t & 1) ? w.z : w.x);
-        const float r2 = uniform01((t & 1) ? w.w : w.y);
-        float cand;
-        if (haar) {
-            cand = __fsub_rn(__fmul_rn(2.0f, r1), 1.0f);
-        } else {
-            const float x = __fmaf_rn(r1, one_minus_e, e);
-            cand = __fadd_rn(1.0f, __fdiv_rn(log_series(x), bk));
-        }
-        cand = cand < -1.0f ? -1.0f : (cand > 1.0f ? 1.0f : cand);
-        if (__fmul_rn(r2, r2) <= __fmaf_rn(-cand, cand, 1.0f)) {
-            a0 = cand;
-            trials = t + 1;
-            break;
-        }
+// One Creutz trial (Phys. Rev. D 21, 2308): candidate a0 = 1 + ln(x)/(beta k),
+// x = e + r1 (1 - e) uniform in [exp(-2 beta k), 1]; on the Haar branch
+// a0 = 2 r1 - 1.  Clamped to [-1, 1]; accepted iff r2^2 <= 1 - a0^2.
+__device__ __forceinline__ bool creutz_trial(float r1, float r2, float bk, float e, float one_minus_e, bool haar,
+                                             float &cand)
+{
+    float c;
+    if (haar) {
+        c = __fsub_rn(__fmul_rn(2.0f, r1), 1.0f);
+    } else {
+        c = __fadd_rn(1.0f, __fdiv_rn(log_series(__fmaf_rn(r1, one_minus_e, e)), bk));
     }
-    if (trials == 0) return 0;
+    c = c < -1.0f ? -1.0f : (c > 1.0f ? 1.0f : c);
+    cand = c;
+    return __fmul_rn(r2, r2) <= __fmaf_rn(-c, c, 1.0f);
+}
 
-    const uint4 d = draw(k0, k1, eo, sweep, kDirection, parity, mu, 0u);
+// Vector part uniform on the sphere of radius sqrt(1 - a0^2): c = 2 u0 - 1,
+// phi = 2 pi u1 (direction block 0); returns U' = a U~^dag.
+__device__ __forceinline__ float4 direction_update(float a0, float4 ut, uint4 d)
+{
     const float r = __fsqrt_rn(__fmaf_rn(-a0, a0, 1.0f));
     const float c = __fsub_rn(__fmul_rn(2.0f, uniform01(d.x)), 1.0f);
     const float st = __fsqrt_rn(__fmaf_rn(-c, c, 1.0f));
@@ -219,8 +234,61 @@ __device__ __forceinline__ int heatbath_draw(float4 v, float beta, uint32_t k0, 
     sincos_2pi(uniform01(d.y), sn, cs);
     const float rs = __fmul_rn(r, st);
     const float4 a = make_float4(a0, __fmul_rn(rs, cs), __fmul_rn(rs, sn), __fmul_rn(r, c));
-    out = qmul(a, ut);
+    return qmul(a, ut);
+}
+
+// The whole heat-bath draw of one link from its staple v (Sec. 2), trial by
+// trial: trial t uses words 2(t&1), 2(t&1)+1 of Creutz block t>>1; the
+// direction uses words 0, 1 of direction block 0.  Returns the number of
+// trials, or 0 if kMaxTrials were all rejected (out untouched).
+__device__ __forceinline__ int heatbath_draw(float4 v, float beta, const RoundKeys &rk, uint32_t eo, uint32_t sweep,
+                                             uint32_t parity, uint32_t mu, float4 &out)
+{
+    const DrawSetup s = prepare_draw(v, beta);
+    const bool haar = s.bk < kHaarBelow;
+    const float ome = __fsub_rn(1.0f, s.e);
+    float a0 = 0.0f;
+    int trials = 0;
+    for (int b = 0; b < kMaxTrials / 2 && trials == 0; ++b) {
+        const uint4 w = philox_rk(make_uint4(eo, sweep, stream_word(kCreutz, parity, mu), (uint32_t)b), rk);
+        float cand;
+        if (creutz_trial(uniform01(w.x), uniform01(w.y), s.bk, s.e, ome, haar, cand)) {
+            a0 = cand;
+            trials = 2 * b + 1;
+        } else if (creutz_trial(uniform01(w.z), uniform01(w.w), s.bk, s.e, ome, haar, cand)) {
+            a0 = cand;
+            trials = 2 * b + 2;
+        }
+    }
+    if (trials == 0) return 0;
+    out = direction_update(a0, s.ut, philox_rk(make_uint4(eo, sweep, stream_word(kDirection, parity, mu), 0u), rk));
     return trials;
+}
+
+// Division by an invariant positive integer d < 2^31 with a multiply-high and
+// shifts (Granlund & Montgomery, PLDI 1994, Fig. 4.1): with l = ceil(log2 d),
+// m = floor(2^32 (2^l - d) / d) + 1, q = (t + ((n - t) >> min(l,1))) >> max(l-1,0),
+// t = mulhi(m, n), exact for every 32-bit n.
+struct FastDiv {
+    uint32_t d, m, s1, s2;
+};
+
+inline FastDiv make_fastdiv(uint32_t d)
+{
+    uint32_t l = 0;
+    while ((1ull << l) < d) ++l;
+    FastDiv f;
+    f.d = d;
+    f.m = (uint32_t)((((1ull << 32) * ((1ull << l) - d)) / d) + 1);
+    f.s1 = l < 1 ? l : 1;
+    f.s2 = l > 1 ? l - 1 : 0;
+    return f;
+}
+
+__device__ __forceinline__ uint32_t fastdiv(uint32_t n, const FastDiv &f)
+{
+    const uint32_t t = __umulhi(f.m, n);
+    return (t + ((n - t) >> f.s1)) >> f.s2;
 }
 
 // --------------------------------------------------------------- geometry
@@ -229,43 +297,47 @@ __device__ __forceinline__ int heatbath_draw(float4 v, float beta, uint32_t k0, 
 // at (2 mu + parity) vh + i, vh = V/2.
 struct Geom {
     int ns, nt;
-    int vh;   // V / 2
-    int vs;   // Ns^3
+    int vh;         // V / 2
+    int vs;         // Ns^3
+    FastDiv div_ns;
+    int ext[4];     // extent of direction mu
+    int stride[4];  // lexicographic stride of direction mu: 1, Ns, Ns^2, Ns^3
+    int wrap[4];    // (extent - 1) * stride: the jump across the periodic boundary
 };
 
 struct Coord {
     int c[4];
+    int lex;
 };
 
-// Site of parity p with even/odd index i.
+// Site of parity p with even/odd index i: lex = 2i or 2i + 1, whichever has
+// parity p (Ns is even, so the two share y, z, t).
 __device__ __forceinline__ Coord eo_to_coord(const Geom &g, int i, int p)
 {
-    const int lex0 = 2 * i;
+    const uint32_t lex0 = 2u * (uint32_t)i;
     Coord r;
-    int rest = lex0 / g.ns;
-    const int x0 = lex0 - rest * g.ns;
-    const int rest2 = rest / g.ns;
-    r.c[1] = rest - rest2 * g.ns;
-    r.c[3] = rest2 / g.ns;
-    r.c[2] = rest2 - r.c[3] * g.ns;
-    r.c[0] = x0 + ((r.c[1] + r.c[2] + r.c[3] + p) & 1);
+    const uint32_t rest = fastdiv(lex0, g.div_ns);
+    const uint32_t x0 = lex0 - rest * (uint32_t)g.ns;
+    const uint32_t rest2 = fastdiv(rest, g.div_ns);
+    r.c[1] = (int)(rest - rest2 * (uint32_t)g.ns);
+    r.c[3] = (int)fastdiv(rest2, g.div_ns);
+    r.c[2] = (int)rest2 - r.c[3] * g.ns;
+    const int odd = (r.c[1] + r.c[2] + r.c[3] + p) & 1;
+    r.c[0] = (int)x0 + odd;
+    r.lex = (int)lex0 + odd;
     return r;
 }
 
-__device__ __forceinline__ int coord_to_eo(const Geom &g, const Coord &x)
+// Lexicographic index of the neighbour at +mu / -mu of a site with index lex
+// and coordinate c_mu in direction mu (periodic).
+__device__ __forceinline__ int lex_fwd(const Geom &g, int lex, int c_mu, int mu)
 {
-    return (((x.c[3] * g.ns + x.c[2]) * g.ns + x.c[1]) * g.ns + x.c[0]) >> 1;
+    return c_mu == g.ext[mu] - 1 ? lex - g.wrap[mu] : lex + g.stride[mu];
 }
 
-__device__ __forceinline__ int extent(const Geom &g, int mu) { return mu == 3 ? g.nt : g.ns; }
-
-__device__ __forceinline__ Coord step(const Geom &g, Coord x, int mu, int s)
+__device__ __forceinline__ int lex_bwd(const Geom &g, int lex, int c_mu, int mu)
 {
-    const int L = extent(g, mu);
-    int v = x.c[mu] + s;
-    v = v < 0 ? v + L : (v >= L ? v - L : v);
-    x.c[mu] = v;
-    return x;
+    return c_mu == 0 ? lex + g.wrap[mu] : lex - g.stride[mu];
 }
 
 __device__ __forceinline__ size_t link_index(const Geom &g, int mu, int parity, int eo)

@@ -15,7 +15,7 @@ namespace su2 {
 
 constexpr int kTrialSlots = 64;      // trial counters are spread over 64 slots per phase
 constexpr int kReduceThreads = 256;  // block size of the observable kernels
-constexpr int kHbThreads = 256;      // block size of the heat-bath phase kernel
+constexpr int kHbThreads = 128;      // block size of the heat-bath phase kernel (4 warps)
 
 // Device scratch of a lattice, carved from one allocation.
 struct DeviceScratch {
@@ -87,6 +87,14 @@ inline Geom geom_of(const su2_lattice *lat)
     g.nt = lat->nt;
     g.vh = lat->vh;
     g.vs = lat->ns * lat->ns * lat->ns;
+    g.div_ns = make_fastdiv((uint32_t)lat->ns);
+    int stride = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        g.ext[mu] = mu == 3 ? lat->nt : lat->ns;
+        g.stride[mu] = stride;
+        g.wrap[mu] = (g.ext[mu] - 1) * stride;
+        stride *= g.ext[mu];
+    }
     return g;
 }
 
