@@ -159,6 +159,27 @@ su2_status su2_set_timing(su2_lattice *lat, int enable);
 su2_status su2_selftest_philox(const uint32_t *ck, uint32_t *out, size_t n);
 su2_status su2_selftest_math(int which, const float *x, float *y, float *y2, size_t n);
 
+/* Mean plaquette of links that already sit in device memory, computed without
+ * allocating anything (no cudaMalloc, cudaFree or allocating library call).
+ * The paper has no counterpart: this is for callers that cannot allocate
+ * device memory where they need the observable, e.g. a process whose
+ * framework has claimed all device memory for its own pool, or code running
+ * where an allocation would stall or is forbidden.
+ *   links  device pointer to 8 (V/2) float4 in the even/odd layout described at
+ *          su2_device_links (V = ns^3 nt), read only;
+ *   out    device pointer to one double, written in stream order (same value as
+ *          su2_plaquette up to the order of the fp64 sum);
+ *   cuda_stream  cudaStream_t or NULL.  The call does not synchronise.
+ * Limits: ns, nt even and >= 2; V <= 67,108,864 sites, else SU2_E_INVAL with
+ * the limit in su2_last_error().  Scratch: a fixed 131,328-byte device array
+ * inside libsu2 (held on every GPU that loads the library until exit).  The
+ * first call on each device looks up that array's address
+ * (cudaGetSymbolAddress), so make it before capturing a stream into a CUDA
+ * graph.  All calls share the array and it keeps the last call's contents:
+ * calls whose kernels may overlap on the GPU (unordered streams) race and
+ * give wrong results -- order them. */
+su2_status su2_plaquette_noalloc(const void *links, int ns, int nt, double *out, void *cuda_stream);
+
 /* Human-readable status and the last CUDA error text of this thread. */
 const char *su2_status_str(su2_status s);
 const char *su2_last_error(void);

@@ -79,6 +79,7 @@ _SIGS = {
     "su2_set_timing": [_P, _i32],
     "su2_selftest_philox": [_P, _P, ctypes.c_size_t],
     "su2_selftest_math": [_i32, _P, _P, _P, ctypes.c_size_t],
+    "su2_plaquette_noalloc": [_P, _i32, _i32, _P, _P],
 }
 for _name, _args in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -260,6 +261,14 @@ def su2_selftest_math(which: int, x: np.ndarray):
     _check(_lib.su2_selftest_math(which, _host_ptr(x), _host_ptr(y), _host_ptr(y2) if y2 is not None else None,
                                   x.size), "su2_selftest_math")
     return (y, y2) if which == 2 else y
+
+
+def su2_plaquette_noalloc(links_ptr: int, ns: int, nt: int, out_ptr: int, stream=None) -> None:
+    """Mean plaquette of device-resident links (even/odd layout of
+    su2_device_links) into the device double at out_ptr, allocating nothing.
+    For callers that cannot allocate device memory at this point; see
+    include/su2.h for the scratch it shares between calls and its size limit."""
+    _check(_lib.su2_plaquette_noalloc(links_ptr, ns, nt, out_ptr, _stream_handle(stream)), "su2_plaquette_noalloc")
 
 
 def su2_status_str(status: int) -> str:
