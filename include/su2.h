@@ -159,6 +159,55 @@ su2_status su2_set_timing(su2_lattice *lat, int enable);
 su2_status su2_selftest_philox(const uint32_t *ck, uint32_t *out, size_t n);
 su2_status su2_selftest_math(int which, const float *x, float *y, float *y2, size_t n);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many independent lattices (own Ns^3 x Nt, beta and seed each) swept
+ * together.  Each lattice follows exactly the chain of su2_create +
+ * su2_heatbath_sweep with its own arguments.  One sweep of the whole batch is
+ * one persistent cooperative kernel launch: the eight even/odd phases of every
+ * lattice with a grid-wide barrier between phases (each barrier wait bounded,
+ * 2 s), then optionally the plaquette and Polyakov loop of every lattice.  On
+ * a non-NULL stream the launch is captured into a CUDA graph once and replayed
+ * per sweep.  The batch owns its device memory like a lattice.
+ * ------------------------------------------------------------------------- */
+typedef struct su2_batch su2_batch;
+
+/* n >= 1 lattices; ns[i], nt[i] even >= 2 with 4 V_i < 2^31; beta[i] finite
+ * >= 0; seed[i] any.  Cold or hot start for all.  Fails with SU2_E_CUDA on a
+ * device without cooperative launches. */
+su2_status su2_batch_create(int n, const int *ns, const int *nt, const double *beta, const uint64_t *seed,
+                            su2_start start, void *cuda_stream, su2_batch **out);
+su2_status su2_batch_destroy(su2_batch *b);
+
+/* nsweeps sweeps of every lattice; synchronises; stats (nullable) sum the
+ * trials over lattices.  SU2_E_DEVICE_TIMEOUT if a barrier wait gave up. */
+su2_status su2_batch_sweep(su2_batch *b, int nsweeps, su2_stats *stats);
+
+/* Sweeps with the plaquette and Polyakov loop of every lattice after every
+ * measure_every-th sweep: plaq and poly (host, nullable) receive
+ * (nsweeps / measure_every) x n values, row m = measurement m, column = lattice. */
+su2_status su2_batch_generate(su2_batch *b, int nsweeps, int measure_every, double *plaq, double *poly,
+                              su2_stats *stats);
+
+/* Current plaquette / Polyakov loop of every lattice (out: n doubles). */
+su2_status su2_batch_plaquette(su2_batch *b, double *out_n);
+su2_status su2_batch_polyakov(su2_batch *b, double *out_n);
+
+/* Links of lattice i in the layout of su2_get_links. */
+su2_status su2_batch_get_links(su2_batch *b, int i, float *host);
+
+/* Launch configuration: queue depth (pending links per lane: 2, 4 or 8) and
+ * grid (blocks of 128 threads; <= 0 or too large = all co-resident blocks).
+ * su2_batch_autotune times every depth with the full and the half grid over
+ * `sweeps` sweeps, restores the links and sweep counter, and keeps the fastest. */
+su2_status su2_batch_set_config(su2_batch *b, int queue_depth, int grid);
+su2_status su2_batch_autotune(su2_batch *b, int sweeps, int *queue_depth, int *grid);
+su2_status su2_batch_info(su2_batch *b, int *n, uint32_t *sweep, int *queue_depth, int *grid, int *graphs);
+
+/* Self-test of the bounded grid-barrier wait: `blocks` blocks wait for one
+ * arrival more than there are blocks, so every wait must give up after
+ * timeout_ns (<= 5 s); *timed_out receives the number of blocks that did. */
+su2_status su2_selftest_barrier_timeout(int blocks, uint64_t timeout_ns, unsigned int *timed_out);
+
 /* Mean plaquette of links that already sit in device memory, computed without
  * allocating anything (no cudaMalloc, cudaFree or allocating library call).
  * The paper has no counterpart: this is for callers that cannot allocate

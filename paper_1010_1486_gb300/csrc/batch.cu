@@ -1,0 +1,901 @@
+// batch.cu -- many independent lattices (uneven Ns^3 x Nt, own beta and seed)
+// swept together: one persistent cooperative launch per sweep runs the eight
+// even/odd phases of every lattice (Sec. 2 update, Sec. 4 schedule) with a
+// grid-wide barrier between phases, then the plaquette and Polyakov loop of
+// every lattice (Sec. 4), each reduced in a fixed order.  With a user stream
+// the launch is captured once into a CUDA graph and replayed per sweep.
+//
+// Each lattice follows exactly the single-lattice chain: same Philox
+// counters (its own seed as key), same arithmetic, so its links equal those
+// of su2_create + su2_heatbath_sweep with the same arguments.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "observables.cuh"
+#include "su2_device.cuh"
+#include "su2_internal.h"
+
+namespace su2 {
+
+struct LatDesc {
+    Geom g;
+    float4 *links;
+    uint32_t k0, k1;  // Philox key = seed
+    float beta;
+    int nplaq_rounds;  // ceil(V / 32) rounds of plaquette sites
+    int npoly_rounds;  // ceil(Ns^3 / 32) rounds of Polyakov lines
+};
+
+struct BarrierState {
+    unsigned int count;
+    unsigned int gen;
+    unsigned int error;  // bit 0: a barrier wait timed out
+    unsigned int pad;
+};
+
+struct BatchParams {
+    const LatDesc *desc;        // [n]
+    const int *chunk_prefix;    // [n + 1]: first heat-bath chunk of each lattice
+    const int *mround_prefix;   // [n + 1]: first measurement round of each lattice
+    int n;
+    int total_chunks;
+    int total_mrounds;
+    int do_sweep;               // run the eight phases
+    int measure;                // then the plaquette and Polyakov loop
+    unsigned int *sweep;        // sweep counter: read at start, advanced at the end
+    unsigned int *meas_index;   // next history slot
+    double *round_partials;     // [total_mrounds]
+    double *history;            // [history_cap][2][n]
+    int history_cap;
+    BarrierState *bar;
+    unsigned long long timeout_ns;
+    unsigned long long *trial_slots;  // [8][kTrialSlots]
+    unsigned int *flags;              // [0] sampler cap hits
+};
+
+__device__ __forceinline__ unsigned long long global_time_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident).  Every
+// wait is bounded by timeout_ns: on expiry the block sets bar->error and all
+// blocks stop waiting; the function then returns false everywhere and the
+// caller abandons the sweep.
+__device__ bool grid_barrier(BarrierState *bar, unsigned long long timeout_ns)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int *vgen = &bar->gen;
+        volatile unsigned int *verr = &bar->error;
+        const unsigned int g = *vgen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&bar->count, 1u) + 1u;
+        if (arrived == gridDim.x) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            const unsigned long long t0 = global_time_ns();
+            while (*vgen == g) {
+                if (*verr & 1u) break;
+                if (global_time_ns() - t0 > timeout_ns) {
+                    atomicOr(&bar->error, 1u);
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        ok = (*verr & 1u) == 0u;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Largest l in [0, n) with prefix[l] <= x (prefix[0] = 0, increasing).
+__device__ __forceinline__ int find_owner(const int *__restrict__ prefix, int n, int x)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(prefix + mid) <= x)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Staple of U_mu(x) (Sec. 2), nu ascending, forward then backward term.
+template <int MU>
+__device__ __forceinline__ float4 staple_at(const float4 *__restrict__ L, const Geom &g, const Coord &x, int parity)
+{
+    const int op = parity ^ 1;
+    const int lex_p = lex_fwd(g, x.lex, x.c[MU], MU);
+    float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+    for (int nu = 0; nu < 4; ++nu) {
+        if (nu == MU) continue;
+        const int e_xn = lex_fwd(g, x.lex, x.c[nu], nu) >> 1;
+        const int e_xm = lex_bwd(g, x.lex, x.c[nu], nu) >> 1;
+        const int e_xpm = lex_bwd(g, lex_p, x.c[nu], nu) >> 1;
+        const float4 a = __ldg(L + link_index(g, nu, op, lex_p >> 1));
+        const float4 b = __ldg(L + link_index(g, MU, op, e_xn));
+        const float4 c = __ldg(L + link_index(g, nu, parity, x.lex >> 1));
+        const float4 d = __ldg(L + link_index(g, nu, parity, e_xpm));
+        const float4 e = __ldg(L + link_index(g, MU, op, e_xm));
+        const float4 f = __ldg(L + link_index(g, nu, op, e_xm));
+        v = qadd(v, qmul(qmul(a, qdag(b)), qdag(c)));
+        v = qadd(v, qmul(qmul(qdag(d), qdag(e)), f));
+    }
+    return v;
+}
+
+// One phase (MU, parity) over every lattice: chunks of 32 R consecutive
+// even/odd sites of one lattice; per chunk the warp computes the staples
+// (A), runs the Creutz trials with a lane work queue (B), and draws the
+// directions and stores (C), as in the single-lattice kernel.
+template <int MU, int R>
+__device__ void batch_phase(const BatchParams &bp, int parity, uint32_t sweep, float4 *ut_q, float *bk_q,
+                            float *e_q, unsigned int &my_trials)
+{
+    constexpr int Q = 32 * R;
+    const int lane = threadIdx.x & 31;
+    const unsigned int lanes_below = (1u << lane) - 1u;
+    const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t sw_creutz = stream_word(kCreutz, (uint32_t)parity, MU);
+    const uint32_t sw_dir = stream_word(kDirection, (uint32_t)parity, MU);
+    for (int chunk = warp_global; chunk < bp.total_chunks; chunk += nwarps) {
+        const int l = find_owner(bp.chunk_prefix, bp.n, chunk);
+        const LatDesc *d = bp.desc + l;
+        const Geom g = d->g;
+        float4 *const links = d->links;
+        const uint32_t k0 = d->k0, k1 = d->k1;
+        const float beta = d->beta;
+        const int base = (chunk - __ldg(bp.chunk_prefix + l)) * Q;
+        const int n_items = min(Q, g.vh - base);
+
+#pragma unroll 1
+        for (int r = 0; r < R; ++r) {
+            const int j = r * 32 + lane;
+            if (j < n_items) {
+                const Coord x = eo_to_coord(g, base + j, parity);
+                const DrawSetup s = prepare_draw(staple_at<MU>(links, g, x, parity), beta);
+                ut_q[j] = s.ut;
+                bk_q[j] = s.bk;
+                e_q[j] = s.e;
+            }
+        }
+        __syncwarp();
+
+        int item = lane < n_items ? lane : -1;
+        int next = 32;
+        uint32_t blk = 0;
+        float bk = 0.0f, e = 0.0f, ome = 1.0f;
+        bool haar = false;
+        if (item >= 0) {
+            bk = bk_q[item];
+            e = e_q[item];
+            ome = __fsub_rn(1.0f, e);
+            haar = bk < kHaarBelow;
+        }
+        while (__any_sync(0xffffffffu, item >= 0)) {
+            bool done = false;
+            if (item >= 0) {
+                const uint4 w = philox_key(make_uint4((uint32_t)(base + item), sweep, sw_creutz, blk), k0, k1);
+                float cand;
+                uint32_t t = 0;
+                if (creutz_trial(uniform01(w.x), uniform01(w.y), bk, e, ome, haar, cand))
+                    t = 2 * blk + 1;
+                else if (creutz_trial(uniform01(w.z), uniform01(w.w), bk, e, ome, haar, cand))
+                    t = 2 * blk + 2;
+                if (t) {
+                    bk_q[item] = cand;
+                    my_trials += t;
+                    done = true;
+                } else if (++blk == (uint32_t)(kMaxTrials / 2)) {
+                    bk_q[item] = __int_as_float(0x7fc00000);
+                    my_trials += kMaxTrials;
+                    done = true;
+                }
+            }
+            const unsigned int mask = __ballot_sync(0xffffffffu, done);
+            if (done) {
+                const int idx = next + __popc(mask & lanes_below);
+                item = idx < n_items ? idx : -1;
+                blk = 0;
+                if (item >= 0) {
+                    bk = bk_q[item];
+                    e = e_q[item];
+                    ome = __fsub_rn(1.0f, e);
+                    haar = bk < kHaarBelow;
+                }
+            }
+            next += __popc(mask);
+        }
+        __syncwarp();
+
+#pragma unroll 1
+        for (int r = 0; r < R; ++r) {
+            const int j = r * 32 + lane;
+            if (j < n_items) {
+                const int eo = base + j;
+                const float a0 = bk_q[j];
+                if (a0 == a0) {
+                    const uint4 dw = philox_key(make_uint4((uint32_t)eo, sweep, sw_dir, 0u), k0, k1);
+                    links[link_index(g, MU, parity, eo)] = direction_update(a0, ut_q[j], dw);
+                } else {
+                    atomicAdd(&bp.flags[0], 1u);
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// Per round of 32 sites (or 32 Polyakov lines) of one lattice: the warp's
+// fp64 sum of the binary32 per-site values, in a fixed order.
+__device__ void batch_measure_rounds(const BatchParams &bp)
+{
+    const int lane = threadIdx.x & 31;
+    const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int mr = warp_global; mr < bp.total_mrounds; mr += nwarps) {
+        const int l = find_owner(bp.mround_prefix, bp.n, mr);
+        const LatDesc *d = bp.desc + l;
+        const Geom g = d->g;
+        const int local = mr - __ldg(bp.mround_prefix + l);
+        double val = 0.0;
+        if (local < d->nplaq_rounds) {
+            const int s = local * 32 + lane;
+            if (s < 2 * g.vh) {
+                const int parity = s >= g.vh;
+                const int eo = s - (parity ? g.vh : 0);
+                val = (double)site_plaquette(d->links, g, eo_to_coord(g, eo, parity), eo, parity);
+            }
+        } else {
+            const int xs = (local - d->nplaq_rounds) * 32 + lane;
+            if (xs < g.vs) val = (double)site_polyakov(d->links, g, xs);
+        }
+        val = warp_sum(val);
+        if (lane == 0) bp.round_partials[mr] = val;
+    }
+}
+
+// Per lattice: sums of its round partials in index order -> history slot.
+__device__ void batch_measure_final(const BatchParams &bp, unsigned int slot)
+{
+    const int lane = threadIdx.x & 31;
+    const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int l = warp_global; l < bp.n; l += nwarps) {
+        const LatDesc *d = bp.desc + l;
+        const int r0 = __ldg(bp.mround_prefix + l);
+        const int np = d->nplaq_rounds, nl = d->npoly_rounds;
+        double sp = 0.0, sl = 0.0;
+        for (int r = lane; r < np; r += 32) sp += ((volatile double *)bp.round_partials)[r0 + r];
+        for (int r = lane; r < nl; r += 32) sl += ((volatile double *)bp.round_partials)[r0 + np + r];
+        sp = warp_sum(sp);
+        sl = warp_sum(sl);
+        if (lane == 0) {
+            const double vol = 2.0 * (double)d->g.vh;
+            bp.history[((size_t)slot * 2 + 0) * bp.n + l] = sp / (6.0 * vol);
+            bp.history[((size_t)slot * 2 + 1) * bp.n + l] = sl / (double)d->g.vs;
+        }
+    }
+}
+
+template <int R>
+__global__ void __launch_bounds__(kHbThreads) batch_sweep_kernel(const BatchParams bp)
+{
+    constexpr int Q = 32 * R;
+    __shared__ float4 s_ut[kHbThreads / 32][Q];
+    __shared__ float s_bk[kHbThreads / 32][Q];
+    __shared__ float s_e[kHbThreads / 32][Q];
+    const int wib = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t sweep = *(volatile unsigned int *)bp.sweep;
+    const unsigned int slot = *(volatile unsigned int *)bp.meas_index;
+    bool ok = true;
+    if (bp.do_sweep) {
+        for (int ph = 0; ph < 8 && ok; ++ph) {
+            const int parity = ph & 1;
+            unsigned int my_trials = 0;
+            switch (ph >> 1) {
+            case 0: batch_phase<0, R>(bp, parity, sweep, s_ut[wib], s_bk[wib], s_e[wib], my_trials); break;
+            case 1: batch_phase<1, R>(bp, parity, sweep, s_ut[wib], s_bk[wib], s_e[wib], my_trials); break;
+            case 2: batch_phase<2, R>(bp, parity, sweep, s_ut[wib], s_bk[wib], s_e[wib], my_trials); break;
+            default: batch_phase<3, R>(bp, parity, sweep, s_ut[wib], s_bk[wib], s_e[wib], my_trials); break;
+            }
+            const unsigned int wsum = __reduce_add_sync(0xffffffffu, my_trials);
+            if (lane == 0 && wsum)
+                atomicAdd(&bp.trial_slots[ph * kTrialSlots + (warp_global & (kTrialSlots - 1))],
+                          (unsigned long long)wsum);
+            ok = grid_barrier(bp.bar, bp.timeout_ns);
+        }
+    }
+    if (ok && bp.measure && (int)slot < bp.history_cap) {
+        batch_measure_rounds(bp);
+        ok = grid_barrier(bp.bar, bp.timeout_ns);
+        if (ok) batch_measure_final(bp, slot);
+    }
+    if (ok && blockIdx.x == 0 && threadIdx.x == 0) {
+        if (bp.do_sweep) *bp.sweep = sweep + 1u;
+        if (bp.measure) *bp.meas_index = slot + 1u;
+    }
+}
+
+// Self-test of the barrier's timeout: `expect` arrivals are awaited but only
+// gridDim.x blocks exist, so with expect > gridDim.x every wait must give up
+// after timeout_ns and report it.  The arrival count is reset for the next use.
+__global__ void barrier_timeout_kernel(BarrierState *bar, unsigned int expect, unsigned long long timeout_ns,
+                                       unsigned int *timed_out)
+{
+    if (threadIdx.x == 0) {
+        volatile unsigned int *vgen = &bar->gen;
+        const unsigned int g = *vgen;
+        const unsigned int arrived = atomicAdd(&bar->count, 1u) + 1u;
+        if (arrived == expect) {
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            const unsigned long long t0 = global_time_ns();
+            while (*vgen == g) {
+                if (global_time_ns() - t0 > timeout_ns) {
+                    atomicAdd(timed_out, 1u);
+                    break;
+                }
+                __nanosleep(1000);
+            }
+        }
+    }
+}
+
+}  // namespace su2
+
+using namespace su2;
+
+struct su2_batch {
+    int n = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<int> ns, nt;
+    std::vector<double> beta;
+    std::vector<uint64_t> seed;
+    std::vector<Geom> geom;
+    std::vector<size_t> link_offset;  // in float4 units
+    void *block = nullptr;
+    size_t block_bytes = 0;
+    float4 *links = nullptr;
+    size_t links_count = 0;  // float4
+    LatDesc *d_desc = nullptr;
+    int *d_chunk_prefix = nullptr;
+    int *d_mround_prefix = nullptr;
+    double *d_partials = nullptr;
+    BarrierState *d_bar = nullptr;
+    unsigned int *d_counters = nullptr;  // [0] sweep, [1] measurement index, [2..] flags
+    unsigned long long *d_trials = nullptr;
+    double *d_history = nullptr;
+    int history_cap = 0;
+    int total_mrounds = 0;
+    int total_chunks = 0;
+    int R = 4;
+    int grid = 0;
+    int max_grid[3] = {0, 0, 0};  // co-resident blocks for R = 2, 4, 8
+    uint32_t sweep = 0;
+    unsigned long long timeout_ns = 2000000000ull;
+    bool use_graph = true;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // [measure]
+    void *staging = nullptr;
+    size_t staging_bytes = 0;
+};
+
+namespace su2 {
+namespace {
+
+int r_index(int R) { return R == 2 ? 0 : (R == 4 ? 1 : 2); }
+
+void *kernel_for(int R)
+{
+    if (R == 2) return (void *)batch_sweep_kernel<2>;
+    if (R == 8) return (void *)batch_sweep_kernel<8>;
+    return (void *)batch_sweep_kernel<4>;
+}
+
+void drop_graphs(su2_batch *b)
+{
+    for (auto &g : b->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+// Recomputes the heat-bath chunk table for queue depth R.
+su2_status set_depth(su2_batch *b, int R, int grid)
+{
+    std::vector<int> prefix(b->n + 1, 0);
+    for (int l = 0; l < b->n; ++l) prefix[l + 1] = prefix[l] + (b->geom[l].vh + 32 * R - 1) / (32 * R);
+    SU2_CUDA(cudaMemcpyAsync(b->d_chunk_prefix, prefix.data(), sizeof(int) * (b->n + 1), cudaMemcpyHostToDevice,
+                             b->stream));
+    SU2_CUDA(cudaStreamSynchronize(b->stream));
+    b->total_chunks = prefix[b->n];
+    b->R = R;
+    b->grid = grid;
+    drop_graphs(b);
+    return SU2_OK;
+}
+
+BatchParams params_of(const su2_batch *b, int do_sweep, int measure)
+{
+    BatchParams p;
+    p.desc = b->d_desc;
+    p.chunk_prefix = b->d_chunk_prefix;
+    p.mround_prefix = b->d_mround_prefix;
+    p.n = b->n;
+    p.total_chunks = b->total_chunks;
+    p.total_mrounds = b->total_mrounds;
+    p.do_sweep = do_sweep;
+    p.measure = measure;
+    p.sweep = b->d_counters;
+    p.meas_index = b->d_counters + 1;
+    p.round_partials = b->d_partials;
+    p.history = b->d_history;
+    p.history_cap = b->history_cap;
+    p.bar = b->d_bar;
+    p.timeout_ns = b->timeout_ns;
+    p.trial_slots = b->d_trials;
+    p.flags = b->d_counters + 2;
+    return p;
+}
+
+// Enqueues one launch: reset of the barrier state, then the cooperative kernel.
+cudaError_t enqueue_launch(su2_batch *b, int do_sweep, int measure)
+{
+    cudaError_t e = cudaMemsetAsync(b->d_bar, 0, sizeof(BarrierState), b->stream);
+    if (e != cudaSuccess) return e;
+    BatchParams p = params_of(b, do_sweep, measure);
+    void *args[] = {&p};
+    return cudaLaunchCooperativeKernel(kernel_for(b->R), dim3(b->grid), dim3(kHbThreads), args, 0, b->stream);
+}
+
+su2_status launch_sweep(su2_batch *b, int measure)
+{
+    if (b->use_graph && b->stream) {
+        cudaGraphExec_t &ge = b->graph[measure];
+        if (!ge) {
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                const cudaError_t le = enqueue_launch(b, 1, measure);
+                e = cudaStreamEndCapture(b->stream, &graph);
+                if (le != cudaSuccess) e = le;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                // capture of cooperative launches unavailable: launch directly from now on
+                cudaGetLastError();
+                ge = nullptr;
+                b->use_graph = false;
+            }
+        }
+        if (ge) {
+            SU2_CUDA(cudaGraphLaunch(ge, b->stream));
+            return SU2_OK;
+        }
+    }
+    SU2_CUDA(enqueue_launch(b, 1, measure));
+    return SU2_OK;
+}
+
+su2_status check_flags(su2_batch *b, su2_stats *stats, uint64_t sweeps, int launches)
+{
+    unsigned long long slots[8 * kTrialSlots];
+    unsigned int counters[4];
+    BarrierState bar;
+    SU2_CUDA(cudaMemcpyAsync(slots, b->d_trials, sizeof slots, cudaMemcpyDeviceToHost, b->stream));
+    SU2_CUDA(cudaMemcpyAsync(counters, b->d_counters, sizeof counters, cudaMemcpyDeviceToHost, b->stream));
+    SU2_CUDA(cudaMemcpyAsync(&bar, b->d_bar, sizeof bar, cudaMemcpyDeviceToHost, b->stream));
+    SU2_CUDA(cudaStreamSynchronize(b->stream));
+    uint64_t sites = 0;
+    for (const Geom &g : b->geom) sites += 2ull * (uint64_t)g.vh;
+    if (stats) {
+        memset(stats, 0, sizeof *stats);
+        for (int ph = 0; ph < 8; ++ph) {
+            uint64_t s = 0;
+            for (int j = 0; j < kTrialSlots; ++j) s += slots[ph * kTrialSlots + j];
+            stats->trials[ph] = s;
+        }
+        stats->sampler_failures = counters[2];
+        stats->sweeps = sweeps;
+        stats->link_updates = sweeps * 4ull * sites;
+        stats->kernel_launches = (uint32_t)launches;
+    }
+    b->sweep = counters[0];
+    if (bar.error & 1u) {
+        set_last_error("batch sweep: a grid barrier wait timed out");
+        return SU2_E_DEVICE_TIMEOUT;
+    }
+    if (counters[2]) {
+        set_last_error("heat-bath sampler hit its trial cap");
+        return SU2_E_SAMPLER;
+    }
+    return SU2_OK;
+}
+
+su2_status clear_stats(su2_batch *b)
+{
+    SU2_CUDA(cudaMemsetAsync(b->d_trials, 0, sizeof(unsigned long long) * 8 * kTrialSlots, b->stream));
+    SU2_CUDA(cudaMemsetAsync(b->d_counters + 2, 0, sizeof(unsigned int) * 2, b->stream));
+    return SU2_OK;
+}
+
+su2_status ensure_history(su2_batch *b, int n)
+{
+    if (n <= b->history_cap) return SU2_OK;
+    device_free(b->d_history, sizeof(double) * 2 * b->n * (size_t)b->history_cap, b->device, b->stream);
+    b->d_history = (double *)device_alloc(sizeof(double) * 2 * b->n * (size_t)n, b->device, b->stream);
+    b->history_cap = b->d_history ? n : 0;
+    drop_graphs(b);  // the graphs hold the old history pointer
+    if (!b->d_history) {
+        set_last_error("device allocation of the batch history failed");
+        return SU2_E_NOMEM;
+    }
+    return SU2_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+}  // namespace su2
+
+extern "C" {
+
+su2_status su2_batch_create(int n, const int *ns, const int *nt, const double *beta, const uint64_t *seed,
+                            su2_start start, void *cuda_stream, su2_batch **out)
+{
+    if (!out || !ns || !nt || !beta || !seed || n < 1) {
+        set_last_error("su2_batch_create: n >= 1 and non-NULL arrays required");
+        return SU2_E_INVAL;
+    }
+    *out = nullptr;
+    if (start != SU2_COLD && start != SU2_HOT) return SU2_E_INVAL;
+    for (int l = 0; l < n; ++l) {
+        if (ns[l] < 2 || nt[l] < 2 || (ns[l] & 1) || (nt[l] & 1) ||
+            4.0 * (double)ns[l] * ns[l] * ns[l] * nt[l] >= 2147483648.0) {
+            set_last_error("su2_batch_create: extents must be even, >= 2, 4V < 2^31 (lattice " + std::to_string(l) +
+                           ")");
+            return SU2_E_INVAL;
+        }
+        if (!std::isfinite(beta[l]) || beta[l] < 0.0) {
+            set_last_error("su2_batch_create: beta must be finite and >= 0 (lattice " + std::to_string(l) + ")");
+            return SU2_E_INVAL;
+        }
+    }
+    int dev = 0;
+    SU2_CUDA(cudaGetDevice(&dev));
+    int coop = 0;
+    SU2_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (!coop) {
+        set_last_error("device does not support cooperative launches");
+        return SU2_E_CUDA;
+    }
+    su2_batch *b = new (std::nothrow) su2_batch();
+    if (!b) return SU2_E_NOMEM;
+    b->n = n;
+    b->device = dev;
+    b->stream = (cudaStream_t)cuda_stream;
+    b->ns.assign(ns, ns + n);
+    b->nt.assign(nt, nt + n);
+    b->beta.assign(beta, beta + n);
+    b->seed.assign(seed, seed + n);
+    size_t off = 0;
+    std::vector<int> mprefix(n + 1, 0);
+    for (int l = 0; l < n; ++l) {
+        const Geom g = make_geom(ns[l], nt[l]);
+        b->geom.push_back(g);
+        b->link_offset.push_back(off);
+        off += (8 * (size_t)g.vh + 15) & ~(size_t)15;  // keep each lattice 256-byte aligned
+        const int np = (2 * g.vh + 31) / 32, nl = (g.vs + 31) / 32;
+        mprefix[l + 1] = mprefix[l] + np + nl;
+    }
+    b->links_count = off;
+    b->total_mrounds = mprefix[n];
+    const size_t links_bytes = align256(sizeof(float4) * off);
+    const size_t desc_bytes = align256(sizeof(LatDesc) * n);
+    const size_t prefix_bytes = align256(sizeof(int) * (n + 1));
+    const size_t partial_bytes = align256(sizeof(double) * b->total_mrounds);
+    const size_t bar_bytes = align256(sizeof(BarrierState));
+    const size_t counter_bytes = align256(sizeof(unsigned int) * 8);
+    const size_t trial_bytes = align256(sizeof(unsigned long long) * 8 * kTrialSlots);
+    b->block_bytes = links_bytes + desc_bytes + 2 * prefix_bytes + partial_bytes + bar_bytes + counter_bytes + trial_bytes;
+    b->block = device_alloc(b->block_bytes, dev, b->stream);
+    if (!b->block) {
+        delete b;
+        set_last_error("device allocation of the batch failed");
+        return SU2_E_NOMEM;
+    }
+    char *p = (char *)b->block;
+    b->links = (float4 *)p;
+    p += links_bytes;
+    b->d_desc = (LatDesc *)p;
+    p += desc_bytes;
+    b->d_chunk_prefix = (int *)p;
+    p += prefix_bytes;
+    b->d_mround_prefix = (int *)p;
+    p += prefix_bytes;
+    b->d_partials = (double *)p;
+    p += partial_bytes;
+    b->d_bar = (BarrierState *)p;
+    p += bar_bytes;
+    b->d_counters = (unsigned int *)p;
+    p += counter_bytes;
+    b->d_trials = (unsigned long long *)p;
+
+    std::vector<LatDesc> desc(n);
+    for (int l = 0; l < n; ++l) {
+        desc[l].g = b->geom[l];
+        desc[l].links = b->links + b->link_offset[l];
+        desc[l].k0 = (uint32_t)seed[l];
+        desc[l].k1 = (uint32_t)(seed[l] >> 32);
+        desc[l].beta = (float)beta[l];
+        desc[l].nplaq_rounds = (2 * b->geom[l].vh + 31) / 32;
+        desc[l].npoly_rounds = (b->geom[l].vs + 31) / 32;
+    }
+    su2_status st = SU2_OK;
+    cudaError_t e = cudaMemcpyAsync(b->d_desc, desc.data(), sizeof(LatDesc) * n, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_mround_prefix, mprefix.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bar, 0, bar_bytes + counter_bytes + trial_bytes, b->stream);
+    for (int l = 0; l < n && e == cudaSuccess; ++l)
+        e = start_links(b->links + b->link_offset[l], b->geom[l], start == SU2_HOT, seed[l], b->d_counters + 2,
+                        b->stream);  // the hot-start kernel counts failures in flags[1] = counter 3
+    if (e == cudaSuccess) {
+        for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+            const int R = i == 0 ? 2 : (i == 1 ? 4 : 8);
+            int per_sm = 0, sms = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_for(R), kHbThreads, 0);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            b->max_grid[i] = std::max(1, per_sm * sms);
+        }
+    }
+    if (e != cudaSuccess) st = cuda_fail(e, "su2_batch_create");
+    if (st == SU2_OK) st = set_depth(b, 4, b->max_grid[r_index(4)]);
+    if (st == SU2_OK) {
+        unsigned int c[4];
+        if (cudaMemcpyAsync(c, b->d_counters, sizeof c, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+            cudaStreamSynchronize(b->stream) != cudaSuccess)
+            st = cuda_fail(cudaGetLastError(), "su2_batch_create");
+        else if (c[3]) {
+            set_last_error("hot start: a link found no two disk points in 64 pairs");
+            st = SU2_E_SAMPLER;
+        }
+    }
+    if (st != SU2_OK) {
+        su2_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return SU2_OK;
+}
+
+su2_status su2_batch_destroy(su2_batch *b)
+{
+    if (!b) return SU2_OK;
+    DeviceGuard guard(b->device);
+    drop_graphs(b);
+    device_free(b->staging, b->staging_bytes, b->device, b->stream);
+    device_free(b->d_history, sizeof(double) * 2 * b->n * (size_t)b->history_cap, b->device, b->stream);
+    device_free(b->block, b->block_bytes, b->device, b->stream);
+    const cudaError_t e = cudaStreamSynchronize(b->stream);
+    delete b;
+    if (e != cudaSuccess) return cuda_fail(e, "su2_batch_destroy");
+    return SU2_OK;
+}
+
+su2_status su2_batch_generate(su2_batch *b, int nsweeps, int measure_every, double *plaq, double *poly,
+                              su2_stats *stats)
+{
+    if (!b || nsweeps < 0 || measure_every < 0) return SU2_E_INVAL;
+    DeviceGuard guard(b->device);
+    const int nmeas = measure_every > 0 ? nsweeps / measure_every : 0;
+    su2_status st = ensure_history(b, std::max(nmeas, 1));
+    if (st != SU2_OK) return st;
+    if ((st = clear_stats(b)) != SU2_OK) return st;
+    SU2_CUDA(cudaMemsetAsync(b->d_counters + 1, 0, sizeof(unsigned int), b->stream));
+    for (int s = 1; s <= nsweeps; ++s) {
+        const int measure = (measure_every > 0 && s % measure_every == 0) ? 1 : 0;
+        if ((st = launch_sweep(b, measure)) != SU2_OK) return st;
+    }
+    st = check_flags(b, stats, (uint64_t)nsweeps, nsweeps);
+    if (nmeas > 0 && (plaq || poly)) {
+        std::vector<double> h((size_t)nmeas * 2 * b->n);
+        SU2_CUDA(cudaMemcpyAsync(h.data(), b->d_history, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
+                                 b->stream));
+        SU2_CUDA(cudaStreamSynchronize(b->stream));
+        for (int m = 0; m < nmeas; ++m)
+            for (int l = 0; l < b->n; ++l) {
+                if (plaq) plaq[(size_t)m * b->n + l] = h[((size_t)m * 2 + 0) * b->n + l];
+                if (poly) poly[(size_t)m * b->n + l] = h[((size_t)m * 2 + 1) * b->n + l];
+            }
+    }
+    return st;
+}
+
+su2_status su2_batch_sweep(su2_batch *b, int nsweeps, su2_stats *stats)
+{
+    return su2_batch_generate(b, nsweeps, 0, nullptr, nullptr, stats);
+}
+
+su2_status su2_batch_measure(su2_batch *b, double *plaq, double *poly)
+{
+    if (!b || (!plaq && !poly)) return SU2_E_INVAL;
+    DeviceGuard guard(b->device);
+    su2_status st = ensure_history(b, 1);
+    if (st != SU2_OK) return st;
+    SU2_CUDA(cudaMemsetAsync(b->d_counters + 1, 0, sizeof(unsigned int), b->stream));
+    SU2_CUDA(enqueue_launch(b, 0, 1));
+    std::vector<double> h(2 * (size_t)b->n);
+    SU2_CUDA(cudaMemcpyAsync(h.data(), b->d_history, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, b->stream));
+    BarrierState bar;
+    SU2_CUDA(cudaMemcpyAsync(&bar, b->d_bar, sizeof bar, cudaMemcpyDeviceToHost, b->stream));
+    SU2_CUDA(cudaStreamSynchronize(b->stream));
+    if (bar.error & 1u) {
+        set_last_error("batch measurement: a grid barrier wait timed out");
+        return SU2_E_DEVICE_TIMEOUT;
+    }
+    for (int l = 0; l < b->n; ++l) {
+        if (plaq) plaq[l] = h[l];
+        if (poly) poly[l] = h[b->n + l];
+    }
+    return SU2_OK;
+}
+
+su2_status su2_batch_plaquette(su2_batch *b, double *out_n) { return su2_batch_measure(b, out_n, nullptr); }
+
+su2_status su2_batch_polyakov(su2_batch *b, double *out_n) { return su2_batch_measure(b, nullptr, out_n); }
+
+su2_status su2_batch_get_links(su2_batch *b, int i, float *host)
+{
+    if (!b || !host || i < 0 || i >= b->n) return SU2_E_INVAL;
+    DeviceGuard guard(b->device);
+    const Geom &g = b->geom[i];
+    const size_t need = sizeof(float4) * 8 * (size_t)g.vh;
+    if (!b->staging || b->staging_bytes < need) {
+        device_free(b->staging, b->staging_bytes, b->device, b->stream);
+        size_t most = 0;
+        for (const Geom &x : b->geom) most = std::max(most, sizeof(float4) * 8 * (size_t)x.vh);
+        b->staging = device_alloc(most, b->device, b->stream);
+        b->staging_bytes = b->staging ? most : 0;
+        if (!b->staging) return SU2_E_NOMEM;
+    }
+    SU2_CUDA(convert_links(b->links + b->link_offset[i], (float4 *)b->staging, g, true, b->stream));
+    SU2_CUDA(cudaMemcpyAsync(host, b->staging, need, cudaMemcpyDeviceToHost, b->stream));
+    SU2_CUDA(cudaStreamSynchronize(b->stream));
+    return SU2_OK;
+}
+
+su2_status su2_batch_info(su2_batch *b, int *n, uint32_t *sweep, int *queue_depth, int *grid, int *graphs)
+{
+    if (!b) return SU2_E_INVAL;
+    if (n) *n = b->n;
+    if (sweep) *sweep = b->sweep;
+    if (queue_depth) *queue_depth = b->R;
+    if (grid) *grid = b->grid;
+    if (graphs) *graphs = (b->use_graph && b->stream) ? 1 : 0;
+    return SU2_OK;
+}
+
+su2_status su2_batch_set_config(su2_batch *b, int queue_depth, int grid)
+{
+    if (!b || (queue_depth != 2 && queue_depth != 4 && queue_depth != 8)) return SU2_E_INVAL;
+    const int most = b->max_grid[r_index(queue_depth)];
+    if (grid <= 0 || grid > most) grid = most;
+    DeviceGuard guard(b->device);
+    return set_depth(b, queue_depth, grid);
+}
+
+// Times each candidate (queue depth 2/4/8 x full or half of the co-resident
+// grid) over `sweeps` sweeps of the batch, then restores the links and the
+// sweep counter, and keeps the fastest.
+su2_status su2_batch_autotune(su2_batch *b, int sweeps, int *queue_depth, int *grid)
+{
+    if (!b || sweeps < 1) return SU2_E_INVAL;
+    DeviceGuard guard(b->device);
+    const size_t bytes = sizeof(float4) * b->links_count;
+    void *saved = device_alloc(bytes, b->device, b->stream);
+    if (!saved) return SU2_E_NOMEM;
+    su2_status st = SU2_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float best = 1e30f;
+    int best_r = b->R, best_grid = b->grid;
+    const uint32_t sweep0 = b->sweep;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+        cudaMemcpyAsync(saved, b->links, bytes, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess)
+        st = cuda_fail(cudaGetLastError(), "su2_batch_autotune");
+    const int depths[3] = {2, 4, 8};
+    for (int i = 0; i < 3 && st == SU2_OK; ++i)
+        for (int half = 0; half < 2 && st == SU2_OK; ++half) {
+            const int R = depths[i];
+            const int grid = half ? std::max(1, b->max_grid[i] / 2) : b->max_grid[i];
+            if ((st = set_depth(b, R, grid)) != SU2_OK) break;
+            if ((st = launch_sweep(b, 0)) != SU2_OK) break;  // warm-up (and graph capture)
+            cudaEventRecord(e0, b->stream);
+            for (int s = 0; s < sweeps && st == SU2_OK; ++s) st = launch_sweep(b, 0);
+            cudaEventRecord(e1, b->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                st = cuda_fail(cudaGetLastError(), "su2_batch_autotune");
+                break;
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                best_r = R;
+                best_grid = grid;
+            }
+            // restore the configuration the candidates started from
+            if (cudaMemcpyAsync(b->links, saved, bytes, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess ||
+                cudaMemcpyAsync(b->d_counters, &sweep0, sizeof sweep0, cudaMemcpyHostToDevice, b->stream) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(b->stream) != cudaSuccess) {
+                st = cuda_fail(cudaGetLastError(), "su2_batch_autotune");
+                break;
+            }
+        }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    device_free(saved, bytes, b->device, b->stream);
+    cudaStreamSynchronize(b->stream);
+    b->sweep = sweep0;
+    if (st == SU2_OK) st = set_depth(b, best_r, best_grid);
+    if (st == SU2_OK) st = clear_stats(b);
+    if (queue_depth) *queue_depth = b->R;
+    if (grid) *grid = b->grid;
+    return st;
+}
+
+su2_status su2_selftest_barrier_timeout(int blocks, uint64_t timeout_ns, unsigned int *timed_out)
+{
+    if (blocks < 1 || blocks > 1024 || !timed_out || timeout_ns > 5000000000ull) return SU2_E_INVAL;
+    int dev = 0;
+    SU2_CUDA(cudaGetDevice(&dev));
+    const size_t bytes = 256 + sizeof(unsigned int);
+    char *buf = (char *)device_alloc(bytes, dev, nullptr);
+    if (!buf) return SU2_E_NOMEM;
+    su2_status st = SU2_OK;
+    BarrierState *bar = (BarrierState *)buf;
+    unsigned int *count = (unsigned int *)(buf + 256);
+    if (cudaMemsetAsync(buf, 0, bytes, nullptr) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "memset");
+    if (st == SU2_OK) {
+        // one more arrival is expected than there are blocks: nothing completes the barrier
+        barrier_timeout_kernel<<<blocks, 32>>>(bar, (unsigned int)blocks + 1u, timeout_ns, count);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpy(timed_out, count, sizeof(unsigned int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) st = cuda_fail(e, "barrier self-test");
+    }
+    device_free(buf, bytes, dev, nullptr);
+    cudaStreamSynchronize(nullptr);
+    return st;
+}
+
+}  // extern "C"

@@ -149,6 +149,27 @@ __global__ void reunitarize_kernel(float4 *__restrict__ links, int64_t n)
     }
 }
 
+cudaError_t start_links(float4 *links, const Geom &g, bool hot, uint64_t seed, unsigned int *flags,
+                        cudaStream_t stream)
+{
+    const int64_t n = 8 * (int64_t)g.vh;
+    if (hot)
+        hot_start_kernel<<<grid_for(n, 256), 256, 0, stream>>>(links, g, make_round_keys(seed), flags);
+    else
+        cold_start_kernel<<<grid_for(n, 256), 256, 0, stream>>>(links, n);
+    return cudaGetLastError();
+}
+
+cudaError_t convert_links(float4 *eo_links, float4 *lex_links, const Geom &g, bool to_lex, cudaStream_t stream)
+{
+    const int64_t vol = 2 * (int64_t)g.vh;
+    if (to_lex)
+        convert_kernel<true><<<grid_for(vol, 256), 256, 0, stream>>>(eo_links, lex_links, g);
+    else
+        convert_kernel<false><<<grid_for(vol, 256), 256, 0, stream>>>(eo_links, lex_links, g);
+    return cudaGetLastError();
+}
+
 su2_status launch_cold_start(su2_lattice *lat)
 {
     const int64_t n = 8 * (int64_t)lat->vh;

@@ -76,4 +76,21 @@ __device__ __forceinline__ void finish_reduction(double block_total, double *__r
     }
 }
 
+// (1/2) Tr of U_3(x,0) U_3(x,1) ... U_3(x,Nt-1), multiplied left to right,
+// for spatial site xs (lexicographic in x, y, z).
+__device__ __forceinline__ float site_polyakov(const float4 *__restrict__ L, const Geom &g, int xs)
+{
+    const int rest = xs / g.ns;
+    const int x = xs - rest * g.ns;
+    const int y = rest % g.ns;
+    const int z = rest / g.ns;
+    const int p0 = (x + y + z) & 1;
+    float4 p = __ldg(L + link_index(g, 3, p0, xs >> 1));
+    for (int t = 1; t < g.nt; ++t) {
+        const int64_t lex = (int64_t)t * g.vs + xs;
+        p = qmul(p, __ldg(L + link_index(g, 3, (p0 + t) & 1, (int)(lex >> 1))));
+    }
+    return p.x;
+}
+
 }  // namespace su2

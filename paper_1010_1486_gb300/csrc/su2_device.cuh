@@ -51,6 +51,23 @@ __device__ __forceinline__ uint4 philox_rk(uint4 c, const RoundKeys &rk)
     return c;
 }
 
+// The same generator with the key schedule computed on the fly (for kernels
+// whose key varies per work item, e.g. one seed per lattice of a batch).
+__device__ __forceinline__ uint4 philox_key(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
 // Uniform in (0, 1]: the top 24 bits plus one, times 2^-24 (exact).
 __device__ __forceinline__ float uniform01(uint32_t w)
 {

@@ -80,23 +80,25 @@ struct DeviceGuard {
     }
 };
 
-inline Geom geom_of(const su2_lattice *lat)
+inline Geom make_geom(int ns, int nt)
 {
     Geom g;
-    g.ns = lat->ns;
-    g.nt = lat->nt;
-    g.vh = lat->vh;
-    g.vs = lat->ns * lat->ns * lat->ns;
-    g.div_ns = make_fastdiv((uint32_t)lat->ns);
+    g.ns = ns;
+    g.nt = nt;
+    g.vh = (int)((int64_t)ns * ns * ns * nt / 2);
+    g.vs = ns * ns * ns;
+    g.div_ns = make_fastdiv((uint32_t)ns);
     int stride = 1;
     for (int mu = 0; mu < 4; ++mu) {
-        g.ext[mu] = mu == 3 ? lat->nt : lat->ns;
+        g.ext[mu] = mu == 3 ? nt : ns;
         g.stride[mu] = stride;
         g.wrap[mu] = (g.ext[mu] - 1) * stride;
         stride *= g.ext[mu];
     }
     return g;
 }
+
+inline Geom geom_of(const su2_lattice *lat) { return make_geom(lat->ns, lat->nt); }
 
 inline int grid_for(int64_t n, int threads, int64_t cap = 152 * 64)
 {
@@ -109,6 +111,12 @@ inline int grid_for(int64_t n, int threads, int64_t cap = 152 * 64)
 // Allocation through the installed hook (or cudaMallocAsync).
 void *device_alloc(size_t bytes, int device, cudaStream_t stream);
 void device_free(void *ptr, size_t bytes, int device, cudaStream_t stream);
+
+// Start configurations and layout conversion of one lattice's links
+// (8 vh float4 at `links`), enqueued on `stream`.
+cudaError_t start_links(float4 *links, const Geom &g, bool hot, uint64_t seed, unsigned int *flags,
+                        cudaStream_t stream);
+cudaError_t convert_links(float4 *eo_links, float4 *lex_links, const Geom &g, bool to_lex, cudaStream_t stream);
 
 // Launchers (each enqueues on lat->stream and returns a status of the launch).
 su2_status launch_cold_start(su2_lattice *lat);

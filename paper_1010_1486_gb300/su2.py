@@ -80,6 +80,18 @@ _SIGS = {
     "su2_selftest_philox": [_P, _P, ctypes.c_size_t],
     "su2_selftest_math": [_i32, _P, _P, _P, ctypes.c_size_t],
     "su2_plaquette_noalloc": [_P, _i32, _i32, _P, _P],
+    "su2_batch_create": [_i32, _P, _P, _P, _P, _i32, _P, ctypes.POINTER(_P)],
+    "su2_batch_destroy": [_P],
+    "su2_batch_sweep": [_P, _i32, ctypes.POINTER(su2_stats)],
+    "su2_batch_generate": [_P, _i32, _i32, _P, _P, ctypes.POINTER(su2_stats)],
+    "su2_batch_plaquette": [_P, _P],
+    "su2_batch_polyakov": [_P, _P],
+    "su2_batch_get_links": [_P, _i32, _P],
+    "su2_batch_set_config": [_P, _i32, _i32],
+    "su2_batch_autotune": [_P, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)],
+    "su2_batch_info": [_P, ctypes.POINTER(_i32), ctypes.POINTER(_u32), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                       ctypes.POINTER(_i32)],
+    "su2_selftest_barrier_timeout": [_i32, _u64, ctypes.POINTER(_u32)],
 }
 for _name, _args in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -269,6 +281,81 @@ def su2_plaquette_noalloc(links_ptr: int, ns: int, nt: int, out_ptr: int, stream
     For callers that cannot allocate device memory at this point; see
     include/su2.h for the scratch it shares between calls and its size limit."""
     _check(_lib.su2_plaquette_noalloc(links_ptr, ns, nt, out_ptr, _stream_handle(stream)), "su2_plaquette_noalloc")
+
+
+# ------------------------------------------------------------------ batches
+def su2_batch_create(ns, nt, beta, seed, start: int = SU2_COLD, stream=None) -> int:
+    n = len(ns)
+    a_ns = np.ascontiguousarray(ns, dtype=np.int32)
+    a_nt = np.ascontiguousarray(nt, dtype=np.int32)
+    a_beta = np.ascontiguousarray(beta, dtype=np.float64)
+    a_seed = np.ascontiguousarray(seed, dtype=np.uint64)
+    h = _P()
+    _check(_lib.su2_batch_create(n, _host_ptr(a_ns), _host_ptr(a_nt), _host_ptr(a_beta), _host_ptr(a_seed),
+                                 int(start), _stream_handle(stream), ctypes.byref(h)), "su2_batch_create")
+    return h.value
+
+
+def su2_batch_destroy(b: int) -> None:
+    _check(_lib.su2_batch_destroy(b), "su2_batch_destroy")
+
+
+def su2_batch_sweep(b: int, nsweeps: int = 1) -> dict:
+    st = su2_stats()
+    _check(_lib.su2_batch_sweep(b, nsweeps, ctypes.byref(st)), "su2_batch_sweep")
+    return st.as_dict()
+
+
+def su2_batch_generate(b: int, n: int, nsweeps: int, measure_every: int = 1):
+    """Returns (plaquettes [nmeas, n], Polyakov loops [nmeas, n], stats)."""
+    nmeas = nsweeps // measure_every if measure_every > 0 else 0
+    plaq = np.zeros((max(nmeas, 1), n), dtype=np.float64)
+    poly = np.zeros((max(nmeas, 1), n), dtype=np.float64)
+    st = su2_stats()
+    _check(_lib.su2_batch_generate(b, nsweeps, measure_every, _host_ptr(plaq), _host_ptr(poly), ctypes.byref(st)),
+           "su2_batch_generate")
+    return plaq[:nmeas], poly[:nmeas], st.as_dict()
+
+
+def su2_batch_plaquette(b: int, n: int) -> np.ndarray:
+    out = np.zeros(n, dtype=np.float64)
+    _check(_lib.su2_batch_plaquette(b, _host_ptr(out)), "su2_batch_plaquette")
+    return out
+
+
+def su2_batch_polyakov(b: int, n: int) -> np.ndarray:
+    out = np.zeros(n, dtype=np.float64)
+    _check(_lib.su2_batch_polyakov(b, _host_ptr(out)), "su2_batch_polyakov")
+    return out
+
+
+def su2_batch_get_links(b: int, i: int, ns: int, nt: int) -> np.ndarray:
+    out = np.empty((ns ** 3 * nt, 4, 4), dtype=np.float32)
+    _check(_lib.su2_batch_get_links(b, i, _host_ptr(out)), "su2_batch_get_links")
+    return out
+
+
+def su2_batch_set_config(b: int, queue_depth: int, grid: int = 0) -> None:
+    _check(_lib.su2_batch_set_config(b, queue_depth, grid), "su2_batch_set_config")
+
+
+def su2_batch_autotune(b: int, sweeps: int = 3):
+    r, g = _i32(), _i32()
+    _check(_lib.su2_batch_autotune(b, sweeps, ctypes.byref(r), ctypes.byref(g)), "su2_batch_autotune")
+    return r.value, g.value
+
+
+def su2_batch_info(b: int) -> dict:
+    n, sw, r, g, gr = _i32(), _u32(), _i32(), _i32(), _i32()
+    _check(_lib.su2_batch_info(b, ctypes.byref(n), ctypes.byref(sw), ctypes.byref(r), ctypes.byref(g),
+                               ctypes.byref(gr)), "su2_batch_info")
+    return {"n": n.value, "sweep": sw.value, "queue_depth": r.value, "grid": g.value, "graphs": bool(gr.value)}
+
+
+def su2_selftest_barrier_timeout(blocks: int, timeout_ns: int) -> int:
+    out = _u32()
+    _check(_lib.su2_selftest_barrier_timeout(blocks, timeout_ns, ctypes.byref(out)), "su2_selftest_barrier_timeout")
+    return out.value
 
 
 def su2_status_str(status: int) -> str:
