@@ -83,6 +83,22 @@ def _load():
             "orc_max_threads": (i32, []),
             "orc_creutz_a0_v": (None, [f32, u64, u32, u32, i64, P, P]),
             "orc_heatbath_link_v": (None, [f32, P, u64, u32, u32, i32, i32, i64, P, P]),
+            "orc_mlp_forward": (None, [P, f32, P]),
+            "orc_spline_params": (None, [P, P]),
+            "orc_spline_forward": (f32, [P, f32, P]),
+            "orc_spline_inverse": (f32, [P, f32, P]),
+            "orc_spline_forward_v": (None, [P, P, P, P, i64]),
+            "orc_spline_inverse_v": (None, [P, P, P, P, i64]),
+            "orc_proposal_table": (None, [P, f32, f32, i32, P]),
+            "orc_table_params": (None, [P, i32, f32, f32, f32, P]),
+            "orc_learned_link": (i32, [P, i32, f32, f32, f32, f32, f32, P, P, u64, u32, u32, i32, i32, P]),
+            "orc_learned_phase": (i64, [i32, i32, f64, u64, u32, i32, i32, P, P, i32, f32, f32, f32, f32]),
+            "orc_learned_sweep": (i64, [i32, i32, f64, u64, u32, P, P, i32, f32, f32, f32, f32, P]),
+            "orc_learned_chain": (i64, [P, i32, f32, f32, f32, f32, f32, P, P, u64, i64, P]),
+            "orc_collect_pairs": (i64, [i32, i32, f64, u64, u32, i32, i32, i32, P, P]),
+            "orc_nll_grad": (f64, [P, P, i64, P]),
+            "orc_nll_outputs": (f64, [P, f64, P]),
+            "orc_spline_d": (None, [P, f64, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -250,3 +266,101 @@ def reunitarize(ns: int, nt: int, links: np.ndarray) -> None:
 
 def max_threads() -> int:
     return _load().orc_max_threads()
+
+
+# ------------------------------------------------------- learned proposal
+N_WEIGHTS = 1947      # 1945 trainable + input mean and scale
+N_TRAIN = 1945
+N_PARAMS = 27         # spline knots x0..x8, y0..y8, derivatives d0..d8
+
+
+def mlp_forward(w, s: float) -> np.ndarray:
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    o = np.zeros(25, dtype=np.float32)
+    _load().orc_mlp_forward(_ptr(w), s, _ptr(o))
+    return o
+
+
+def spline_params(o) -> np.ndarray:
+    o = np.ascontiguousarray(o, dtype=np.float32)
+    p = np.zeros(N_PARAMS, dtype=np.float32)
+    _load().orc_spline_params(_ptr(o), _ptr(p))
+    return p
+
+
+def spline_forward(p, z):
+    p = np.ascontiguousarray(p, dtype=np.float32)
+    z = np.ascontiguousarray(z, dtype=np.float32)
+    a, fp = np.empty_like(z), np.empty_like(z)
+    _load().orc_spline_forward_v(_ptr(p), _ptr(z), _ptr(a), _ptr(fp), z.size)
+    return a, fp
+
+
+def spline_inverse(p, a):
+    p = np.ascontiguousarray(p, dtype=np.float32)
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    z, fp = np.empty_like(a), np.empty_like(a)
+    _load().orc_spline_inverse_v(_ptr(p), _ptr(a), _ptr(z), _ptr(fp), a.size)
+    return z, fp
+
+
+def proposal_table(w, s_lo: float, s_hi: float, G: int = 256) -> np.ndarray:
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    t = np.zeros((G, N_PARAMS), dtype=np.float32)
+    _load().orc_proposal_table(_ptr(w), s_lo, s_hi, G, _ptr(t))
+    return t
+
+
+def table_params(table, s_lo, s_hi, s) -> np.ndarray:
+    table = np.ascontiguousarray(table, dtype=np.float32)
+    p = np.zeros(N_PARAMS, dtype=np.float32)
+    _load().orc_table_params(_ptr(table), table.shape[0], s_lo, s_hi, s, _ptr(p))
+    return p
+
+
+def learned_sweep(ns, nt, beta, seed, sweep, links, table, s_lo, s_hi, mean, scale) -> np.ndarray:
+    table = np.ascontiguousarray(table, dtype=np.float32)
+    acc = np.zeros(8, dtype=np.int64)
+    _load().orc_learned_sweep(ns, nt, beta, seed, sweep, _ptr(links), _ptr(table), table.shape[0], s_lo, s_hi, mean,
+                              scale, _ptr(acc))
+    return acc
+
+
+def learned_chain(table, s_lo, s_hi, mean, scale, beta, v, old0, seed, n):
+    table = np.ascontiguousarray(table, dtype=np.float32)
+    v = np.ascontiguousarray(v, dtype=np.float32)
+    old0 = np.ascontiguousarray(old0, dtype=np.float32)
+    a0 = np.zeros(n, dtype=np.float32)
+    acc = _load().orc_learned_chain(_ptr(table), table.shape[0], s_lo, s_hi, mean, scale, beta, _ptr(v), _ptr(old0),
+                                    seed, n, _ptr(a0))
+    return a0, acc
+
+
+def collect_pairs(ns, nt, beta, seed, sweep, mu, parity, stride, links) -> np.ndarray:
+    n_max = ns ** 3 * nt // 2 // stride + 1
+    pairs = np.zeros((n_max, 2), dtype=np.float32)
+    n = _load().orc_collect_pairs(ns, nt, beta, seed, sweep, mu, parity, stride, _ptr(links), _ptr(pairs))
+    return pairs[:n]
+
+
+def nll_grad(w, pairs, want_grad=True):
+    """binary64 mean -log q(a0 | beta k) and its gradient (1945 weights)."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    pairs = np.ascontiguousarray(pairs, dtype=np.float32)
+    g = np.zeros(N_TRAIN, dtype=np.float64) if want_grad else None
+    v = _load().orc_nll_grad(_ptr(w), _ptr(pairs), pairs.shape[0], _ptr(g) if want_grad else None)
+    return v, g
+
+
+def nll_outputs(o, a, want_grad=True):
+    o = np.ascontiguousarray(o, dtype=np.float64)
+    g = np.zeros(25, dtype=np.float64) if want_grad else None
+    v = _load().orc_nll_outputs(_ptr(o), a, _ptr(g) if want_grad else None)
+    return v, g
+
+
+def spline_d(o, z):
+    o = np.ascontiguousarray(o, dtype=np.float64)
+    a, fp, zi = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _load().orc_spline_d(_ptr(o), z, ctypes.byref(a), ctypes.byref(fp), ctypes.byref(zi))
+    return a.value, fp.value, zi.value
