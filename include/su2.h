@@ -229,6 +229,11 @@ su2_status su2_selftest_barrier_timeout(int blocks, uint64_t timeout_ns, unsigne
  * give wrong results -- order them. */
 su2_status su2_plaquette_noalloc(const void *links, int ns, int nt, double *out, void *cuda_stream);
 
+/* Self-test of the tensor-core path used by training: D (128 x 32, FP32,
+ * row-major) = A (128 x K, BF16 bits, row-major) * B (32 x K, BF16 bits)^T,
+ * K = 16 or 32, computed by tcgen05.mma with the accumulator in tensor memory. */
+su2_status su2_selftest_mma(const uint16_t *A, const uint16_t *B, int K, float *D);
+
 /* Human-readable status and the last CUDA error text of this thread. */
 const char *su2_status_str(su2_status s);
 const char *su2_last_error(void);

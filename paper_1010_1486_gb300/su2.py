@@ -92,6 +92,7 @@ _SIGS = {
     "su2_batch_info": [_P, ctypes.POINTER(_i32), ctypes.POINTER(_u32), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
                        ctypes.POINTER(_i32)],
     "su2_selftest_barrier_timeout": [_i32, _u64, ctypes.POINTER(_u32)],
+    "su2_selftest_mma": [_P, _P, _i32, _P],
 }
 for _name, _args in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -356,6 +357,16 @@ def su2_selftest_barrier_timeout(blocks: int, timeout_ns: int) -> int:
     out = _u32()
     _check(_lib.su2_selftest_barrier_timeout(blocks, timeout_ns, ctypes.byref(out)), "su2_selftest_barrier_timeout")
     return out.value
+
+
+def su2_selftest_mma(a_bf16: np.ndarray, b_bf16: np.ndarray) -> np.ndarray:
+    """D = A B^T on the tensor cores; A (128, K) and B (32, K) as uint16 BF16 bits."""
+    a = np.ascontiguousarray(a_bf16, dtype=np.uint16)
+    b = np.ascontiguousarray(b_bf16, dtype=np.uint16)
+    k = a.shape[1]
+    d = np.zeros((128, 32), dtype=np.float32)
+    _check(_lib.su2_selftest_mma(_host_ptr(a), _host_ptr(b), k, _host_ptr(d)), "su2_selftest_mma")
+    return d
 
 
 def su2_status_str(status: int) -> str:
