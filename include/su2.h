@@ -160,6 +160,48 @@ su2_status su2_selftest_philox(const uint32_t *ck, uint32_t *out, size_t n);
 su2_status su2_selftest_math(int which, const float *x, float *y, float *y2, size_t n);
 
 /* ---------------------------------------------------------------------------
+ * Learned proposal (not in the paper).  A small network of beta k (MLP
+ * 1 -> 32 -> 32 -> 25, ReLU) sets an 8-bin monotone rational-quadratic spline
+ * (Durkan et al., NeurIPS 2019) that proposes a0 for the heat-bath law of
+ * Sec. 2; an independence-Metropolis step accepts or rejects the proposed link
+ * against that law, so the chain stays exact for any weights.  Weights as
+ * float[1947]: W1[32], b1[32], W2[32][32], b2[32], W3[25][32], b3[25], input
+ * mean, input scale (network input (beta k - mean) * scale).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    uint64_t link_updates;     /* 4 V per sweep, learned or plain            */
+    uint64_t accepted[8];      /* accepted learned proposals per phase 2 mu + parity */
+    uint64_t plain_trials[8];  /* Creutz trials of the fallback sweeps       */
+    uint32_t learned_sweeps;   /* sweeps done with the learned proposal      */
+    uint32_t plain_sweeps;     /* fallback sweeps done with the heat bath    */
+} su2_learned_stats;
+
+/* Installs the proposal: the network is evaluated (binary32, on the device)
+ * at grid_points (2..400) equally spaced inputs s in [s_lo, s_hi]; a link's
+ * spline parameters are interpolated linearly between the two grid points
+ * around its clamped input.  Synchronous. */
+su2_status su2_set_proposal(su2_lattice *lat, const float *weights, int n, double s_lo, double s_hi, int grid_points);
+
+/* The grid_points x 27 spline parameters (knots x0..x8, y0..y8, derivatives
+ * d0..d8) of the installed proposal. */
+su2_status su2_get_proposal_table(su2_lattice *lat, float *host);
+
+/* nsweeps sweeps with the learned Metropolis step; a sweep whose acceptance
+ * is below min_acceptance (e.g. 0.7) is followed by one plain heat-bath sweep,
+ * after which the learned step resumes.  Measurements as su2_generate.
+ * Synchronises once at the end. */
+su2_status su2_learned_generate(su2_lattice *lat, int nsweeps, int measure_every, double min_acceptance,
+                                double *plaq, double *poly, su2_learned_stats *stats);
+
+/* Training pairs (beta k, a0), float2 each, for the links U_mu(x) of the given
+ * parity whose even/odd index is a multiple of stride: a0 is a fresh Creutz
+ * draw (own counter stream) given the current staple, so the pairs have the
+ * exact heat-bath law and the lattice is not changed.  dev_pairs: device
+ * buffer of cap pairs; *n receives ceil((V/2) / stride).  Asynchronous. */
+su2_status su2_collect_pairs(su2_lattice *lat, int mu, int parity, int stride, float *dev_pairs, size_t cap,
+                             size_t *n);
+
+/* ---------------------------------------------------------------------------
  * Batches: many independent lattices (own Ns^3 x Nt, beta and seed each) swept
  * together.  Each lattice follows exactly the chain of su2_create +
  * su2_heatbath_sweep with its own arguments.  One sweep of the whole batch is

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "observables.cuh"
+#include "staple.cuh"
 #include "su2_device.cuh"
 #include "su2_internal.h"
 
@@ -113,31 +114,6 @@ __device__ __forceinline__ int find_owner(const int *__restrict__ prefix, int n,
             hi = mid - 1;
     }
     return lo;
-}
-
-// Staple of U_mu(x) (Sec. 2), nu ascending, forward then backward term.
-template <int MU>
-__device__ __forceinline__ float4 staple_at(const float4 *__restrict__ L, const Geom &g, const Coord &x, int parity)
-{
-    const int op = parity ^ 1;
-    const int lex_p = lex_fwd(g, x.lex, x.c[MU], MU);
-    float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-#pragma unroll
-    for (int nu = 0; nu < 4; ++nu) {
-        if (nu == MU) continue;
-        const int e_xn = lex_fwd(g, x.lex, x.c[nu], nu) >> 1;
-        const int e_xm = lex_bwd(g, x.lex, x.c[nu], nu) >> 1;
-        const int e_xpm = lex_bwd(g, lex_p, x.c[nu], nu) >> 1;
-        const float4 a = __ldg(L + link_index(g, nu, op, lex_p >> 1));
-        const float4 b = __ldg(L + link_index(g, MU, op, e_xn));
-        const float4 c = __ldg(L + link_index(g, nu, parity, x.lex >> 1));
-        const float4 d = __ldg(L + link_index(g, nu, parity, e_xpm));
-        const float4 e = __ldg(L + link_index(g, MU, op, e_xm));
-        const float4 f = __ldg(L + link_index(g, nu, op, e_xm));
-        v = qadd(v, qmul(qmul(a, qdag(b)), qdag(c)));
-        v = qadd(v, qmul(qmul(qdag(d), qdag(e)), f));
-    }
-    return v;
 }
 
 // One phase (MU, parity) over every lattice: chunks of 32 R consecutive

@@ -28,6 +28,7 @@ struct HbParams {
     uint32_t sweep;
     unsigned long long *trial_slots;
     unsigned int *flags;
+    const unsigned int *gate;  // if non-NULL and *gate == 1 the phase is left to the learned kernel
 };
 
 constexpr int kHbWarps = kHbThreads / 32;
@@ -87,6 +88,7 @@ __device__ __forceinline__ float4 add_nu_terms(float4 v, const NuLinks &n)
 template <int MU, int R>
 __global__ void __launch_bounds__(kHbThreads) hb_phase_kernel(const HbParams p)
 {
+    if (p.gate != nullptr && *(volatile const unsigned int *)p.gate == 1u) return;
     constexpr int Q = 32 * R;
     __shared__ float4 s_ut[kHbWarps][Q];
     __shared__ float s_bk[kHbWarps][Q];  // beta k; after acceptance a0 (NaN: trial cap hit)
@@ -272,9 +274,10 @@ static cudaError_t launch_hb(const HbParams &p, int device, cudaStream_t stream)
     return cudaGetLastError();
 }
 
-su2_status launch_hb_phase(su2_lattice *lat, int mu, int parity, uint32_t sweep)
+su2_status launch_hb_phase(su2_lattice *lat, int mu, int parity, uint32_t sweep, const unsigned int *gate)
 {
     HbParams p;
+    p.gate = gate;
     p.links = lat->links;
     p.g = geom_of(lat);
     p.rk = make_round_keys(lat->seed);

@@ -1,0 +1,340 @@
+// learned.cu -- the learned a0 proposal on the lattice: the proposal table
+// (the network evaluated in binary32 registers at grid points of beta k),
+// the independence-Metropolis phase kernel, the plain heat bath as fallback
+// (a sweep whose acceptance falls below a threshold is followed by a plain
+// sweep), and the collection of (beta k, a0) training pairs from fresh
+// Creutz draws (Sec. 2 sampler) on the current configuration.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "learned.cuh"
+#include "observables.cuh"
+#include "staple.cuh"
+#include "su2_device.cuh"
+#include "su2_internal.h"
+
+namespace su2 {
+
+constexpr int kLearnThreads = 256;
+constexpr int kAcceptSlots = 64;
+
+__global__ void proposal_table_kernel(const float *__restrict__ w, float s_lo, float s_hi, int G,
+                                      float *__restrict__ table)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= G) return;
+    const float ds = __fdiv_rn(__fsub_rn(s_hi, s_lo), (float)(G - 1));
+    float o[learned::kOut];
+    learned::mlp_forward(w, __fmaf_rn((float)j, ds, s_lo), o);
+    learned::spline_params(o, table + j * learned::kParams);
+}
+
+struct LearnedParams {
+    float4 *links;
+    Geom g;
+    RoundKeys rk;
+    int parity;
+    float beta;
+    uint32_t sweep;
+    const float *table;
+    int G;
+    float s_lo, s_hi, mean, scale;
+    const unsigned int *gate;          // runs only while *gate == 1
+    unsigned long long *acc_slots;     // [8][64]: accepted links per phase (call total)
+    unsigned long long *sweep_slots;   // [64]: accepted links of this sweep
+};
+
+__device__ __forceinline__ unsigned int block_sum_u32(unsigned int v)
+{
+    __shared__ unsigned int warp_sums[32];
+    const unsigned int lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    v = __reduce_add_sync(0xffffffffu, v);
+    if (lane == 0) warp_sums[warp] = v;
+    __syncthreads();
+    unsigned int total = 0;
+    if (warp == 0) {
+        total = lane < (blockDim.x >> 5) ? warp_sums[lane] : 0u;
+        total = __reduce_add_sync(0xffffffffu, total);
+    }
+    return total;
+}
+
+template <int MU>
+__global__ void __launch_bounds__(kLearnThreads) learned_phase_kernel(const LearnedParams p)
+{
+    extern __shared__ float s_table[];
+    if (*(volatile const unsigned int *)p.gate != 1u) return;
+    const int n_tab = p.G * learned::kParams;
+    for (int i = threadIdx.x; i < n_tab; i += blockDim.x) s_table[i] = p.table[i];
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned int acc = 0;
+    if (i < p.g.vh) {
+        const Coord x = eo_to_coord(p.g, i, p.parity);
+        const float4 v = staple_at<MU>(p.links, p.g, x, p.parity);
+        const size_t li = link_index(p.g, MU, p.parity, i);
+        const float4 old = p.links[li];
+        const uint4 w = philox_rk(make_uint4((uint32_t)i, p.sweep, stream_word(kLearned, (uint32_t)p.parity, MU), 0u),
+                                  p.rk);
+        const learned::Proposal pr{s_table, p.G, p.s_lo, p.s_hi, p.mean, p.scale};
+        float4 out;
+        acc = (unsigned int)learned::learned_link(pr, p.beta, v, old, w, out);
+        if (acc) p.links[li] = out;
+    }
+    const unsigned int total = block_sum_u32(acc);
+    if (threadIdx.x == 0 && total) {
+        atomicAdd(&p.acc_slots[(2 * MU + p.parity) * kAcceptSlots + (blockIdx.x & (kAcceptSlots - 1))],
+                  (unsigned long long)total);
+        atomicAdd(&p.sweep_slots[blockIdx.x & (kAcceptSlots - 1)], (unsigned long long)total);
+    }
+}
+
+// End of a sweep: after a learned sweep whose acceptance is below the
+// threshold, the next sweep is plain; after a plain sweep, learned again.
+__global__ void learned_decide_kernel(unsigned int *ctl, unsigned long long *sweep_slots, double links,
+                                      double min_acceptance)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    unsigned long long acc = 0;
+    for (int j = 0; j < kAcceptSlots; ++j) {
+        acc += sweep_slots[j];
+        sweep_slots[j] = 0ull;
+    }
+    if (ctl[0] == 1u) {
+        ctl[2] += 1u;
+        ctl[0] = ((double)acc < min_acceptance * links) ? 0u : 1u;
+    } else {
+        ctl[1] += 1u;
+        ctl[0] = 1u;
+    }
+}
+
+// One (beta k, a0) pair per link U_mu(x) of parity p with even/odd index a
+// multiple of `stride`: a0 is a Creutz draw on the collection stream (trial t
+// uses words 2(t&1), 2(t&1)+1 of block t>>1), so the pair has the exact
+// conditional law without touching the chain.
+template <int MU>
+__global__ void __launch_bounds__(kLearnThreads) collect_kernel(const float4 *__restrict__ links, Geom g, int parity,
+                                                                 RoundKeys rk, float beta, uint32_t sweep, int stride,
+                                                                 float2 *__restrict__ pairs, int n_pairs)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n_pairs) return;
+    const int eo = q * stride;
+    const Coord x = eo_to_coord(g, eo, parity);
+    const DrawSetup d = prepare_draw(staple_at<MU>(links, g, x, parity), beta);
+    const bool haar = d.bk < kHaarBelow;
+    const float ome = __fsub_rn(1.0f, d.e);
+    float a0 = 0.0f;
+    const uint32_t sw = stream_word(4u, (uint32_t)parity, MU);
+    for (int b = 0; b < kMaxTrials / 2; ++b) {
+        const uint4 w = philox_rk(make_uint4((uint32_t)eo, sweep, sw, (uint32_t)b), rk);
+        float cand;
+        if (creutz_trial(uniform01(w.x), uniform01(w.y), d.bk, d.e, ome, haar, cand)) {
+            a0 = cand;
+            break;
+        }
+        if (creutz_trial(uniform01(w.z), uniform01(w.w), d.bk, d.e, ome, haar, cand)) {
+            a0 = cand;
+            break;
+        }
+    }
+    pairs[q] = make_float2(d.bk, a0);
+}
+
+static su2_status launch_learned_phase(su2_lattice *lat, int mu, int parity)
+{
+    LearnedParams p;
+    p.links = lat->links;
+    p.g = geom_of(lat);
+    p.rk = make_round_keys(lat->seed);
+    p.parity = parity;
+    p.beta = (float)lat->beta;
+    p.sweep = lat->sweep;
+    p.table = lat->proposal;
+    p.G = lat->proposal_g;
+    p.s_lo = lat->prop_s_lo;
+    p.s_hi = lat->prop_s_hi;
+    p.mean = lat->prop_mean;
+    p.scale = lat->prop_scale;
+    p.gate = lat->learned_ctl;
+    p.acc_slots = lat->accept_slots;
+    p.sweep_slots = lat->accept_slots + 8 * kAcceptSlots;
+    const int grid = (p.g.vh + kLearnThreads - 1) / kLearnThreads;
+    const size_t smem = sizeof(float) * (size_t)p.G * learned::kParams;
+    switch (mu) {
+    case 0: learned_phase_kernel<0><<<grid, kLearnThreads, smem, lat->stream>>>(p); break;
+    case 1: learned_phase_kernel<1><<<grid, kLearnThreads, smem, lat->stream>>>(p); break;
+    case 2: learned_phase_kernel<2><<<grid, kLearnThreads, smem, lat->stream>>>(p); break;
+    default: learned_phase_kernel<3><<<grid, kLearnThreads, smem, lat->stream>>>(p); break;
+    }
+    SU2_CUDA(cudaGetLastError());
+    return SU2_OK;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace su2
+
+using namespace su2;
+
+extern "C" {
+
+su2_status su2_set_proposal(su2_lattice *lat, const float *weights, int n, double s_lo, double s_hi, int grid_points)
+{
+    if (!lat || !weights || n != learned::kWeights || grid_points < 2 || grid_points > 400 || !(s_hi > s_lo) ||
+        !std::isfinite(s_lo) || !std::isfinite(s_hi)) {
+        set_last_error("su2_set_proposal: 1947 weights, 2 <= grid_points <= 400, finite s_lo < s_hi");
+        return SU2_E_INVAL;
+    }
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(weights[i])) {
+            set_last_error("su2_set_proposal: non-finite weight");
+            return SU2_E_NUMERIC;
+        }
+    DeviceGuard guard(lat->device);
+    const size_t table_bytes = align256(sizeof(float) * learned::kParams * 400);
+    const size_t w_bytes = align256(sizeof(float) * learned::kWeights);
+    const size_t ctl_bytes = align256(sizeof(unsigned int) * 4);
+    const size_t slot_bytes = align256(sizeof(unsigned long long) * 9 * kAcceptSlots);
+    if (!lat->learned_block) {
+        lat->learned_bytes = table_bytes + w_bytes + ctl_bytes + slot_bytes;
+        lat->learned_block = device_alloc(lat->learned_bytes, lat->device, lat->stream);
+        if (!lat->learned_block) {
+            set_last_error("device allocation of the learned proposal failed");
+            return SU2_E_NOMEM;
+        }
+        char *q = (char *)lat->learned_block;
+        lat->proposal = (float *)q;
+        lat->learned_ctl = (unsigned int *)(q + table_bytes + w_bytes);
+        lat->accept_slots = (unsigned long long *)(q + table_bytes + w_bytes + ctl_bytes);
+        SU2_CUDA(cudaMemsetAsync(lat->learned_ctl, 0, ctl_bytes + slot_bytes, lat->stream));
+    }
+    float *d_w = (float *)((char *)lat->learned_block + table_bytes);
+    SU2_CUDA(cudaMemcpyAsync(d_w, weights, sizeof(float) * learned::kWeights, cudaMemcpyHostToDevice, lat->stream));
+    proposal_table_kernel<<<(grid_points + 63) / 64, 64, 0, lat->stream>>>(d_w, (float)s_lo, (float)s_hi, grid_points,
+                                                                         lat->proposal);
+    SU2_CUDA(cudaGetLastError());
+    SU2_CUDA(cudaStreamSynchronize(lat->stream));
+    lat->proposal_g = grid_points;
+    lat->prop_s_lo = (float)s_lo;
+    lat->prop_s_hi = (float)s_hi;
+    lat->prop_mean = weights[learned::kOffMean];
+    lat->prop_scale = weights[learned::kOffScale];
+    return SU2_OK;
+}
+
+su2_status su2_get_proposal_table(su2_lattice *lat, float *host)
+{
+    if (!lat || !host) return SU2_E_INVAL;
+    if (!lat->proposal_g) return SU2_E_STATE;
+    DeviceGuard guard(lat->device);
+    SU2_CUDA(cudaMemcpyAsync(host, lat->proposal, sizeof(float) * learned::kParams * lat->proposal_g,
+                             cudaMemcpyDeviceToHost, lat->stream));
+    SU2_CUDA(cudaStreamSynchronize(lat->stream));
+    return SU2_OK;
+}
+
+su2_status su2_learned_generate(su2_lattice *lat, int nsweeps, int measure_every, double min_acceptance,
+                                double *plaq, double *poly, su2_learned_stats *stats)
+{
+    if (!lat || nsweeps < 0 || measure_every < 0 || !(min_acceptance >= 0.0) || min_acceptance > 1.0)
+        return SU2_E_INVAL;
+    if (!lat->proposal_g) {
+        set_last_error("su2_learned_generate: no proposal set (su2_set_proposal)");
+        return SU2_E_STATE;
+    }
+    DeviceGuard guard(lat->device);
+    const int nmeas = measure_every > 0 ? nsweeps / measure_every : 0;
+    if (nmeas > 0) {
+        // reuse the history buffer of su2_generate
+        if (nmeas > lat->scratch.history_cap) {
+            device_free(lat->scratch.history, sizeof(double) * 2 * (size_t)lat->scratch.history_cap, lat->device,
+                        lat->stream);
+            lat->scratch.history = (double *)device_alloc(sizeof(double) * 2 * (size_t)nmeas, lat->device, lat->stream);
+            lat->scratch.history_cap = lat->scratch.history ? nmeas : 0;
+            if (!lat->scratch.history) return SU2_E_NOMEM;
+        }
+    }
+    su2_status st = launch_clear_counters(lat);
+    if (st != SU2_OK) return st;
+    const unsigned int ctl0[4] = {1u, 0u, 0u, 0u};
+    SU2_CUDA(cudaMemcpyAsync(lat->learned_ctl, ctl0, sizeof ctl0, cudaMemcpyHostToDevice, lat->stream));
+    SU2_CUDA(cudaMemsetAsync(lat->accept_slots, 0, sizeof(unsigned long long) * 9 * kAcceptSlots, lat->stream));
+    lat->events_used = 0;
+    const double links = 4.0 * (double)lat->vol;
+    int m = 0;
+    for (int s = 1; s <= nsweeps; ++s) {
+        for (int mu = 0; mu < 4; ++mu)
+            for (int parity = 0; parity < 2; ++parity) {
+                if ((st = launch_learned_phase(lat, mu, parity)) != SU2_OK) return st;
+                if ((st = launch_hb_phase(lat, mu, parity, lat->sweep, lat->learned_ctl)) != SU2_OK) return st;
+            }
+        learned_decide_kernel<<<1, 32, 0, lat->stream>>>(lat->learned_ctl, lat->accept_slots + 8 * kAcceptSlots,
+                                                         links, min_acceptance);
+        SU2_CUDA(cudaGetLastError());
+        lat->sweep += 1;
+        if (measure_every > 0 && s % measure_every == 0) {
+            if ((st = launch_plaquette(lat, lat->scratch.history + m)) != SU2_OK) return st;
+            if ((st = launch_polyakov(lat, lat->scratch.history + lat->scratch.history_cap + m)) != SU2_OK) return st;
+            ++m;
+        }
+    }
+    if (nmeas > 0 && plaq)
+        SU2_CUDA(cudaMemcpyAsync(plaq, lat->scratch.history, sizeof(double) * nmeas, cudaMemcpyDeviceToHost,
+                                 lat->stream));
+    if (nmeas > 0 && poly)
+        SU2_CUDA(cudaMemcpyAsync(poly, lat->scratch.history + lat->scratch.history_cap, sizeof(double) * nmeas,
+                                 cudaMemcpyDeviceToHost, lat->stream));
+    unsigned long long slots[8 * kAcceptSlots];
+    unsigned int ctl[4];
+    SU2_CUDA(cudaMemcpyAsync(slots, lat->accept_slots, sizeof slots, cudaMemcpyDeviceToHost, lat->stream));
+    SU2_CUDA(cudaMemcpyAsync(ctl, lat->learned_ctl, sizeof ctl, cudaMemcpyDeviceToHost, lat->stream));
+    su2_stats plain;
+    memset(&plain, 0, sizeof plain);
+    st = collect_stats(lat, &plain, (uint64_t)nsweeps);
+    if (stats) {
+        memset(stats, 0, sizeof *stats);
+        for (int ph = 0; ph < 8; ++ph) {
+            uint64_t a = 0;
+            for (int j = 0; j < kAcceptSlots; ++j) a += slots[ph * kAcceptSlots + j];
+            stats->accepted[ph] = a;
+            stats->plain_trials[ph] = plain.trials[ph];
+        }
+        stats->plain_sweeps = ctl[1];
+        stats->learned_sweeps = ctl[2];
+        stats->link_updates = (uint64_t)nsweeps * 4ull * (uint64_t)lat->vol;
+    }
+    return st;
+}
+
+su2_status su2_collect_pairs(su2_lattice *lat, int mu, int parity, int stride, float *dev_pairs, size_t cap,
+                             size_t *n)
+{
+    if (!lat || !dev_pairs || !n || mu < 0 || mu > 3 || (parity != 0 && parity != 1) || stride < 1) return SU2_E_INVAL;
+    const int n_pairs = (lat->vh + stride - 1) / stride;
+    if ((size_t)n_pairs > cap) {
+        set_last_error("su2_collect_pairs: buffer too small");
+        return SU2_E_INVAL;
+    }
+    DeviceGuard guard(lat->device);
+    const Geom g = geom_of(lat);
+    const RoundKeys rk = make_round_keys(lat->seed);
+    const int grid = (n_pairs + kLearnThreads - 1) / kLearnThreads;
+    float2 *out = (float2 *)dev_pairs;
+    const float beta = (float)lat->beta;
+    switch (mu) {
+    case 0: collect_kernel<0><<<grid, kLearnThreads, 0, lat->stream>>>(lat->links, g, parity, rk, beta, lat->sweep, stride, out, n_pairs); break;
+    case 1: collect_kernel<1><<<grid, kLearnThreads, 0, lat->stream>>>(lat->links, g, parity, rk, beta, lat->sweep, stride, out, n_pairs); break;
+    case 2: collect_kernel<2><<<grid, kLearnThreads, 0, lat->stream>>>(lat->links, g, parity, rk, beta, lat->sweep, stride, out, n_pairs); break;
+    default: collect_kernel<3><<<grid, kLearnThreads, 0, lat->stream>>>(lat->links, g, parity, rk, beta, lat->sweep, stride, out, n_pairs); break;
+    }
+    SU2_CUDA(cudaGetLastError());
+    *n = (size_t)n_pairs;
+    return SU2_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,216 @@
+// learned.cuh -- device side of the learned a0 proposal: the small MLP of
+// beta k, the monotone rational-quadratic spline it parametrises (Durkan,
+// Bekasov, Murray, Papamakarios, "Neural Spline Flows", NeurIPS 2019), and the
+// independence-Metropolis link step that uses it as the proposal for the
+// heat-bath law of a0 (Sec. 2 of Cardoso & Bicudo).  binary32 with explicit
+// round-to-nearest intrinsics throughout.
+//
+// Weights (float[1947]): W1[32], b1[32], W2[32][32], b2[32], W3[25][32],
+// b3[25], input mean, input scale; network input s = (beta k - mean) scale,
+// h1 = relu(W1 s + b1), h2 = relu(W2 h1 + b2), o = W3 h2 + b3.
+// Spline parameters (27 floats): knots x_0..x_8 and y_0..y_8 on [-1, 1] from
+// widths / heights 2 (m + (1 - 8 m) softmax), m = 1e-3, and knot derivatives
+// d_0..d_8 = 1e-3 + softplus.
+#pragma once
+
+#include "su2_device.cuh"
+
+namespace su2 {
+namespace learned {
+
+constexpr int kBins = 8;
+constexpr int kHidden = 32;
+constexpr int kOut = 25;
+constexpr int kParams = 27;
+constexpr int kWeights = 1947;
+constexpr int kTrainable = 1945;
+constexpr int kOffW1 = 0, kOffB1 = 32, kOffW2 = 64, kOffB2 = 1088, kOffW3 = 1120, kOffB3 = 1920;
+constexpr int kOffMean = 1945, kOffScale = 1946;
+constexpr float kMinBin = 1e-3f;
+constexpr float kMinDer = 1e-3f;
+
+__device__ __forceinline__ float exp_neg(float y) { return y < -87.0f ? 0.0f : exp_series(y); }
+__device__ __forceinline__ float relu(float x) { return x > 0.0f ? x : 0.0f; }
+
+// Sums start at the bias and add w[i] x[i], i ascending, one fused multiply-add each.
+__device__ __forceinline__ void mlp_forward(const float *__restrict__ w, float s, float (&o)[kOut])
+{
+    float h1[kHidden], h2[kHidden];
+#pragma unroll
+    for (int j = 0; j < kHidden; ++j) h1[j] = relu(__fmaf_rn(w[kOffW1 + j], s, w[kOffB1 + j]));
+#pragma unroll 4
+    for (int j = 0; j < kHidden; ++j) {
+        float acc = w[kOffB2 + j];
+#pragma unroll
+        for (int i = 0; i < kHidden; ++i) acc = __fmaf_rn(w[kOffW2 + j * kHidden + i], h1[i], acc);
+        h2[j] = relu(acc);
+    }
+#pragma unroll 5
+    for (int j = 0; j < kOut; ++j) {
+        float acc = w[kOffB3 + j];
+#pragma unroll
+        for (int i = 0; i < kHidden; ++i) acc = __fmaf_rn(w[kOffW3 + j * kHidden + i], h2[i], acc);
+        o[j] = acc;
+    }
+}
+
+// Knots -1 = k_0 < ... < k_8 = 1 from 8 unnormalised log-widths.
+__device__ __forceinline__ void knots_from(const float *o8, float *k9)
+{
+    float mx = o8[0];
+#pragma unroll
+    for (int i = 1; i < kBins; ++i) mx = o8[i] > mx ? o8[i] : mx;
+    float e[kBins], sum = 0.0f;
+#pragma unroll
+    for (int i = 0; i < kBins; ++i) {
+        e[i] = exp_neg(__fsub_rn(o8[i], mx));
+        sum = __fadd_rn(sum, e[i]);
+    }
+    k9[0] = -1.0f;
+#pragma unroll
+    for (int i = 0; i < kBins - 1; ++i) {
+        const float width = __fmul_rn(2.0f, __fmaf_rn(1.0f - 8.0f * kMinBin, __fdiv_rn(e[i], sum), kMinBin));
+        k9[i + 1] = __fadd_rn(k9[i], width);
+    }
+    k9[kBins] = 1.0f;
+}
+
+// softplus(t) = max(t, 0) + log(1 + exp(-|t|))
+__device__ __forceinline__ float softplus(float t)
+{
+    const float at = t < 0.0f ? -t : t;
+    return __fadd_rn(t > 0.0f ? t : 0.0f, log_series(__fadd_rn(1.0f, exp_neg(-at))));
+}
+
+__device__ __forceinline__ void spline_params(const float (&o)[kOut], float *p)
+{
+    knots_from(o, p);
+    knots_from(o + kBins, p + kBins + 1);
+#pragma unroll
+    for (int i = 0; i <= kBins; ++i) p[2 * (kBins + 1) + i] = __fadd_rn(kMinDer, softplus(o[2 * kBins + i]));
+}
+
+__device__ __forceinline__ int bin_of(const float *k9, float v)
+{
+    int k = 0;
+#pragma unroll
+    for (int j = 1; j < kBins; ++j)
+        if (k9[j] <= v) k = j;
+    return k;
+}
+
+// a = y_k + h (s xi^2 + d_k t)/den, den = s + (d_{k+1} + d_k - 2 s) t, t = xi (1 - xi),
+// f' = s^2 (d_{k+1} xi^2 + 2 s t + d_k (1 - xi)^2) / den^2.
+__device__ __forceinline__ float spline_eval(const float *p, int k, float xi, float &fprime)
+{
+    const float *x = p, *y = p + kBins + 1, *d = p + 2 * (kBins + 1);
+    const float w = __fsub_rn(x[k + 1], x[k]);
+    const float h = __fsub_rn(y[k + 1], y[k]);
+    const float s = __fdiv_rn(h, w);
+    const float t = __fmul_rn(xi, __fsub_rn(1.0f, xi));
+    const float sigma = __fsub_rn(__fadd_rn(d[k + 1], d[k]), __fmul_rn(2.0f, s));
+    const float den = __fmaf_rn(sigma, t, s);
+    const float num = __fmul_rn(h, __fmaf_rn(__fmul_rn(s, xi), xi, __fmul_rn(d[k], t)));
+    const float omx = __fsub_rn(1.0f, xi);
+    const float m = __fmaf_rn(__fmul_rn(d[k + 1], xi), xi,
+                              __fmaf_rn(__fmul_rn(2.0f, s), t, __fmul_rn(__fmul_rn(d[k], omx), omx)));
+    fprime = __fdiv_rn(__fmul_rn(__fmul_rn(s, s), m), __fmul_rn(den, den));
+    return __fadd_rn(y[k], __fdiv_rn(num, den));
+}
+
+__device__ __forceinline__ float spline_forward(const float *p, float z, float &fprime)
+{
+    const int k = bin_of(p, z);
+    const float w = __fsub_rn(p[k + 1], p[k]);
+    float xi = __fdiv_rn(__fsub_rn(z, p[k]), w);
+    xi = xi < 0.0f ? 0.0f : (xi > 1.0f ? 1.0f : xi);
+    const float a = spline_eval(p, k, xi, fprime);
+    return a < -1.0f ? -1.0f : (a > 1.0f ? 1.0f : a);
+}
+
+// Inverse on bin k of y: alpha xi^2 + beta xi + c = 0, xi = 2c / (-beta - sqrt(beta^2 - 4 alpha c)).
+__device__ __forceinline__ float spline_inverse(const float *p, float a, float &fprime)
+{
+    const float *x = p, *y = p + kBins + 1, *d = p + 2 * (kBins + 1);
+    const int k = bin_of(y, a);
+    const float w = __fsub_rn(x[k + 1], x[k]);
+    const float h = __fsub_rn(y[k + 1], y[k]);
+    const float s = __fdiv_rn(h, w);
+    const float dy = __fsub_rn(a, y[k]);
+    const float sigma = __fsub_rn(__fadd_rn(d[k + 1], d[k]), __fmul_rn(2.0f, s));
+    const float alpha = __fmaf_rn(dy, sigma, __fmul_rn(h, __fsub_rn(s, d[k])));
+    const float beta = __fmaf_rn(-dy, sigma, __fmul_rn(h, d[k]));
+    const float c = __fmul_rn(-s, dy);
+    float disc = __fmaf_rn(beta, beta, __fmul_rn(__fmul_rn(-4.0f, alpha), c));
+    disc = disc > 0.0f ? disc : 0.0f;
+    const float denom = __fsub_rn(-beta, __fsqrt_rn(disc));
+    float xi = denom != 0.0f ? __fdiv_rn(__fmul_rn(2.0f, c), denom) : 0.0f;
+    xi = xi < 0.0f ? 0.0f : (xi > 1.0f ? 1.0f : xi);
+    spline_eval(p, k, xi, fprime);
+    return __fmaf_rn(xi, w, x[k]);
+}
+
+// Parameters at network input s by linear interpolation between the two
+// table rows around it (s clamped to the table's range).
+__device__ __forceinline__ void table_params(const float *table, int G, float s_lo, float s_hi, float s,
+                                             float (&p)[kParams])
+{
+    const float inv_ds = __fdiv_rn((float)(G - 1), __fsub_rn(s_hi, s_lo));
+    float u = __fmul_rn(__fsub_rn(s, s_lo), inv_ds);
+    u = u < 0.0f ? 0.0f : (u > (float)(G - 1) ? (float)(G - 1) : u);
+    int j = (int)floorf(u);
+    if (j > G - 2) j = G - 2;
+    const float f = __fsub_rn(u, (float)j);
+    const float *r0 = table + j * kParams, *r1 = r0 + kParams;
+#pragma unroll
+    for (int i = 0; i < kParams; ++i) p[i] = __fmaf_rn(f, __fsub_rn(r1[i], r0[i]), r0[i]);
+}
+
+struct Proposal {
+    const float *table;  // G x 27 (shared or global memory)
+    int G;
+    float s_lo, s_hi, mean, scale;
+};
+
+// Independence-Metropolis update of one link (staple v, current link old):
+// proposal a0' = f(2 u0 - 1) with density 1/(2 f'), direction from u2, u3;
+// accepted iff u1 <= exp(Delta) (or Delta >= 0) with
+// Delta = beta k (a0' - a_cur) + log(sqrt((1 - a0'^2)/(1 - a_cur^2)) f'(z')/f'(z_cur)),
+// a_cur = old U~.  All four uniforms from one Philox block of the learned stream.
+// Returns 1 (out = new link) or 0 (out = old).
+__device__ __forceinline__ int learned_link(const Proposal &pr, float beta, float4 v, float4 old, uint4 w,
+                                            float4 &out)
+{
+    const DrawSetup d = prepare_draw(v, beta);
+    float p[kParams];
+    table_params(pr.table, pr.G, pr.s_lo, pr.s_hi, __fmul_rn(__fsub_rn(d.bk, pr.mean), pr.scale), p);
+    const float u0 = uniform01(w.x), u1 = uniform01(w.y), u2 = uniform01(w.z), u3 = uniform01(w.w);
+    float fp_new, fp_cur;
+    const float a_new = spline_forward(p, __fsub_rn(__fmul_rn(2.0f, u0), 1.0f), fp_new);
+    float acur = chain4(old.x, d.ut.x, old.y, d.ut.y, old.z, d.ut.z, old.w, d.ut.w);
+    acur = acur < -1.0f ? -1.0f : (acur > 1.0f ? 1.0f : acur);
+    spline_inverse(p, acur, fp_cur);
+    const float one_cur = __fmaf_rn(-acur, acur, 1.0f);
+    bool accept;
+    if (!(one_cur > 0.0f)) {
+        accept = true;
+    } else {
+        const float one_new = __fmaf_rn(-a_new, a_new, 1.0f);
+        const float ratio = __fmul_rn(__fsqrt_rn(__fdiv_rn(one_new, one_cur)), __fdiv_rn(fp_new, fp_cur));
+        if (!(ratio > 0.0f)) {
+            accept = false;
+        } else {
+            const float delta = __fmaf_rn(d.bk, __fsub_rn(a_new, acur), log_series(ratio));
+            accept = delta >= 0.0f || u1 <= exp_neg(delta);
+        }
+    }
+    if (!accept) {
+        out = old;
+        return 0;
+    }
+    out = direction_from_uniforms(a_new, d.ut, u2, u3);
+    return 1;
+}
+
+}  // namespace learned
+}  // namespace su2

@@ -242,16 +242,21 @@ __device__ __forceinline__ bool creutz_trial(float r1, float r2, float bk, float
 
 // Vector part uniform on the sphere of radius sqrt(1 - a0^2): c = 2 u0 - 1,
 // phi = 2 pi u1 (direction block 0); returns U' = a U~^dag.
-__device__ __forceinline__ float4 direction_update(float a0, float4 ut, uint4 d)
+__device__ __forceinline__ float4 direction_from_uniforms(float a0, float4 ut, float uc, float uphi)
 {
     const float r = __fsqrt_rn(__fmaf_rn(-a0, a0, 1.0f));
-    const float c = __fsub_rn(__fmul_rn(2.0f, uniform01(d.x)), 1.0f);
+    const float c = __fsub_rn(__fmul_rn(2.0f, uc), 1.0f);
     const float st = __fsqrt_rn(__fmaf_rn(-c, c, 1.0f));
     float sn, cs;
-    sincos_2pi(uniform01(d.y), sn, cs);
+    sincos_2pi(uphi, sn, cs);
     const float rs = __fmul_rn(r, st);
     const float4 a = make_float4(a0, __fmul_rn(rs, cs), __fmul_rn(rs, sn), __fmul_rn(r, c));
     return qmul(a, ut);
+}
+
+__device__ __forceinline__ float4 direction_update(float a0, float4 ut, uint4 d)
+{
+    return direction_from_uniforms(a0, ut, uniform01(d.x), uniform01(d.y));
 }
 
 // The whole heat-bath draw of one link from its staple v (Sec. 2), trial by

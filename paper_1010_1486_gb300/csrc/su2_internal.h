@@ -52,6 +52,15 @@ struct su2_lattice {
     bool timing = false;
     std::vector<cudaEvent_t> events;  // pairs around timed phase launches
     size_t events_used = 0;
+
+    // learned proposal (allocated by su2_set_proposal)
+    void *learned_block = nullptr;
+    size_t learned_bytes = 0;
+    float *proposal = nullptr;                 // G x 27 spline parameters
+    int proposal_g = 0;
+    float prop_s_lo = 0, prop_s_hi = 1, prop_mean = 0, prop_scale = 1;
+    unsigned int *learned_ctl = nullptr;       // [0] gate (1 = learned sweep), [1] plain sweeps, [2] learned sweeps
+    unsigned long long *accept_slots = nullptr;  // [8][64] per call, then [64] per sweep
 };
 
 namespace su2 {
@@ -121,7 +130,8 @@ cudaError_t convert_links(float4 *eo_links, float4 *lex_links, const Geom &g, bo
 // Launchers (each enqueues on lat->stream and returns a status of the launch).
 su2_status launch_cold_start(su2_lattice *lat);
 su2_status launch_hot_start(su2_lattice *lat);
-su2_status launch_hb_phase(su2_lattice *lat, int mu, int parity, uint32_t sweep);
+su2_status launch_hb_phase(su2_lattice *lat, int mu, int parity, uint32_t sweep,
+                           const unsigned int *gate = nullptr);
 su2_status launch_reunitarize(su2_lattice *lat);
 // Observables: write the value into *dst (device memory) without synchronising.
 su2_status launch_plaquette(su2_lattice *lat, double *dst);

@@ -50,6 +50,17 @@ class su2_stats(ctypes.Structure):
                 "timed": bool(self.timed), "kernel_ms": self.kernel_ms}
 
 
+class su2_learned_stats(ctypes.Structure):
+    _fields_ = [("link_updates", ctypes.c_uint64), ("accepted", ctypes.c_uint64 * 8),
+                ("plain_trials", ctypes.c_uint64 * 8), ("learned_sweeps", ctypes.c_uint32),
+                ("plain_sweeps", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {"link_updates": self.link_updates, "accepted": list(self.accepted),
+                "plain_trials": list(self.plain_trials), "learned_sweeps": self.learned_sweeps,
+                "plain_sweeps": self.plain_sweeps}
+
+
 class su2_state(ctypes.Structure):
     _fields_ = [("ns", ctypes.c_int32), ("nt", ctypes.c_int32), ("beta", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("sweep", ctypes.c_uint32)]
@@ -93,6 +104,10 @@ _SIGS = {
                        ctypes.POINTER(_i32)],
     "su2_selftest_barrier_timeout": [_i32, _u64, ctypes.POINTER(_u32)],
     "su2_selftest_mma": [_P, _P, _i32, _P],
+    "su2_set_proposal": [_P, _P, _i32, _f64, _f64, _i32],
+    "su2_get_proposal_table": [_P, _P],
+    "su2_learned_generate": [_P, _i32, _i32, _f64, _P, _P, ctypes.POINTER(su2_learned_stats)],
+    "su2_collect_pairs": [_P, _i32, _i32, _i32, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)],
 }
 for _name, _args in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -282,6 +297,43 @@ def su2_plaquette_noalloc(links_ptr: int, ns: int, nt: int, out_ptr: int, stream
     For callers that cannot allocate device memory at this point; see
     include/su2.h for the scratch it shares between calls and its size limit."""
     _check(_lib.su2_plaquette_noalloc(links_ptr, ns, nt, out_ptr, _stream_handle(stream)), "su2_plaquette_noalloc")
+
+
+# --------------------------------------------------------- learned proposal
+N_WEIGHTS = 1947
+N_SPLINE = 27
+
+
+def su2_set_proposal(lat: int, weights: np.ndarray, s_lo: float, s_hi: float, grid_points: int = 256) -> None:
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    _check(_lib.su2_set_proposal(lat, _host_ptr(w), w.size, float(s_lo), float(s_hi), int(grid_points)),
+           "su2_set_proposal")
+
+
+def su2_get_proposal_table(lat: int, grid_points: int) -> np.ndarray:
+    out = np.zeros((grid_points, N_SPLINE), dtype=np.float32)
+    _check(_lib.su2_get_proposal_table(lat, _host_ptr(out)), "su2_get_proposal_table")
+    return out
+
+
+def su2_learned_generate(lat: int, nsweeps: int, measure_every: int = 1, min_acceptance: float = 0.7,
+                         plaq: np.ndarray | None = None, poly: np.ndarray | None = None):
+    nmeas = nsweeps // measure_every if measure_every > 0 else 0
+    if plaq is None:
+        plaq = np.zeros(max(nmeas, 1), dtype=np.float64)
+    if poly is None:
+        poly = np.zeros(max(nmeas, 1), dtype=np.float64)
+    st = su2_learned_stats()
+    _check(_lib.su2_learned_generate(lat, nsweeps, measure_every, float(min_acceptance), _host_ptr(plaq),
+                                     _host_ptr(poly), ctypes.byref(st)), "su2_learned_generate")
+    return plaq[:nmeas], poly[:nmeas], st.as_dict()
+
+
+def su2_collect_pairs(lat: int, mu: int, parity: int, stride: int, dev_ptr: int, cap: int) -> int:
+    """(beta k, a0) float2 pairs into the device buffer at dev_ptr (cap pairs)."""
+    n = ctypes.c_size_t()
+    _check(_lib.su2_collect_pairs(lat, mu, parity, stride, dev_ptr, cap, ctypes.byref(n)), "su2_collect_pairs")
+    return n.value
 
 
 # ------------------------------------------------------------------ batches

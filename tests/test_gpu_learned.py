@@ -1,0 +1,118 @@
+"""Learned proposal on the GPU against the CPU oracle: the proposal table
+(network evaluated at grid points), learned Metropolis sweeps with the plain
+heat bath as fallback, and the collection of (beta k, a0) training pairs --
+all link for link / bit for bit, through the C ABI."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1010_1486_gb300 import su2
+
+pytestmark = pytest.mark.gpu
+
+
+def threads():
+    return min(16, os.cpu_count() or 1)
+
+
+def weights(seed, scale=0.3, mean=4.0, inv_sd=0.5):
+    rng = np.random.default_rng(seed)
+    w = np.zeros(su2.N_WEIGHTS, dtype=np.float32)
+    w[:1945] = rng.normal(size=1945) * scale
+    w[1945], w[1946] = mean, inv_sd
+    return w
+
+
+def test_proposal_table_is_bitwise_the_oracles():
+    h = su2.su2_create(4, 4, 2.3, 1, su2.SU2_HOT)
+    try:
+        for seed, (lo, hi, G) in enumerate([(-3.0, 3.0, 256), (-1.5, 2.5, 64), (0.0, 1.0, 2)]):
+            w = weights(seed, 0.5)
+            su2.su2_set_proposal(h, w, lo, hi, G)
+            got = su2.su2_get_proposal_table(h, G)
+            want = oracle.proposal_table(w, lo, hi, G)
+            assert np.array_equal(got.view(np.uint32), want.view(np.uint32)), seed
+    finally:
+        su2.su2_destroy(h)
+
+
+@pytest.mark.parametrize("ns,nt,beta", [(4, 4, 2.3), (6, 4, 1.8), (8, 8, 2.4)])
+def test_learned_sweeps_link_for_link(ns, nt, beta):
+    seed = 41
+    w = weights(ns + nt, 0.2, mean=beta * 3.0, inv_sd=0.6)
+    lo, hi, G = -3.0, 3.0, 128
+    h = su2.su2_create(ns, nt, beta, seed, su2.SU2_HOT)
+    try:
+        su2.su2_heatbath_sweep(h, 2)
+        su2.su2_set_proposal(h, w, lo, hi, G)
+        plaq, poly, st = su2.su2_learned_generate(h, 3, 1, 0.0)
+        got = su2.su2_get_links(h, ns, nt)
+    finally:
+        su2.su2_destroy(h)
+    links = oracle.hot_start(ns, nt, seed)
+    for s in range(2):
+        oracle.heatbath_sweep(ns, nt, beta, seed, s, links)
+    table = oracle.proposal_table(w, lo, hi, G)
+    acc = np.zeros(8, dtype=np.int64)
+    for s in range(2, 5):
+        acc += oracle.learned_sweep(ns, nt, beta, seed, s, links, table, lo, hi, float(w[1945]), float(w[1946]))
+        assert abs(plaq[s - 2] - oracle.plaquette(ns, nt, links)) <= 1e-6 * max(1, abs(plaq[s - 2]))
+    assert np.array_equal(got, links)
+    assert st["accepted"] == [int(a) for a in acc]
+    assert st["learned_sweeps"] == 3 and st["plain_sweeps"] == 0
+    assert 0 < sum(acc) < 3 * 4 * ns ** 3 * nt
+
+
+def test_fallback_alternates_with_the_plain_heat_bath():
+    ns, nt, beta, seed = 6, 6, 2.3, 5
+    w = weights(9, 0.2, mean=7.0, inv_sd=0.5)
+    lo, hi, G = -3.0, 3.0, 64
+    threshold = 0.999  # no learned sweep reaches it: every learned sweep is followed by a plain one
+    h = su2.su2_create(ns, nt, beta, seed, su2.SU2_HOT)
+    try:
+        su2.su2_set_proposal(h, w, lo, hi, G)
+        _, _, st = su2.su2_learned_generate(h, 5, 0, threshold)
+        got = su2.su2_get_links(h, ns, nt)
+    finally:
+        su2.su2_destroy(h)
+    links = oracle.hot_start(ns, nt, seed)
+    table = oracle.proposal_table(w, lo, hi, G)
+    learned = True
+    n_learned = n_plain = 0
+    acc_total = np.zeros(8, dtype=np.int64)
+    trials = np.zeros(8, dtype=np.int64)
+    for s in range(5):
+        if learned:
+            acc = oracle.learned_sweep(ns, nt, beta, seed, s, links, table, lo, hi, float(w[1945]), float(w[1946]))
+            acc_total += acc
+            n_learned += 1
+            learned = not (acc.sum() < threshold * 4 * ns ** 3 * nt)
+        else:
+            trials += oracle.heatbath_sweep(ns, nt, beta, seed, s, links)
+            n_plain += 1
+            learned = True
+    assert np.array_equal(got, links)
+    assert (st["learned_sweeps"], st["plain_sweeps"]) == (n_learned, n_plain) == (3, 2)
+    assert st["accepted"] == [int(a) for a in acc_total]
+    assert st["plain_trials"] == [int(t) for t in trials]
+
+
+def test_collected_pairs_are_bitwise_the_oracles():
+    torch = pytest.importorskip("torch")
+    ns, nt, beta, seed = 8, 6, 2.4, 12
+    h = su2.su2_create(ns, nt, beta, seed, su2.SU2_HOT)
+    try:
+        su2.su2_heatbath_sweep(h, 3)
+        links = su2.su2_get_links(h, ns, nt)
+        buf = torch.zeros((ns ** 3 * nt, 2), dtype=torch.float32, device="cuda")
+        for mu, par, stride in [(0, 0, 1), (3, 1, 5), (2, 0, 7)]:
+            n = su2.su2_collect_pairs(h, mu, par, stride, buf.data_ptr(), buf.shape[0])
+            torch.cuda.synchronize()
+            got = buf[:n].cpu().numpy()
+            want = oracle.collect_pairs(ns, nt, beta, seed, 3, mu, par, stride, links)
+            assert np.array_equal(got.view(np.uint32), want.view(np.uint32)), (mu, par, stride)
+        assert np.array_equal(su2.su2_get_links(h, ns, nt), links)  # the chain did not move
+    finally:
+        su2.su2_destroy(h)
