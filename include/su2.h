@@ -201,6 +201,37 @@ su2_status su2_learned_generate(su2_lattice *lat, int nsweeps, int measure_every
 su2_status su2_collect_pairs(su2_lattice *lat, int mu, int parity, int stride, float *dev_pairs, size_t cap,
                              size_t *n);
 
+/* Training of the proposal by maximum likelihood on (beta k, a0) pairs: mean
+ * -log q(a0 | beta k) over mini-batches, minimised with Adam (beta1 0.9,
+ * beta2 0.999, eps 1e-8).  Per step, 128 samples per CTA: the two hidden
+ * contractions of the forward pass and the two of the backward pass run on
+ * the tensor cores (tcgen05, BF16 operands, FP32 accumulation in tensor
+ * memory); the spline likelihood, its gradient and the weight-gradient sums
+ * are FP32 on the CUDA cores.  The trainer owns its device memory; all calls
+ * are ordered on its stream. */
+typedef struct su2_trainer su2_trainer;
+
+/* init_weights: float[1947] (host); seed keys the mini-batch sampling. */
+su2_status su2_trainer_create(const float *init_weights, uint64_t seed, void *cuda_stream, su2_trainer **out);
+su2_status su2_trainer_destroy(su2_trainer *tr);
+
+/* Sets the input mean and scale (weights 1945, 1946) to the mean and
+ * 1/standard deviation of beta k over n device pairs (float2). */
+su2_status su2_trainer_set_input_scaling(su2_trainer *tr, const float *dev_pairs, size_t n);
+
+/* `steps` Adam steps of `batch` (multiple of 128, <= 65536) pairs drawn with
+ * replacement from the n device pairs; loss_per_step (host, nullable)
+ * receives each step's mean loss.  Synchronises at the end. */
+su2_status su2_trainer_fit(su2_trainer *tr, const float *dev_pairs, size_t n, int steps, int batch, double lr,
+                           float *loss_per_step);
+
+/* Mean loss and gradient (1945 floats, host) over exactly the n device pairs
+ * (n a multiple of 128, <= 65536), without updating the weights. */
+su2_status su2_trainer_gradient(su2_trainer *tr, const float *dev_pairs, size_t n, double *loss, float *grad);
+
+/* Current weights (float[1947], host). */
+su2_status su2_trainer_get_weights(su2_trainer *tr, float *host);
+
 /* ---------------------------------------------------------------------------
  * Batches: many independent lattices (own Ns^3 x Nt, beta and seed each) swept
  * together.  Each lattice follows exactly the chain of su2_create +

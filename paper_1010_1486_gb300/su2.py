@@ -108,6 +108,12 @@ _SIGS = {
     "su2_get_proposal_table": [_P, _P],
     "su2_learned_generate": [_P, _i32, _i32, _f64, _P, _P, ctypes.POINTER(su2_learned_stats)],
     "su2_collect_pairs": [_P, _i32, _i32, _i32, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)],
+    "su2_trainer_create": [_P, _u64, _P, ctypes.POINTER(_P)],
+    "su2_trainer_destroy": [_P],
+    "su2_trainer_set_input_scaling": [_P, _P, ctypes.c_size_t],
+    "su2_trainer_fit": [_P, _P, ctypes.c_size_t, _i32, _i32, _f64, _P],
+    "su2_trainer_gradient": [_P, _P, ctypes.c_size_t, ctypes.POINTER(_f64), _P],
+    "su2_trainer_get_weights": [_P, _P],
 }
 for _name, _args in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -334,6 +340,43 @@ def su2_collect_pairs(lat: int, mu: int, parity: int, stride: int, dev_ptr: int,
     n = ctypes.c_size_t()
     _check(_lib.su2_collect_pairs(lat, mu, parity, stride, dev_ptr, cap, ctypes.byref(n)), "su2_collect_pairs")
     return n.value
+
+
+def su2_trainer_create(init_weights: np.ndarray, seed: int = 0, stream=None) -> int:
+    w = np.ascontiguousarray(init_weights, dtype=np.float32)
+    if w.size != N_WEIGHTS:
+        raise ValueError("1947 weights expected")
+    h = _P()
+    _check(_lib.su2_trainer_create(_host_ptr(w), int(seed), _stream_handle(stream), ctypes.byref(h)),
+           "su2_trainer_create")
+    return h.value
+
+
+def su2_trainer_destroy(tr: int) -> None:
+    _check(_lib.su2_trainer_destroy(tr), "su2_trainer_destroy")
+
+
+def su2_trainer_set_input_scaling(tr: int, dev_pairs: int, n: int) -> None:
+    _check(_lib.su2_trainer_set_input_scaling(tr, dev_pairs, n), "su2_trainer_set_input_scaling")
+
+
+def su2_trainer_fit(tr: int, dev_pairs: int, n: int, steps: int, batch: int = 4096, lr: float = 1e-3) -> np.ndarray:
+    losses = np.zeros(max(steps, 1), dtype=np.float32)
+    _check(_lib.su2_trainer_fit(tr, dev_pairs, n, steps, batch, float(lr), _host_ptr(losses)), "su2_trainer_fit")
+    return losses[:steps]
+
+
+def su2_trainer_gradient(tr: int, dev_pairs: int, n: int):
+    loss = _f64()
+    grad = np.zeros(1945, dtype=np.float32)
+    _check(_lib.su2_trainer_gradient(tr, dev_pairs, n, ctypes.byref(loss), _host_ptr(grad)), "su2_trainer_gradient")
+    return loss.value, grad
+
+
+def su2_trainer_get_weights(tr: int) -> np.ndarray:
+    w = np.zeros(N_WEIGHTS, dtype=np.float32)
+    _check(_lib.su2_trainer_get_weights(tr, _host_ptr(w)), "su2_trainer_get_weights")
+    return w
 
 
 # ------------------------------------------------------------------ batches
