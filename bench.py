@@ -44,6 +44,7 @@ UNIT = "link updates/s"
 # 10^6 configurations of 48^4 per day on two GTX 295 cards (one sweep each)
 PAPER_RATE = 1.0e6 * LINKS / 86400.0
 BYTES_PER_UPDATE = 128  # reads 3.5 V + writes 0.5 V float4 per phase of V/2 updates
+BYTES_PER_LEARNED_UPDATE = 144  # + the old link of the updated direction and parity
 HB_SOURCES = ["paper_1010_1486_gb300/csrc/heatbath.cu", "paper_1010_1486_gb300/csrc/su2_device.cuh"]
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "hb_phase_48x48x48x48_beta6.md")
 
@@ -55,9 +56,14 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=20)
-    ap.add_argument("--tau-sweeps", type=int, default=2000, help="extra sweeps for tau_int (0 = skip)")
+    ap.add_argument("--tau-sweeps", type=int, default=2000,
+                    help="sweeps per form for tau_int and the plaquette comparison (0 = skip)")
+    ap.add_argument("--therm", type=int, default=1500, help="thermalisation sweeps before the form comparison")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sample length")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--learned-pairs", type=int, default=1_000_000, help="training pairs (0 = skip the learned form)")
+    ap.add_argument("--train-steps", type=int, default=1500)
+    ap.add_argument("--batched-steps", type=int, default=200, help="sweeps of the 64-lattice batch (0 = skip)")
     return ap.parse_args(argv)
 
 
@@ -226,16 +232,15 @@ def run_ours(args, dist):
         if args.e2e_steps > 0:
             e2e = run_e2e(args, dist, lat, su2, torch)
 
-        tau = None
-        if args.tau_sweeps > 0:
-            tp, _, _ = su2.su2_generate(lat, args.tau_sweeps, 1, 0)
-            half = tp[len(tp) // 2:]
-            t, dt, w, err = tau_int(half)
-            tau = {"observable": "plaquette", "sweeps": len(half), "tau_int": t, "tau_int_err": dt,
-                   "plaquette_mean": float(np.mean(half)), "plaquette_err": err,
-                   "value_tau_adjusted": value / (2.0 * t)}
+        forms = None
+        if args.learned_pairs > 0:
+            forms = compare_forms(args, dist, lat, su2, torch, stream, tau_int)
     finally:
         su2.su2_destroy(lat)
+
+    batched = None
+    if args.batched_steps > 0:
+        batched = run_batched(args, dist, su2, torch)
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
@@ -255,9 +260,148 @@ def run_ours(args, dist):
         "clocks": clk,
         "trials_per_update": trials_per_update,
         "plaquette_last": float(plaq[-1]), "polyakov_last": float(poly[-1]),
-        "tau_int": tau,
+        "forms": forms,
+        "batched": batched,
     }
+    if forms and "value_tau_adjusted" in forms:
+        result["value_tau_adjusted"] = forms["value_tau_adjusted"]
     return result
+
+
+def timed(stream, torch, dist, fn):
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dist.barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    out = fn()
+    ev1.record(stream)
+    ev1.synchronize()
+    return dist.reduce(ev0.elapsed_time(ev1), "max"), out
+
+
+def compare_forms(args, dist, lat, su2, torch, stream, tau_int):
+    """Plain heat bath against the learned proposal on the same thermalised
+    48^4 lattice.  After `therm` more sweeps: (beta k, a0) pairs from the plain
+    sampler, training on the GPU, then both forms timed back to back, then
+    interleaved blocks plain / learned / plain ... for tau_int and the
+    plaquette: every learned block is compared with the mean of the plain
+    blocks around it, so a slow drift of the lattice cancels."""
+    import numpy as np
+
+    from paper_1010_1486_gb300 import learn
+
+    su2.su2_generate(lat, args.therm, 0, 0)
+    t0 = time.perf_counter()
+    pairs = learn.collect(lat, NS, NT, args.learned_pairs, sweeps_between=1)
+    t1 = time.perf_counter()
+    w, losses, s_lo, s_hi = learn.train(pairs, steps=args.train_steps, batch=4096, lr=2e-3, seed=11)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    del pairs
+    su2.su2_set_proposal(lat, w, s_lo, s_hi, 256)
+    peak, _ = measured_peaks()
+
+    # plain, timed on the thermalised lattice
+    su2.su2_set_timing(lat, True)
+    ms_p, (_, _, st_p) = timed(stream, torch, dist, lambda: su2.su2_generate(lat, args.steps, 1, 0))
+    plain_phase_s = st_p["kernel_ms"] / st_p["kernel_launches"] * 1e-3
+    value_plain = dist.reduce(float(st_p["link_updates"]), "sum") / (ms_p * 1e-3)
+    # learned, timed
+    su2.su2_learned_generate(lat, 2, 1, 0.7)
+    ms_l, (_, _, st_l) = timed(stream, torch, dist, lambda: su2.su2_learned_generate(lat, args.steps, 1, 0.7))
+    su2.su2_set_timing(lat, False)
+    learned_phase_s = st_l["kernel_ms"] / max(1, st_l["kernel_launches"]) * 1e-3
+    value_learned = dist.reduce(float(st_l["link_updates"]), "sum") / (ms_l * 1e-3)
+    proposals = st_l["learned_sweeps"] * 4 * VOL
+
+    out = {"lattice": "thermalised 48^4, beta = 6.0 (after warm-up, timed steps and %d more sweeps)" % args.therm,
+           "plain": {"value": value_plain, "unit": UNIT, "ms_per_step": ms_p / args.steps,
+                     "trials_per_update": sum(st_p["trials"]) / st_p["link_updates"],
+                     "roofline": {"bound": "hbm", "kernel": "hb_phase_kernel",
+                                  "achieved": BYTES_PER_UPDATE * (VOL // 2) / plain_phase_s / 1e9, "peak": peak,
+                                  "unit": "GB/s", "avg_launch_us": plain_phase_s * 1e6}},
+           "learned": {"value": value_learned, "unit": UNIT, "ms_per_step": ms_l / args.steps,
+                       "acceptance": sum(st_l["accepted"]) / max(1, proposals),
+                       "learned_sweeps": st_l["learned_sweeps"], "fallback_sweeps": st_l["plain_sweeps"],
+                       "roofline": {"bound": "hbm", "kernel": "learned_phase_kernel",
+                                    "achieved": BYTES_PER_LEARNED_UPDATE * (VOL // 2) / learned_phase_s / 1e9,
+                                    "peak": peak, "unit": "GB/s", "avg_launch_us": learned_phase_s * 1e6,
+                                    "bytes_per_launch": BYTES_PER_LEARNED_UPDATE * (VOL // 2)},
+                       "gpu_launches": st_l["kernel_launches"] * 2 + args.steps * 3,
+                       "training": {"pairs": args.learned_pairs, "steps": args.train_steps, "batch": 4096,
+                                    "collect_s": t1 - t0, "train_s": t2 - t1,
+                                    "loss_first": float(losses[:10].mean()), "loss_last": float(losses[-50:].mean())}}}
+    for form in ("plain", "learned"):
+        r = out[form]["roofline"]
+        r["frac"] = r["achieved"] / peak
+    if args.tau_sweeps > 0:
+        nblk = 8
+        per = max(50, args.tau_sweeps // nblk)
+        plain_blocks, learned_blocks = [], []
+        for k in range(nblk):
+            plain_blocks.append(su2.su2_generate(lat, per, 1, 0)[0].copy())
+            learned_blocks.append(su2.su2_learned_generate(lat, per, 1, 0.7)[0].copy())
+        plain_blocks.append(su2.su2_generate(lat, per, 1, 0)[0].copy())
+        tau_p = np.mean([tau_int(b)[0] for b in plain_blocks])
+        tau_l = np.mean([tau_int(b)[0] for b in learned_blocks])
+        d = np.array([learned_blocks[k].mean() - 0.5 * (plain_blocks[k].mean() + plain_blocks[k + 1].mean())
+                      for k in range(nblk)])
+        se = d.std(ddof=1) / np.sqrt(nblk)
+        out["plain"]["tau_int"] = float(tau_p)
+        out["learned"]["tau_int"] = float(tau_l)
+        out["plain"]["value_tau_adjusted"] = value_plain / (2 * tau_p)
+        out["learned"]["value_tau_adjusted"] = value_learned / (2 * tau_l)
+        out["plaquette_check"] = {"blocks": nblk, "sweeps_per_block": per,
+                                  "plain_mean": float(np.mean([b.mean() for b in plain_blocks])),
+                                  "learned_mean": float(np.mean([b.mean() for b in learned_blocks])),
+                                  "learned_minus_plain": float(d.mean()), "stderr": float(se),
+                                  "sigma": float(d.mean() / se) if se > 0 else None}
+        out["value_tau_adjusted"] = {"plain": out["plain"]["value_tau_adjusted"],
+                                     "learned": out["learned"]["value_tau_adjusted"],
+                                     "convention": "link updates/s / (2 tau_int(plaquette)), tau_int = 1/2 + sum rho"}
+    return out
+
+
+def run_batched(args, dist, su2, torch):
+    """64 independent lattices (8^4, 12^3x4, 16^3x6, 16^4, 24^3x8; beta in
+    [1.5, 3]; cold start): one persistent cooperative launch per sweep,
+    replayed from a CUDA graph, plaquette and Polyakov loop of every lattice
+    every sweep; launch shape autotuned first."""
+    from paper_1010_1486_gb300 import workloads
+
+    cfg = workloads.batched(64, seed=5 + dist.rank)
+    n = len(cfg["ns"])
+    sites = sum(x ** 3 * t for x, t in zip(cfg["ns"], cfg["nt"]))
+    stream = torch.cuda.Stream()
+    b = su2.su2_batch_create(cfg["ns"], cfg["nt"], cfg["beta"], cfg["seed"], cfg["start"], stream=stream)
+    try:
+        su2.su2_batch_sweep(b, 20)
+        depth, grid = su2.su2_batch_autotune(b, 5)
+        su2.su2_batch_generate(b, n, 5, 1)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        dist.barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        plaq, poly, st = su2.su2_batch_generate(b, n, args.batched_steps, 1)
+        ev1.record(stream)
+        ev1.synchronize()
+        info = su2.su2_batch_info(b)
+    finally:
+        su2.su2_batch_destroy(b)
+    ms = dist.reduce(ev0.elapsed_time(ev1), "max")
+    updates = dist.reduce(float(st["link_updates"]), "sum")
+    value = updates / (ms * 1e-3)
+    peak, _ = measured_peaks()
+    achieved = BYTES_PER_UPDATE * updates / dist.world / (ms * 1e-3) / 1e9
+    return {"workload": "64 lattices: 8^4, 12^3x4, 16^3x6, 16^4, 24^3x8 (13/13/13/13/12), beta uniform in [1.5, 3], "
+                        "cold start, plaquette and Polyakov loop of every lattice every sweep",
+            "sites": sites, "value": value, "unit": UNIT, "sweeps_per_s": args.batched_steps / (ms * 1e-3),
+            "ms_per_sweep": ms / args.batched_steps, "queue_depth": depth, "grid_blocks": grid,
+            "cuda_graph": info["graphs"], "gpu_launches": args.batched_steps,
+            "roofline": {"bound": "hbm", "kernel": "batch_sweep_kernel", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak,
+                         "note": "whole sweep incl. barriers and measurements; 169 MB of links, partly L2-resident"},
+            "plaquette_last": [float(x) for x in plaq[-1][:5]]}
 
 
 def run_e2e(args, dist, lat, su2, torch):

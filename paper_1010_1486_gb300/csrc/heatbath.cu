@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 
+#include "staple.cuh"
 #include "su2_device.cuh"
 #include "su2_internal.h"
 
@@ -32,39 +33,6 @@ struct HbParams {
 };
 
 constexpr int kHbWarps = kHbThreads / 32;
-
-// Forward and backward staple terms of direction nu (Sec. 2), from the six
-// links they need: U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag and
-// U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu).
-struct NuLinks {
-    float4 nu_xp, mu_xn, nu_x, nu_xpm, mu_xm, nu_xm;
-};
-
-template <int MU, int NU>
-__device__ __forceinline__ NuLinks load_nu(const float4 *__restrict__ L, const Geom &g, const Coord &x, int lex_p,
-                                           int parity)
-{
-    constexpr int nu = NU;
-    const int op = parity ^ 1;
-    NuLinks n;
-    const int e_xn = lex_fwd(g, x.lex, x.c[nu], nu) >> 1;
-    const int e_xm = lex_bwd(g, x.lex, x.c[nu], nu) >> 1;
-    const int e_xpm = lex_bwd(g, lex_p, x.c[nu], nu) >> 1;  // x + mu - nu keeps the nu coordinate of x
-    n.nu_xp = __ldg(L + link_index(g, nu, op, lex_p >> 1));
-    n.mu_xn = __ldg(L + link_index(g, MU, op, e_xn));
-    n.nu_x = __ldg(L + link_index(g, nu, parity, x.lex >> 1));
-    n.nu_xpm = __ldg(L + link_index(g, nu, parity, e_xpm));
-    n.mu_xm = __ldg(L + link_index(g, MU, op, e_xm));
-    n.nu_xm = __ldg(L + link_index(g, nu, op, e_xm));
-    return n;
-}
-
-__device__ __forceinline__ float4 add_nu_terms(float4 v, const NuLinks &n)
-{
-    const float4 fwd = qmul(qmul(n.nu_xp, qdag(n.mu_xn)), qdag(n.nu_x));
-    const float4 bwd = qmul(qmul(qdag(n.nu_xpm), qdag(n.mu_xm)), n.nu_xm);
-    return qadd(qadd(v, fwd), bwd);
-}
 
 // One heat-bath phase (mu = MU, sites of parity p.parity).
 //
@@ -307,24 +275,27 @@ su2_status launch_hb_phase(su2_lattice *lat, int mu, int parity, uint32_t sweep,
 }
 
 // ------------------------------------------------------------- timing
-static su2_status timed_phase(su2_lattice *lat, int mu, int parity, uint32_t sweep)
+su2_status timing_begin(su2_lattice *lat)
 {
-    if (!lat->timing) return launch_hb_phase(lat, mu, parity, sweep);
+    if (!lat->timing) return SU2_OK;
     while (lat->events.size() < lat->events_used + 2) {
         cudaEvent_t e;
         SU2_CUDA(cudaEventCreate(&e));
         lat->events.push_back(e);
     }
-    cudaEvent_t b = lat->events[lat->events_used], e = lat->events[lat->events_used + 1];
-    lat->events_used += 2;
-    SU2_CUDA(cudaEventRecord(b, lat->stream));
-    su2_status st = launch_hb_phase(lat, mu, parity, sweep);
-    if (st != SU2_OK) return st;
-    SU2_CUDA(cudaEventRecord(e, lat->stream));
+    SU2_CUDA(cudaEventRecord(lat->events[lat->events_used], lat->stream));
     return SU2_OK;
 }
 
-static su2_status read_timing(su2_lattice *lat, su2_stats *stats)
+su2_status timing_end(su2_lattice *lat)
+{
+    if (!lat->timing) return SU2_OK;
+    SU2_CUDA(cudaEventRecord(lat->events[lat->events_used + 1], lat->stream));
+    lat->events_used += 2;
+    return SU2_OK;
+}
+
+su2_status timing_read(su2_lattice *lat, double *ms_out)
 {
     double ms = 0.0;
     if (lat->timing && lat->events_used) {
@@ -335,12 +306,28 @@ static su2_status read_timing(su2_lattice *lat, su2_stats *stats)
             ms += t;
         }
     }
+    *ms_out = ms;
+    lat->events_used = 0;
+    return SU2_OK;
+}
+
+static su2_status timed_phase(su2_lattice *lat, int mu, int parity, uint32_t sweep)
+{
+    su2_status st = timing_begin(lat);
+    if (st == SU2_OK) st = launch_hb_phase(lat, mu, parity, sweep);
+    if (st == SU2_OK) st = timing_end(lat);
+    return st;
+}
+
+static su2_status read_timing(su2_lattice *lat, su2_stats *stats)
+{
+    double ms = 0.0;
+    su2_status st = timing_read(lat, &ms);
     if (stats) {
         stats->kernel_ms = ms;
         stats->timed = lat->timing ? 1u : 0u;
     }
-    lat->events_used = 0;
-    return SU2_OK;
+    return st;
 }
 
 static su2_status one_sweep(su2_lattice *lat)

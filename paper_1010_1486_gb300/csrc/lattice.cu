@@ -1,6 +1,7 @@
 // lattice.cu -- lattice handles: creation, device memory, cold/hot start
 // (Sec. 4 of Cardoso & Bicudo), link layout conversion, reunitarization,
 // resumable state, status strings.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -322,7 +323,8 @@ su2_status su2_create(int ns, int nt, double beta, uint64_t seed, su2_start star
 
     // one allocation: links | partials | ticket | result | trials | flags
     const size_t links_bytes = align256(sizeof(float4) * 8 * (size_t)lat->vh);
-    const int partials_cap = 152 * 64;
+    // one partial per block of the observable kernels (one site per thread)
+    const int partials_cap = (int)std::max<int64_t>(152 * 64, (lat->vol + kReduceThreads - 1) / kReduceThreads);
     const size_t partials_bytes = align256(sizeof(double) * partials_cap);
     const size_t ticket_bytes = align256(sizeof(unsigned int) * 4);
     const size_t result_bytes = align256(sizeof(double) * 4);

@@ -62,6 +62,10 @@ __device__ __forceinline__ unsigned int block_sum_u32(unsigned int v)
     return total;
 }
 
+// One learned phase (MU, parity).  Persistent grid: each thread walks the
+// links i, i + T, i + 2T, ... (T threads in the grid).  The 18 staple links of
+// its next link are loaded before the Metropolis step of the current one, so
+// their latency hides behind that step's arithmetic.
 template <int MU>
 __global__ void __launch_bounds__(kLearnThreads) learned_phase_kernel(const LearnedParams p)
 {
@@ -70,19 +74,40 @@ __global__ void __launch_bounds__(kLearnThreads) learned_phase_kernel(const Lear
     const int n_tab = p.G * learned::kParams;
     for (int i = threadIdx.x; i < n_tab; i += blockDim.x) s_table[i] = p.table[i];
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const learned::Proposal pr{s_table, p.G, p.s_lo, p.s_hi, p.mean, p.scale};
+    const int stride = gridDim.x * blockDim.x;
+    const uint32_t sw = stream_word(kLearned, (uint32_t)p.parity, MU);
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned int acc = 0;
+    NuLinks n0, n1, n2;
     if (i < p.g.vh) {
         const Coord x = eo_to_coord(p.g, i, p.parity);
-        const float4 v = staple_at<MU>(p.links, p.g, x, p.parity);
+        const int lex_p = lex_fwd(p.g, x.lex, x.c[MU], MU);
+        n0 = load_nu<MU, OtherDir<MU, 0>::value>(p.links, p.g, x, lex_p, p.parity);
+        n1 = load_nu<MU, OtherDir<MU, 1>::value>(p.links, p.g, x, lex_p, p.parity);
+        n2 = load_nu<MU, OtherDir<MU, 2>::value>(p.links, p.g, x, lex_p, p.parity);
+    }
+    while (i < p.g.vh) {
+        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        v = add_nu_terms(v, n0);
+        v = add_nu_terms(v, n1);
+        v = add_nu_terms(v, n2);
         const size_t li = link_index(p.g, MU, p.parity, i);
         const float4 old = p.links[li];
-        const uint4 w = philox_rk(make_uint4((uint32_t)i, p.sweep, stream_word(kLearned, (uint32_t)p.parity, MU), 0u),
-                                  p.rk);
-        const learned::Proposal pr{s_table, p.G, p.s_lo, p.s_hi, p.mean, p.scale};
+        const int inext = i + stride;
+        if (inext < p.g.vh) {
+            const Coord x = eo_to_coord(p.g, inext, p.parity);
+            const int lex_p = lex_fwd(p.g, x.lex, x.c[MU], MU);
+            n0 = load_nu<MU, OtherDir<MU, 0>::value>(p.links, p.g, x, lex_p, p.parity);
+            n1 = load_nu<MU, OtherDir<MU, 1>::value>(p.links, p.g, x, lex_p, p.parity);
+            n2 = load_nu<MU, OtherDir<MU, 2>::value>(p.links, p.g, x, lex_p, p.parity);
+        }
+        const uint4 w = philox_rk(make_uint4((uint32_t)i, p.sweep, sw, 0u), p.rk);
         float4 out;
-        acc = (unsigned int)learned::learned_link(pr, p.beta, v, old, w, out);
-        if (acc) p.links[li] = out;
+        const int a = learned::learned_link(pr, p.beta, v, old, w, out);
+        if (a) p.links[li] = out;
+        acc += (unsigned int)a;
+        i = inext;
     }
     const unsigned int total = block_sum_u32(acc);
     if (threadIdx.x == 0 && total) {
@@ -145,6 +170,20 @@ __global__ void __launch_bounds__(kLearnThreads) collect_kernel(const float4 *__
     pairs[q] = make_float2(d.bk, a0);
 }
 
+// Grid of all co-resident blocks (at most `want`), for the kernels that walk
+// their links in a loop.
+template <typename Kernel>
+static cudaError_t launch_persistent(Kernel kernel, const LearnedParams &p, int want, size_t smem, su2_lattice *lat)
+{
+    int per_sm = 0, sms = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kLearnThreads, smem);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, lat->device);
+    if (e != cudaSuccess) return e;
+    const int grid = std::max(1, std::min(want, std::max(1, per_sm) * sms));
+    kernel<<<grid, kLearnThreads, smem, lat->stream>>>(p);
+    return cudaGetLastError();
+}
+
 static su2_status launch_learned_phase(su2_lattice *lat, int mu, int parity)
 {
     LearnedParams p;
@@ -163,15 +202,16 @@ static su2_status launch_learned_phase(su2_lattice *lat, int mu, int parity)
     p.gate = lat->learned_ctl;
     p.acc_slots = lat->accept_slots;
     p.sweep_slots = lat->accept_slots + 8 * kAcceptSlots;
-    const int grid = (p.g.vh + kLearnThreads - 1) / kLearnThreads;
     const size_t smem = sizeof(float) * (size_t)p.G * learned::kParams;
+    const int want = (p.g.vh + kLearnThreads - 1) / kLearnThreads;
+    cudaError_t e;
     switch (mu) {
-    case 0: learned_phase_kernel<0><<<grid, kLearnThreads, smem, lat->stream>>>(p); break;
-    case 1: learned_phase_kernel<1><<<grid, kLearnThreads, smem, lat->stream>>>(p); break;
-    case 2: learned_phase_kernel<2><<<grid, kLearnThreads, smem, lat->stream>>>(p); break;
-    default: learned_phase_kernel<3><<<grid, kLearnThreads, smem, lat->stream>>>(p); break;
+    case 0: e = launch_persistent(learned_phase_kernel<0>, p, want, smem, lat); break;
+    case 1: e = launch_persistent(learned_phase_kernel<1>, p, want, smem, lat); break;
+    case 2: e = launch_persistent(learned_phase_kernel<2>, p, want, smem, lat); break;
+    default: e = launch_persistent(learned_phase_kernel<3>, p, want, smem, lat); break;
     }
-    SU2_CUDA(cudaGetLastError());
+    SU2_CUDA(e);
     return SU2_OK;
 }
 
@@ -270,7 +310,9 @@ su2_status su2_learned_generate(su2_lattice *lat, int nsweeps, int measure_every
     for (int s = 1; s <= nsweeps; ++s) {
         for (int mu = 0; mu < 4; ++mu)
             for (int parity = 0; parity < 2; ++parity) {
+                if ((st = timing_begin(lat)) != SU2_OK) return st;
                 if ((st = launch_learned_phase(lat, mu, parity)) != SU2_OK) return st;
+                if ((st = timing_end(lat)) != SU2_OK) return st;
                 if ((st = launch_hb_phase(lat, mu, parity, lat->sweep, lat->learned_ctl)) != SU2_OK) return st;
             }
         learned_decide_kernel<<<1, 32, 0, lat->stream>>>(lat->learned_ctl, lat->accept_slots + 8 * kAcceptSlots,
@@ -296,6 +338,9 @@ su2_status su2_learned_generate(su2_lattice *lat, int nsweeps, int measure_every
     su2_stats plain;
     memset(&plain, 0, sizeof plain);
     st = collect_stats(lat, &plain, (uint64_t)nsweeps);
+    double kms = 0.0;
+    su2_status st_t = timing_read(lat, &kms);
+    if (st == SU2_OK) st = st_t;
     if (stats) {
         memset(stats, 0, sizeof *stats);
         for (int ph = 0; ph < 8; ++ph) {
@@ -307,6 +352,9 @@ su2_status su2_learned_generate(su2_lattice *lat, int nsweeps, int measure_every
         stats->plain_sweeps = ctl[1];
         stats->learned_sweeps = ctl[2];
         stats->link_updates = (uint64_t)nsweeps * 4ull * (uint64_t)lat->vol;
+        stats->kernel_launches = (uint32_t)(8 * nsweeps);
+        stats->timed = lat->timing ? 1u : 0u;
+        stats->kernel_ms = kms;
     }
     return st;
 }

@@ -90,56 +90,80 @@ __device__ __forceinline__ void spline_params(const float (&o)[kOut], float *p)
     for (int i = 0; i <= kBins; ++i) p[2 * (kBins + 1) + i] = __fadd_rn(kMinDer, softplus(o[2 * kBins + i]));
 }
 
-__device__ __forceinline__ int bin_of(const float *k9, float v)
+// Parameter accessors: p(i) is spline parameter i (x_0..x_8, y_0..y_8, d_0..d_8).
+struct ArrayParams {
+    const float *v;
+    __device__ __forceinline__ float operator()(int i) const { return v[i]; }
+};
+
+// Linear interpolation between two table rows, element by element on demand
+// (p_i = r0_i + f (r1_i - r0_i) as one fused multiply-add), so no per-thread
+// copy of the 27 parameters is needed.
+struct InterpParams {
+    const float *r0, *r1;
+    float f;
+    __device__ __forceinline__ float operator()(int i) const { return __fmaf_rn(f, __fsub_rn(r1[i], r0[i]), r0[i]); }
+};
+
+template <class P>
+__device__ __forceinline__ int bin_of(const P &p, int base, float v)
 {
     int k = 0;
 #pragma unroll
     for (int j = 1; j < kBins; ++j)
-        if (k9[j] <= v) k = j;
+        if (p(base + j) <= v) k = j;
     return k;
 }
 
 // a = y_k + h (s xi^2 + d_k t)/den, den = s + (d_{k+1} + d_k - 2 s) t, t = xi (1 - xi),
 // f' = s^2 (d_{k+1} xi^2 + 2 s t + d_k (1 - xi)^2) / den^2.
-__device__ __forceinline__ float spline_eval(const float *p, int k, float xi, float &fprime)
+template <class P>
+__device__ __forceinline__ float spline_eval(const P &p, int k, float xi, float &fprime)
 {
-    const float *x = p, *y = p + kBins + 1, *d = p + 2 * (kBins + 1);
-    const float w = __fsub_rn(x[k + 1], x[k]);
-    const float h = __fsub_rn(y[k + 1], y[k]);
+    constexpr int Y = kBins + 1, D = 2 * (kBins + 1);
+    const float w = __fsub_rn(p(k + 1), p(k));
+    const float yk = p(Y + k);
+    const float h = __fsub_rn(p(Y + k + 1), yk);
+    const float dk = p(D + k), dk1 = p(D + k + 1);
     const float s = __fdiv_rn(h, w);
     const float t = __fmul_rn(xi, __fsub_rn(1.0f, xi));
-    const float sigma = __fsub_rn(__fadd_rn(d[k + 1], d[k]), __fmul_rn(2.0f, s));
+    const float sigma = __fsub_rn(__fadd_rn(dk1, dk), __fmul_rn(2.0f, s));
     const float den = __fmaf_rn(sigma, t, s);
-    const float num = __fmul_rn(h, __fmaf_rn(__fmul_rn(s, xi), xi, __fmul_rn(d[k], t)));
+    const float num = __fmul_rn(h, __fmaf_rn(__fmul_rn(s, xi), xi, __fmul_rn(dk, t)));
     const float omx = __fsub_rn(1.0f, xi);
-    const float m = __fmaf_rn(__fmul_rn(d[k + 1], xi), xi,
-                              __fmaf_rn(__fmul_rn(2.0f, s), t, __fmul_rn(__fmul_rn(d[k], omx), omx)));
+    const float m = __fmaf_rn(__fmul_rn(dk1, xi), xi, __fmaf_rn(__fmul_rn(2.0f, s), t, __fmul_rn(__fmul_rn(dk, omx), omx)));
     fprime = __fdiv_rn(__fmul_rn(__fmul_rn(s, s), m), __fmul_rn(den, den));
-    return __fadd_rn(y[k], __fdiv_rn(num, den));
+    return __fadd_rn(yk, __fdiv_rn(num, den));
 }
 
-__device__ __forceinline__ float spline_forward(const float *p, float z, float &fprime)
+template <class P>
+__device__ __forceinline__ float spline_forward(const P &p, float z, float &fprime)
 {
-    const int k = bin_of(p, z);
-    const float w = __fsub_rn(p[k + 1], p[k]);
-    float xi = __fdiv_rn(__fsub_rn(z, p[k]), w);
+    const int k = bin_of(p, 0, z);
+    const float xk = p(k);
+    const float w = __fsub_rn(p(k + 1), xk);
+    float xi = __fdiv_rn(__fsub_rn(z, xk), w);
     xi = xi < 0.0f ? 0.0f : (xi > 1.0f ? 1.0f : xi);
     const float a = spline_eval(p, k, xi, fprime);
     return a < -1.0f ? -1.0f : (a > 1.0f ? 1.0f : a);
 }
 
 // Inverse on bin k of y: alpha xi^2 + beta xi + c = 0, xi = 2c / (-beta - sqrt(beta^2 - 4 alpha c)).
-__device__ __forceinline__ float spline_inverse(const float *p, float a, float &fprime)
+template <class P>
+__device__ __forceinline__ float spline_inverse(const P &p, float a, float &fprime)
 {
-    const float *x = p, *y = p + kBins + 1, *d = p + 2 * (kBins + 1);
-    const int k = bin_of(y, a);
-    const float w = __fsub_rn(x[k + 1], x[k]);
-    const float h = __fsub_rn(y[k + 1], y[k]);
+    constexpr int Y = kBins + 1, D = 2 * (kBins + 1);
+    const int k = bin_of(p, Y, a);
+    const float xk = p(k);
+    const float w = __fsub_rn(p(k + 1), xk);
+    const float yk = p(Y + k);
+    const float h = __fsub_rn(p(Y + k + 1), yk);
+    const float dk = p(D + k), dk1 = p(D + k + 1);
     const float s = __fdiv_rn(h, w);
-    const float dy = __fsub_rn(a, y[k]);
-    const float sigma = __fsub_rn(__fadd_rn(d[k + 1], d[k]), __fmul_rn(2.0f, s));
-    const float alpha = __fmaf_rn(dy, sigma, __fmul_rn(h, __fsub_rn(s, d[k])));
-    const float beta = __fmaf_rn(-dy, sigma, __fmul_rn(h, d[k]));
+    const float dy = __fsub_rn(a, yk);
+    const float sigma = __fsub_rn(__fadd_rn(dk1, dk), __fmul_rn(2.0f, s));
+    const float alpha = __fmaf_rn(dy, sigma, __fmul_rn(h, __fsub_rn(s, dk)));
+    const float beta = __fmaf_rn(-dy, sigma, __fmul_rn(h, dk));
     const float c = __fmul_rn(-s, dy);
     float disc = __fmaf_rn(beta, beta, __fmul_rn(__fmul_rn(-4.0f, alpha), c));
     disc = disc > 0.0f ? disc : 0.0f;
@@ -147,23 +171,23 @@ __device__ __forceinline__ float spline_inverse(const float *p, float a, float &
     float xi = denom != 0.0f ? __fdiv_rn(__fmul_rn(2.0f, c), denom) : 0.0f;
     xi = xi < 0.0f ? 0.0f : (xi > 1.0f ? 1.0f : xi);
     spline_eval(p, k, xi, fprime);
-    return __fmaf_rn(xi, w, x[k]);
+    return __fmaf_rn(xi, w, xk);
 }
 
-// Parameters at network input s by linear interpolation between the two
-// table rows around it (s clamped to the table's range).
-__device__ __forceinline__ void table_params(const float *table, int G, float s_lo, float s_hi, float s,
-                                             float (&p)[kParams])
+// The two table rows around network input s (clamped to the table's range)
+// and the interpolation weight.
+__device__ __forceinline__ InterpParams table_params(const float *table, int G, float s_lo, float s_hi, float s)
 {
     const float inv_ds = __fdiv_rn((float)(G - 1), __fsub_rn(s_hi, s_lo));
     float u = __fmul_rn(__fsub_rn(s, s_lo), inv_ds);
     u = u < 0.0f ? 0.0f : (u > (float)(G - 1) ? (float)(G - 1) : u);
     int j = (int)floorf(u);
     if (j > G - 2) j = G - 2;
-    const float f = __fsub_rn(u, (float)j);
-    const float *r0 = table + j * kParams, *r1 = r0 + kParams;
-#pragma unroll
-    for (int i = 0; i < kParams; ++i) p[i] = __fmaf_rn(f, __fsub_rn(r1[i], r0[i]), r0[i]);
+    InterpParams ip;
+    ip.r0 = table + j * kParams;
+    ip.r1 = ip.r0 + kParams;
+    ip.f = __fsub_rn(u, (float)j);
+    return ip;
 }
 
 struct Proposal {
@@ -182,8 +206,7 @@ __device__ __forceinline__ int learned_link(const Proposal &pr, float beta, floa
                                             float4 &out)
 {
     const DrawSetup d = prepare_draw(v, beta);
-    float p[kParams];
-    table_params(pr.table, pr.G, pr.s_lo, pr.s_hi, __fmul_rn(__fsub_rn(d.bk, pr.mean), pr.scale), p);
+    const InterpParams p = table_params(pr.table, pr.G, pr.s_lo, pr.s_hi, __fmul_rn(__fsub_rn(d.bk, pr.mean), pr.scale));
     const float u0 = uniform01(w.x), u1 = uniform01(w.y), u2 = uniform01(w.z), u3 = uniform01(w.w);
     float fp_new, fp_cur;
     const float a_new = spline_forward(p, __fsub_rn(__fmul_rn(2.0f, u0), 1.0f), fp_new);

@@ -6,22 +6,26 @@
 // sum is binary64: warp shuffles, then one partial per block, then the last
 // block to finish adds the partials in block order, so the result does not
 // depend on the order in which blocks run.
+#include <algorithm>
+
 #include "observables.cuh"
 #include "su2_device.cuh"
 #include "su2_internal.h"
 
 namespace su2 {
 
-__global__ void __launch_bounds__(kReduceThreads) plaquette_kernel(const float4 *__restrict__ L, Geom g,
+__global__ void __launch_bounds__(kReduceThreads, 4) plaquette_kernel(const float4 *__restrict__ L, Geom g,
                                                                    double *__restrict__ partials,
                                                                    unsigned int *__restrict__ ticket,
                                                                    double *__restrict__ dst)
 {
     double acc = 0.0;
     const int64_t vol = 2 * (int64_t)g.vh;
+    // sites in lexicographic order (both parities interleaved), so the
+    // neighbour links a block reads were just read by its neighbours (L2)
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < vol; s += (int64_t)gridDim.x * blockDim.x) {
-        const int parity = s >= g.vh;
-        const int eo = (int)(s - (parity ? g.vh : 0));
+        const int eo = (int)(s >> 1);
+        const int parity = (int)(s & 1) ^ (eo_to_coord(g, eo, 0).lex != 2 * eo);
         const Coord x = eo_to_coord(g, eo, parity);
         acc += (double)site_plaquette(L, g, x, eo, parity);
     }
@@ -43,6 +47,7 @@ __global__ void __launch_bounds__(kReduceThreads) polyakov_kernel(const float4 *
         const int z = rest / g.ns;
         const int p0 = (x + y + z) & 1;
         float4 p = __ldg(L + link_index(g, 3, p0, xs >> 1));
+#pragma unroll 4
         for (int t = 1; t < g.nt; ++t) {
             const int64_t lex = (int64_t)t * g.vs + xs;
             p = qmul(p, __ldg(L + link_index(g, 3, (p0 + t) & 1, (int)(lex >> 1))));
@@ -56,7 +61,11 @@ __global__ void __launch_bounds__(kReduceThreads) polyakov_kernel(const float4 *
 su2_status launch_plaquette(su2_lattice *lat, double *dst)
 {
     const Geom g = geom_of(lat);
-    const int grid = grid_for(lat->vol, kReduceThreads, 152 * 8);
+    // persistent grid (4 blocks of 256 per SM): each thread sums several
+    // sites, one block reduction per block
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, lat->device);
+    const int grid = grid_for(lat->vol, kReduceThreads, std::min(lat->scratch.partials_cap, 4 * sms));
     plaquette_kernel<<<grid, kReduceThreads, 0, lat->stream>>>(lat->links, g, lat->scratch.partials,
                                                                lat->scratch.ticket, dst);
     SU2_CUDA(cudaGetLastError());

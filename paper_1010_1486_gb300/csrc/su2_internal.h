@@ -137,6 +137,11 @@ su2_status launch_reunitarize(su2_lattice *lat);
 su2_status launch_plaquette(su2_lattice *lat, double *dst);
 su2_status launch_polyakov(su2_lattice *lat, double *dst);
 su2_status launch_clear_counters(su2_lattice *lat);
+// CUDA events around a kernel on the lattice's stream (when timing is on),
+// and the summed duration of the recorded pairs (synchronises, then resets).
+su2_status timing_begin(su2_lattice *lat);
+su2_status timing_end(su2_lattice *lat);
+su2_status timing_read(su2_lattice *lat, double *ms);
 // Reads and clears the trial counters and flags (synchronises).
 su2_status collect_stats(su2_lattice *lat, su2_stats *stats, uint64_t sweeps);
 

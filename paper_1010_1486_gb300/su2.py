@@ -53,12 +53,14 @@ class su2_stats(ctypes.Structure):
 class su2_learned_stats(ctypes.Structure):
     _fields_ = [("link_updates", ctypes.c_uint64), ("accepted", ctypes.c_uint64 * 8),
                 ("plain_trials", ctypes.c_uint64 * 8), ("learned_sweeps", ctypes.c_uint32),
-                ("plain_sweeps", ctypes.c_uint32)]
+                ("plain_sweeps", ctypes.c_uint32), ("kernel_launches", ctypes.c_uint32),
+                ("timed", ctypes.c_uint32), ("kernel_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {"link_updates": self.link_updates, "accepted": list(self.accepted),
                 "plain_trials": list(self.plain_trials), "learned_sweeps": self.learned_sweeps,
-                "plain_sweeps": self.plain_sweeps}
+                "plain_sweeps": self.plain_sweeps, "kernel_launches": self.kernel_launches,
+                "timed": bool(self.timed), "kernel_ms": self.kernel_ms}
 
 
 class su2_state(ctypes.Structure):

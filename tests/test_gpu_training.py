@@ -124,3 +124,27 @@ def test_training_lowers_the_loss_and_lifts_acceptance():
         assert acc1 > 0.7 and acc1 > acc0 + 0.1, (acc0, acc1)
     finally:
         su2.su2_destroy(h)
+
+
+def test_learned_chain_reproduces_the_plain_plaquette():
+    """Exactness of the learned chain: same <P> as the plain heat bath within
+    the combined statistical error (Gamma-method errors), 8^4 at beta = 2.3."""
+    pytest.importorskip("torch")
+    from paper_1010_1486_gb300.analysis import tau_int
+
+    ns = nt = 8
+    h = su2.su2_create(ns, nt, 2.3, 31, su2.SU2_HOT)
+    try:
+        su2.su2_heatbath_sweep(h, 100)
+        pairs = learn.collect(h, ns, nt, 100_000)
+        w, _, s_lo, s_hi = learn.train(pairs, steps=400, batch=4096, lr=3e-3)
+        plain, _, _ = su2.su2_generate(h, 4000, 1, 0)
+        su2.su2_set_proposal(h, w, s_lo, s_hi, 256)
+        lp, _, st = su2.su2_learned_generate(h, 4000, 1, 0.7)
+    finally:
+        su2.su2_destroy(h)
+    _, _, _, e_plain = tau_int(plain)
+    t_l, _, _, e_learn = tau_int(lp)
+    diff = lp.mean() - plain.mean()
+    assert abs(diff) < 4 * np.hypot(e_plain, e_learn), (plain.mean(), lp.mean(), e_plain, e_learn)
+    assert sum(st["accepted"]) / (st["learned_sweeps"] * 4 * ns ** 4) > 0.7
