@@ -306,6 +306,13 @@ def compare_forms(args, dist, lat, su2, torch, stream, tau_int):
     ms_p, (_, _, st_p) = timed(stream, torch, dist, lambda: su2.su2_generate(lat, args.steps, 1, 0))
     plain_phase_s = st_p["kernel_ms"] / st_p["kernel_launches"] * 1e-3
     value_plain = dist.reduce(float(st_p["link_updates"]), "sum") / (ms_p * 1e-3)
+    # plain with the Kennedy-Pendleton sampler, timed
+    su2.su2_set_sampler(lat, su2.SU2_SAMPLER_KP)
+    su2.su2_generate(lat, 2, 1, 0)
+    ms_k, (_, _, st_k) = timed(stream, torch, dist, lambda: su2.su2_generate(lat, args.steps, 1, 0))
+    su2.su2_set_sampler(lat, su2.SU2_SAMPLER_CREUTZ)
+    kp_phase_s = st_k["kernel_ms"] / st_k["kernel_launches"] * 1e-3
+    value_kp = dist.reduce(float(st_k["link_updates"]), "sum") / (ms_k * 1e-3)
     # learned, timed
     su2.su2_learned_generate(lat, 2, 1, 0.7)
     ms_l, (_, _, st_l) = timed(stream, torch, dist, lambda: su2.su2_learned_generate(lat, args.steps, 1, 0.7))
@@ -320,6 +327,12 @@ def compare_forms(args, dist, lat, su2, torch, stream, tau_int):
                      "roofline": {"bound": "hbm", "kernel": "hb_phase_kernel",
                                   "achieved": BYTES_PER_UPDATE * (VOL // 2) / plain_phase_s / 1e9, "peak": peak,
                                   "unit": "GB/s", "avg_launch_us": plain_phase_s * 1e6}},
+           "plain_kennedy_pendleton": {
+               "value": value_kp, "unit": UNIT, "ms_per_step": ms_k / args.steps,
+               "trials_per_update": sum(st_k["trials"]) / st_k["link_updates"],
+               "roofline": {"bound": "hbm", "kernel": "kp_phase_kernel",
+                            "achieved": BYTES_PER_UPDATE * (VOL // 2) / kp_phase_s / 1e9, "peak": peak,
+                            "unit": "GB/s", "avg_launch_us": kp_phase_s * 1e6}},
            "learned": {"value": value_learned, "unit": UNIT, "ms_per_step": ms_l / args.steps,
                        "acceptance": sum(st_l["accepted"]) / max(1, proposals),
                        "learned_sweeps": st_l["learned_sweeps"], "fallback_sweeps": st_l["plain_sweeps"],
@@ -331,19 +344,25 @@ def compare_forms(args, dist, lat, su2, torch, stream, tau_int):
                        "training": {"pairs": args.learned_pairs, "steps": args.train_steps, "batch": 4096,
                                     "collect_s": t1 - t0, "train_s": t2 - t1,
                                     "loss_first": float(losses[:10].mean()), "loss_last": float(losses[-50:].mean())}}}
-    for form in ("plain", "learned"):
+    for form in ("plain", "plain_kennedy_pendleton", "learned"):
         r = out[form]["roofline"]
         r["frac"] = r["achieved"] / peak
     if args.tau_sweeps > 0:
         nblk = 8
         per = max(50, args.tau_sweeps // nblk)
-        plain_blocks, learned_blocks = [], []
+        plain_blocks, learned_blocks, kp_blocks = [], [], []
         for k in range(nblk):
             plain_blocks.append(su2.su2_generate(lat, per, 1, 0)[0].copy())
             learned_blocks.append(su2.su2_learned_generate(lat, per, 1, 0.7)[0].copy())
+            su2.su2_set_sampler(lat, su2.SU2_SAMPLER_KP)
+            kp_blocks.append(su2.su2_generate(lat, per, 1, 0)[0].copy())
+            su2.su2_set_sampler(lat, su2.SU2_SAMPLER_CREUTZ)
         plain_blocks.append(su2.su2_generate(lat, per, 1, 0)[0].copy())
         tau_p = np.mean([tau_int(b)[0] for b in plain_blocks])
         tau_l = np.mean([tau_int(b)[0] for b in learned_blocks])
+        tau_k = np.mean([tau_int(b)[0] for b in kp_blocks])
+        out["plain_kennedy_pendleton"]["tau_int"] = float(tau_k)
+        out["plain_kennedy_pendleton"]["value_tau_adjusted"] = value_kp / (2 * tau_k)
         d = np.array([learned_blocks[k].mean() - 0.5 * (plain_blocks[k].mean() + plain_blocks[k + 1].mean())
                       for k in range(nblk)])
         se = d.std(ddof=1) / np.sqrt(nblk)
@@ -357,6 +376,7 @@ def compare_forms(args, dist, lat, su2, torch, stream, tau_int):
                                   "learned_minus_plain": float(d.mean()), "stderr": float(se),
                                   "sigma": float(d.mean() / se) if se > 0 else None}
         out["value_tau_adjusted"] = {"plain": out["plain"]["value_tau_adjusted"],
+                                     "plain_kennedy_pendleton": out["plain_kennedy_pendleton"]["value_tau_adjusted"],
                                      "learned": out["learned"]["value_tau_adjusted"],
                                      "convention": "link updates/s / (2 tau_int(plaquette)), tau_int = 1/2 + sum rho"}
     return out

@@ -118,6 +118,16 @@ su2_status su2_heatbath_phase(su2_lattice *lat, int mu, int parity);
 su2_status su2_generate(su2_lattice *lat, int nsweeps, int measure_every, int reunit_every, double *plaq,
                         double *poly, su2_stats *stats);
 
+/* a0 sampler of the plain heat bath.  SU2_SAMPLER_CREUTZ (default): Creutz's
+ * rejection method (the method the paper cites).  SU2_SAMPLER_KP: the
+ * Kennedy-Pendleton method (Phys. Lett. B 156 (1985) 393) for links with
+ * beta k >= 2 -- same law, about one trial per link at large beta k, drawn
+ * from its own Philox stream -- and Creutz's method below beta k = 2.  The
+ * choice applies to the following sweeps (and to the learned fallback). */
+#define SU2_SAMPLER_CREUTZ 0
+#define SU2_SAMPLER_KP 1
+su2_status su2_set_sampler(su2_lattice *lat, int sampler);
+
 /* a <- a / |a| for every link (the links drift from |a| = 1 by rounding). */
 su2_status su2_reunitarize(su2_lattice *lat);
 
@@ -174,6 +184,9 @@ typedef struct {
     uint64_t plain_trials[8];  /* Creutz trials of the fallback sweeps       */
     uint32_t learned_sweeps;   /* sweeps done with the learned proposal      */
     uint32_t plain_sweeps;     /* fallback sweeps done with the heat bath    */
+    uint32_t kernel_launches;  /* learned phase launches (8 per sweep)       */
+    uint32_t timed;            /* 1 if kernel_ms is valid (su2_set_timing)   */
+    double kernel_ms;          /* summed device time of the learned phase kernels */
 } su2_learned_stats;
 
 /* Installs the proposal: the network is evaluated (binary32, on the device)

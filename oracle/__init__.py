@@ -83,6 +83,9 @@ def _load():
             "orc_max_threads": (i32, []),
             "orc_creutz_a0_v": (None, [f32, u64, u32, u32, i64, P, P]),
             "orc_heatbath_link_v": (None, [f32, P, u64, u32, u32, i32, i32, i64, P, P]),
+            "orc_heatbath_sweep_kp": (i64, [i32, i32, f64, u64, u32, P, P, i32]),
+            "orc_heatbath_phase_kp": (i64, [i32, i32, f64, u64, u32, i32, i32, P, ctypes.POINTER(i64), i32]),
+            "orc_kp_a0_v": (None, [f32, u64, u32, i64, P, P]),
             "orc_mlp_forward": (None, [P, f32, P]),
             "orc_spline_params": (None, [P, P]),
             "orc_spline_forward": (f32, [P, f32, P]),
@@ -227,6 +230,23 @@ def heatbath_sweep(ns: int, nt: int, beta: float, seed: int, sweep: int, links: 
     if err:
         raise RuntimeError(f"{err} links hit the trial cap")
     return trials
+
+
+def heatbath_sweep_kp(ns: int, nt: int, beta: float, seed: int, sweep: int, links: np.ndarray,
+                      nthreads: int = 1) -> np.ndarray:
+    """One sweep with the Kennedy-Pendleton sampler (Creutz below beta k = 2)."""
+    trials = np.zeros(8, dtype=np.int64)
+    err = _load().orc_heatbath_sweep_kp(ns, nt, beta, seed, sweep, _ptr(links), _ptr(trials), nthreads)
+    if err:
+        raise RuntimeError(f"{err} links hit the trial cap")
+    return trials
+
+
+def kp_a0_many(bk: float, seed: int, n: int, eo0: int = 0):
+    a0 = np.zeros(n, dtype=np.float32)
+    t = np.zeros(n, dtype=np.int32)
+    _load().orc_kp_a0_v(bk, seed, eo0, n, _ptr(a0), _ptr(t))
+    return a0, t
 
 
 def heatbath_phase(ns: int, nt: int, beta: float, seed: int, sweep: int, mu: int, parity: int,

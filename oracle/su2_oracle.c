@@ -632,3 +632,105 @@ void orc_heatbath_link_v(float beta, const float v[4], uint64_t seed, uint32_t e
     for (int64_t i = 0; i < n; ++i)
         trials[i] = orc_heatbath_link(beta, v, seed, eo, sweep0 + (uint32_t)i, parity, mu, out + 4 * i);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Kennedy-Pendleton a0 sampler (Phys. Lett. B 156 (1985) 393), the same    */
+/* heat-bath law as Creutz's method with near-unit acceptance at large       */
+/* beta k.  With a0 = 1 - 2u the law of u is u^{1/2} sqrt(1 - u) exp(-2 beta k u) */
+/* on [0, 1]: u is drawn from the Gamma(3/2) part,                            */
+/* u = -(ln r1 + cos^2(2 pi r2) ln r3) / (2 beta k) (an exponential plus half */
+/* a squared Box-Muller normal), and accepted iff u <= 1 and r4^2 <= 1 - u.  */
+/* Trial t uses the four uniforms of block t of the KP stream (kind 5).      */
+/* Below beta k = 2 (where KP accepts poorly) the link is drawn by Creutz's  */
+/* method exactly as orc_heatbath_link does.                                 */
+/* ------------------------------------------------------------------------ */
+#define ORC_KP_MIN_BK 2.0f
+enum { ORC_KIND_KP = 5 };
+
+int orc_heatbath_link_kp(float beta, const float v[4], uint64_t seed, uint32_t eo, uint32_t sweep, int parity, int mu,
+                         float out[4])
+{
+    float k = sqrtf(dot4(v[0], v[0], v[1], v[1], v[2], v[2], v[3], v[3]));
+    const float bk = beta * k;
+    if (!(bk >= ORC_KP_MIN_BK)) return orc_heatbath_link(beta, v, seed, eo, sweep, parity, mu, out);
+    const float inv_k = 1.0f / k;
+    const float ut[4] = {v[0] * inv_k, -v[1] * inv_k, -v[2] * inv_k, -v[3] * inv_k};
+    const float two_bk = 2.0f * bk;
+    float a0 = 0.0f;
+    int trials = 0;
+    for (int t = 0; t < ORC_MAX_TRIALS; ++t) {
+        float u[4];
+        draw_block(seed, eo, sweep, ORC_KIND_KP, parity, mu, (uint32_t)t, u);
+        float sn, cs;
+        orc_sincos2pi(u[1], &sn, &cs);
+        const float num = fmaf(cs * cs, orc_logf(u[2]), orc_logf(u[0]));
+        const float lam2 = -num / two_bk;
+        if (lam2 <= 1.0f && u[3] * u[3] <= 1.0f - lam2) {
+            a0 = fmaf(-2.0f, lam2, 1.0f);
+            trials = t + 1;
+            break;
+        }
+    }
+    if (trials == 0) return -1;
+    float d[4];
+    draw_block(seed, eo, sweep, ORC_KIND_DIRECTION, parity, mu, 0u, d);
+    float r = sqrtf(fmaf(-a0, a0, 1.0f));
+    float c = 2.0f * d[0] - 1.0f;
+    float st = sqrtf(fmaf(-c, c, 1.0f));
+    float sn, cs;
+    orc_sincos2pi(d[1], &sn, &cs);
+    float rs = r * st;
+    float a[4] = {a0, rs * cs, rs * sn, r * c};
+    orc_quat_mul(a, ut, out);
+    return trials;
+}
+
+int64_t orc_heatbath_phase_kp(int ns, int nt, double beta, uint64_t seed, uint32_t sweep, int mu, int p, float *links,
+                              int64_t *trials_out, int nthreads)
+{
+    int64_t vol = (int64_t)ns * ns * ns * nt;
+    float beta_f = (float)beta;
+    int64_t trials = 0, errors = 0;
+#ifdef _OPENMP
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(static) reduction(+ : trials, errors) num_threads(nthreads)
+#endif
+    for (int64_t s = 0; s < vol; ++s) {
+        if (site_parity(s, ns) != p) continue;
+        float v[4];
+        orc_staple(ns, nt, links, s, mu, v);
+        float *l = links + (s * 4 + mu) * 4;
+        int n = orc_heatbath_link_kp(beta_f, v, seed, (uint32_t)(s >> 1), sweep, p, mu, l);
+        if (n < 0) {
+            errors += 1;
+            trials += ORC_MAX_TRIALS;
+        } else {
+            trials += n;
+        }
+    }
+    (void)nthreads;
+    *trials_out = trials;
+    return errors;
+}
+
+int64_t orc_heatbath_sweep_kp(int ns, int nt, double beta, uint64_t seed, uint32_t sweep, float *links,
+                              int64_t trials[8], int nthreads)
+{
+    int64_t errors = 0;
+    for (int mu = 0; mu < 4; ++mu)
+        for (int p = 0; p < 2; ++p)
+            errors += orc_heatbath_phase_kp(ns, nt, beta, seed, sweep, mu, p, links, &trials[2 * mu + p], nthreads);
+    return errors;
+}
+
+/* n draws of a0 at fixed beta k with the Kennedy-Pendleton sampler (draw i
+ * uses even/odd index eo0 + i). */
+void orc_kp_a0_v(float bk, uint64_t seed, uint32_t eo0, int64_t n, float *a0, int32_t *trials)
+{
+    const float v[4] = {bk, 0.0f, 0.0f, 0.0f};
+    for (int64_t i = 0; i < n; ++i) {
+        float out[4];
+        trials[i] = orc_heatbath_link_kp(1.0f, v, seed, eo0 + (uint32_t)i, 0u, 0, 0, out);
+        a0[i] = out[0];
+    }
+}

@@ -244,6 +244,7 @@ static cudaError_t launch_hb(const HbParams &p, int device, cudaStream_t stream)
 
 su2_status launch_hb_phase(su2_lattice *lat, int mu, int parity, uint32_t sweep, const unsigned int *gate)
 {
+    if (lat->sampler == SU2_SAMPLER_KP) return launch_kp_phase(lat, mu, parity, sweep, gate);
     HbParams p;
     p.gate = gate;
     p.links = lat->links;

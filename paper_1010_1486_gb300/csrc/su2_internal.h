@@ -38,6 +38,7 @@ struct su2_lattice {
     double beta = 0.0;
     uint64_t seed = 0;
     uint32_t sweep = 0;
+    int sampler = 0;  // SU2_SAMPLER_CREUTZ or SU2_SAMPLER_KP
     int device = 0;
     cudaStream_t stream = nullptr;
 
@@ -132,6 +133,7 @@ su2_status launch_cold_start(su2_lattice *lat);
 su2_status launch_hot_start(su2_lattice *lat);
 su2_status launch_hb_phase(su2_lattice *lat, int mu, int parity, uint32_t sweep,
                            const unsigned int *gate = nullptr);
+su2_status launch_kp_phase(su2_lattice *lat, int mu, int parity, uint32_t sweep, const unsigned int *gate);
 su2_status launch_reunitarize(su2_lattice *lat);
 // Observables: write the value into *dst (device memory) without synchronising.
 su2_status launch_plaquette(su2_lattice *lat, double *dst);

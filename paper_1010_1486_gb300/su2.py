@@ -27,6 +27,7 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 SU2_COLD, SU2_HOT = 0, 1
+SU2_SAMPLER_CREUTZ, SU2_SAMPLER_KP = 0, 1
 STATUS = {0: "SU2_OK", 1: "SU2_E_INVAL", 2: "SU2_E_NOMEM", 3: "SU2_E_CUDA", 4: "SU2_E_SAMPLER",
           5: "SU2_E_DEVICE_TIMEOUT", 6: "SU2_E_NUMERIC", 7: "SU2_E_STATE"}
 
@@ -90,6 +91,7 @@ _SIGS = {
     "su2_set_beta": [_P, _f64],
     "su2_device_links": [_P, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_size_t)],
     "su2_set_timing": [_P, _i32],
+    "su2_set_sampler": [_P, _i32],
     "su2_selftest_philox": [_P, _P, ctypes.c_size_t],
     "su2_selftest_math": [_i32, _P, _P, _P, ctypes.c_size_t],
     "su2_plaquette_noalloc": [_P, _i32, _i32, _P, _P],
@@ -277,6 +279,10 @@ def su2_device_links(lat: int):
     n = ctypes.c_size_t()
     _check(_lib.su2_device_links(lat, ctypes.byref(p), ctypes.byref(n)), "su2_device_links")
     return p.value, n.value
+
+
+def su2_set_sampler(lat: int, sampler: int) -> None:
+    _check(_lib.su2_set_sampler(lat, int(sampler)), "su2_set_sampler")
 
 
 def su2_set_timing(lat: int, enable: bool) -> None:

@@ -253,3 +253,33 @@ def test_full_size_48_hot_start_one_sweep(lattice):
     assert st["trials"] == [int(t) for t in tr]
     assert obs_close(su2.su2_plaquette(lat.h), oracle.plaquette(ns, nt, ref))
     assert obs_close(su2.su2_polyakov(lat.h), oracle.polyakov(ns, nt, ref))
+
+
+# ------------------------------------------------ Kennedy-Pendleton sampler
+@pytest.mark.parametrize("ns,nt,beta,start", [(8, 8, 2.3, su2.SU2_HOT), (6, 4, 6.0, su2.SU2_HOT),
+                                              (4, 6, 0.4, su2.SU2_COLD), (12, 4, 2.5, su2.SU2_COLD)])
+def test_kennedy_pendleton_sweeps_link_for_link(lattice, ns, nt, beta, start):
+    seed = 60 + ns
+    lat = lattice(ns, nt, beta, seed, start)
+    su2.su2_set_sampler(lat.h, su2.SU2_SAMPLER_KP)
+    ref = oracle.hot_start(ns, nt, seed) if start == su2.SU2_HOT else oracle.cold_start(ns, nt)
+    for s in range(4):
+        st = su2.su2_heatbath_sweep(lat.h, 1, stats=True)
+        tr = oracle.heatbath_sweep_kp(ns, nt, beta, seed, s, ref, nthreads=nthreads())
+        assert st["trials"] == [int(t) for t in tr], s
+        assert np.array_equal(lat.links(), ref), s
+    assert obs_close(su2.su2_plaquette(lat.h), oracle.plaquette(ns, nt, ref))
+
+
+def test_kennedy_pendleton_full_size_48(lattice):
+    ns = nt = 48
+    lat = lattice(ns, nt, 6.0, 3)
+    su2.su2_heatbath_sweep(lat.h, 2)
+    ref = lat.links()
+    su2.su2_set_sampler(lat.h, su2.SU2_SAMPLER_KP)
+    st = su2.su2_heatbath_sweep(lat.h, 1, stats=True)
+    tr = oracle.heatbath_sweep_kp(ns, nt, 6.0, 3, 2, ref, nthreads=nthreads())
+    assert st["trials"] == [int(t) for t in tr]
+    assert np.array_equal(lat.links(), ref)
+    # about one trial per link at beta = 6
+    assert sum(tr) / (4 * ns ** 3 * nt) < 1.2

@@ -128,3 +128,35 @@ def test_tau_int_on_ar1_series():
     tau0, _, _, err0 = tau_int(rng.normal(size=100_000))
     assert abs(tau0 - 0.5) < 0.05
     assert abs(err0 - 1 / np.sqrt(100_000)) < 0.1 / np.sqrt(100_000)
+
+
+# ------------------------------------------------- Kennedy-Pendleton sampler
+@pytest.mark.parametrize("bk", [2.0, 5.0, 15.0, 36.0])
+def test_kennedy_pendleton_exact_distribution(bk):
+    a0, trials = oracle.kp_a0_many(bk, seed=77 + int(bk), n=N_DRAWS)
+    assert trials.min() >= 1
+    assert chi2_pvalue_a0(a0.astype(np.float64), float(np.float32(bk))) > 1e-3
+    m = a0.astype(np.float64).mean()
+    sd = a0.astype(np.float64).std() / np.sqrt(N_DRAWS)
+    assert abs(m - mean_a0(float(np.float32(bk)))) < 5 * sd
+    # far fewer trials than Creutz's method where beta k is large
+    if bk >= 15:
+        assert trials.mean() < 1.1 and trials.mean() < 0.5 / creutz_acceptance(bk)
+
+
+def test_kennedy_pendleton_chain_matches_creutz_chain():
+    """Both samplers draw the same heat-bath law: equal <P> at beta = 2.3."""
+    ns, nt, beta = 6, 6, 2.3
+    res = []
+    for sweep_fn, seed in ((oracle.heatbath_sweep, 41), (oracle.heatbath_sweep_kp, 42)):
+        links = oracle.hot_start(ns, nt, seed)
+        series = []
+        for s in range(1200):
+            sweep_fn(ns, nt, beta, seed, s, links, nthreads=min(8, oracle.max_threads()))
+            if s >= 200:
+                series.append(oracle.plaquette(ns, nt, links))
+        series = np.array(series)
+        _, _, _, err = tau_int(series)
+        res.append((series.mean(), err))
+    (m1, e1), (m2, e2) = res
+    assert abs(m1 - m2) < 4 * np.hypot(e1, e2), res
