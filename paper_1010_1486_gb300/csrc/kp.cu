@@ -1,8 +1,8 @@
 // kp.cu -- heat-bath phase with the Kennedy-Pendleton a0 sampler
 // (Phys. Lett. B 156 (1985) 393).  Same law as Creutz's method (Sec. 2
-// heat bath), but at large beta k nearly every trial is accepted, so there
-// is no rejection loop to balance: one thread per link, persistent grid, the
-// 18 staple links of the next link loaded before the draw of the current one.
+// heat bath), but at large beta k nearly every trial is accepted: one thread
+// per link, persistent grid, the staple of the next link loaded during the
+// draw of the current one, and the few rejected links retried warp-wide.
 //
 // With a0 = 1 - 2u the law of u is u^{1/2} sqrt(1 - u) exp(-2 beta k u) on
 // [0, 1]; a trial draws u = -(ln r1 + cos^2(2 pi r2) ln r3) / (2 beta k) and
@@ -17,6 +17,10 @@
 namespace su2 {
 
 constexpr int kKpThreads = 256;
+#ifndef SU2_KP_MIN_BLOCKS
+#define SU2_KP_MIN_BLOCKS 3
+#endif
+constexpr int kKpMinBlocks = SU2_KP_MIN_BLOCKS;  // blocks per SM the register budget is set for
 constexpr float kKpMinBk = 2.0f;
 constexpr uint32_t kKennedyPendleton = 5u;
 
@@ -32,81 +36,165 @@ struct KpParams {
     const unsigned int *gate;  // skip the phase while *gate == 1 (learned sweeps)
 };
 
-// Returns the number of trials (0: cap hit, out unchanged).
-template <int MU>
-__device__ __forceinline__ int kp_draw(float4 v, float beta, const RoundKeys &rk, uint32_t eo, uint32_t sweep,
-                                       uint32_t parity, float4 &out)
+// One trial (block t of the KP stream): true and a0 if accepted.
+__device__ __forceinline__ bool kp_trial(uint4 w, float two_bk, float &a0)
 {
-    const float k = __fsqrt_rn(qnorm2(v));
-    const float bk = __fmul_rn(beta, k);
-    if (!(bk >= kKpMinBk)) return heatbath_draw(v, beta, rk, eo, sweep, parity, MU, out);
-    const float inv_k = __fdiv_rn(1.0f, k);
-    const float4 ut = make_float4(__fmul_rn(v.x, inv_k), __fmul_rn(-v.y, inv_k), __fmul_rn(-v.z, inv_k),
-                                  __fmul_rn(-v.w, inv_k));
-    const float two_bk = __fmul_rn(2.0f, bk);
-    const uint32_t sw = stream_word(kKennedyPendleton, parity, MU);
-    float a0 = 0.0f;
-    int trials = 0;
-    for (int t = 0; t < kMaxTrials; ++t) {
-        const uint4 w = philox_rk(make_uint4(eo, sweep, sw, (uint32_t)t), rk);
-        float sn, cs;
-        sincos_2pi(uniform01(w.y), sn, cs);
-        const float num = __fmaf_rn(__fmul_rn(cs, cs), log_series(uniform01(w.z)), log_series(uniform01(w.x)));
-        const float lam2 = __fdiv_rn(-num, two_bk);
-        const float r4 = uniform01(w.w);
-        if (lam2 <= 1.0f && __fmul_rn(r4, r4) <= __fsub_rn(1.0f, lam2)) {
-            a0 = __fmaf_rn(-2.0f, lam2, 1.0f);
-            trials = t + 1;
-            break;
-        }
+    float sn, cs;
+    sincos_2pi(uniform01(w.y), sn, cs);
+    const float num = __fmaf_rn(__fmul_rn(cs, cs), log_series(uniform01(w.z)), log_series(uniform01(w.x)));
+    const float lam2 = __fdiv_rn(-num, two_bk);
+    const float r4 = uniform01(w.w);
+    if (lam2 <= 1.0f && __fmul_rn(r4, r4) <= __fsub_rn(1.0f, lam2)) {
+        a0 = __fmaf_rn(-2.0f, lam2, 1.0f);
+        return true;
     }
-    if (trials == 0) return 0;
-    out = direction_update(a0, ut, philox_rk(make_uint4(eo, sweep, stream_word(kDirection, parity, MU), 0u), rk));
-    return trials;
+    return false;
 }
 
+constexpr int kKpWarps = kKpThreads / 32;
+constexpr int kRetryCap = 64;  // per warp: at most 31 left over + 32 pushed by one round
+
+// Warp w of the grid takes the rounds of 32 consecutive links w, w + W, ...
+// (W warps).  Each loop iteration (three per round) issues the six loads of
+// one nu-group of the next round, does one third of the current round's
+// draw, then folds the loaded group into the next round's staple, so 24
+// registers of loads are in flight and the draw's arithmetic covers their
+// latency:
+//   part 0  k, beta k, U~^dag; the first trial's Philox block;
+//   part 1  the first trial (Creutz's method instead if beta k < 2);
+//   part 2  the direction and the store of every accepted link.
+// A link whose first trial is rejected is parked in the warp's retry queue
+// in shared memory (U~^dag, beta k, index).  Once 32 links wait, the whole
+// warp runs their further trials 1, 2, ... together, so no warp spins on one
+// lane's rejections.  Every draw depends only on the link's counters, so the
+// phase computes exactly the one-thread-per-link definition.
 template <int MU>
-__global__ void __launch_bounds__(kKpThreads) kp_phase_kernel(const KpParams p)
+__global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(const KpParams p)
 {
     if (p.gate != nullptr && *(volatile const unsigned int *)p.gate == 1u) return;
-    const int stride = gridDim.x * blockDim.x;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ float4 s_ut[kKpWarps][kRetryCap];
+    __shared__ float s_bk[kKpWarps][kRetryCap];
+    __shared__ int s_eo[kKpWarps][kRetryCap];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const unsigned int lanes_below = (1u << lane) - 1u;
+    const int stride = gridDim.x * kKpThreads;
+    const uint32_t sw_kp = stream_word(kKennedyPendleton, (uint32_t)p.parity, MU);
+    const uint32_t sw_dir = stream_word(kDirection, (uint32_t)p.parity, MU);
     unsigned int trials = 0;
-    NuLinks n0, n1, n2;
-    if (i < p.g.vh) {
-        const Coord x = eo_to_coord(p.g, i, p.parity);
+    int queued = 0;  // warp-uniform length of the retry queue
+
+    // Trials 1, 2, ... of the queue entry of this lane (lane < n), then the
+    // direction and the store.
+    auto retry = [&](int first, int n) {
+        if (lane < n) {
+            const int q = first + lane;
+            const float4 ut = s_ut[wib][q];
+            const float two_bk = __fmul_rn(2.0f, s_bk[wib][q]);
+            const int eo = s_eo[wib][q];
+            float a0 = 0.0f;
+            int t = 1;
+            for (; t < kMaxTrials; ++t)
+                if (kp_trial(philox_rk(make_uint4((uint32_t)eo, p.sweep, sw_kp, (uint32_t)t), p.rk), two_bk, a0))
+                    break;
+            if (t < kMaxTrials) {
+                p.links[link_index(p.g, MU, p.parity, eo)] =
+                    direction_update(a0, ut, philox_rk(make_uint4((uint32_t)eo, p.sweep, sw_dir, 0u), p.rk));
+                trials += (unsigned int)(t + 1);
+            } else {
+                atomicAdd(&p.flags[0], 1u);  // trial cap: the link keeps its old value
+                trials += (unsigned int)kMaxTrials;
+            }
+        }
+        __syncwarp();
+    };
+
+    int base = blockIdx.x * kKpThreads + (wib << 5);
+    int cur = base + lane;
+    float4 v_cur = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (cur < p.g.vh) {
+        const Coord x = eo_to_coord(p.g, cur, p.parity);
         const int lex_p = lex_fwd(p.g, x.lex, x.c[MU], MU);
-        n0 = load_nu<MU, OtherDir<MU, 0>::value>(p.links, p.g, x, lex_p, p.parity);
-        n1 = load_nu<MU, OtherDir<MU, 1>::value>(p.links, p.g, x, lex_p, p.parity);
-        n2 = load_nu<MU, OtherDir<MU, 2>::value>(p.links, p.g, x, lex_p, p.parity);
+        v_cur = add_nu_terms(v_cur, load_nu<MU, OtherDir<MU, 0>::value>(p.links, p.g, x, lex_p, p.parity));
+        v_cur = add_nu_terms(v_cur, load_nu<MU, OtherDir<MU, 1>::value>(p.links, p.g, x, lex_p, p.parity));
+        v_cur = add_nu_terms(v_cur, load_nu<MU, OtherDir<MU, 2>::value>(p.links, p.g, x, lex_p, p.parity));
     }
-    while (i < p.g.vh) {
-        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        v = add_nu_terms(v, n0);
-        v = add_nu_terms(v, n1);
-        v = add_nu_terms(v, n2);
-        const int inext = i + stride;
-        if (inext < p.g.vh) {
-            const Coord x = eo_to_coord(p.g, inext, p.parity);
-            const int lex_p = lex_fwd(p.g, x.lex, x.c[MU], MU);
-            n0 = load_nu<MU, OtherDir<MU, 0>::value>(p.links, p.g, x, lex_p, p.parity);
-            n1 = load_nu<MU, OtherDir<MU, 1>::value>(p.links, p.g, x, lex_p, p.parity);
-            n2 = load_nu<MU, OtherDir<MU, 2>::value>(p.links, p.g, x, lex_p, p.parity);
+    while (base < p.g.vh) {  // warp-uniform
+        const bool valid = cur < p.g.vh;
+        const int nxt = cur + stride;
+        const bool has_next = nxt < p.g.vh;
+        Coord xn;
+        int lex_pn = 0;
+        float4 v_next = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        // ---- part 0
+        NuLinks nl;
+        if (has_next) {
+            xn = eo_to_coord(p.g, nxt, p.parity);
+            lex_pn = lex_fwd(p.g, xn.lex, xn.c[MU], MU);
+            nl = load_nu<MU, OtherDir<MU, 0>::value>(p.links, p.g, xn, lex_pn, p.parity);
         }
+        const float k = __fsqrt_rn(qnorm2(v_cur));
+        const float bk = __fmul_rn(p.beta, k);
+        const bool use_kp = bk >= kKpMinBk;
+        float4 ut = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+        uint4 w = make_uint4(0u, 0u, 0u, 0u);
+        if (valid && use_kp) {
+            const float inv_k = __fdiv_rn(1.0f, k);
+            ut = make_float4(__fmul_rn(v_cur.x, inv_k), __fmul_rn(-v_cur.y, inv_k), __fmul_rn(-v_cur.z, inv_k),
+                             __fmul_rn(-v_cur.w, inv_k));
+            w = philox_rk(make_uint4((uint32_t)cur, p.sweep, sw_kp, 0u), p.rk);
+        }
+        if (has_next) v_next = add_nu_terms(v_next, nl);
+        // ---- part 1
+        if (has_next) nl = load_nu<MU, OtherDir<MU, 1>::value>(p.links, p.g, xn, lex_pn, p.parity);
+        float a0 = 0.0f;
+        bool accepted = false, park = false;
         float4 out;
-        const int n = kp_draw<MU>(v, p.beta, p.rk, (uint32_t)i, p.sweep, (uint32_t)p.parity, out);
-        if (n > 0) {
-            p.links[link_index(p.g, MU, p.parity, i)] = out;
-            trials += (unsigned int)n;
-        } else {
-            atomicAdd(&p.flags[0], 1u);  // trial cap: the link keeps its old value
-            trials += (unsigned int)kMaxTrials;
+        if (valid) {
+            if (use_kp) {
+                accepted = kp_trial(w, __fmul_rn(2.0f, bk), a0);
+                park = !accepted;
+            } else {
+                const int n = heatbath_draw(v_cur, p.beta, p.rk, (uint32_t)cur, p.sweep, (uint32_t)p.parity, MU, out);
+                if (n > 0) {
+                    p.links[link_index(p.g, MU, p.parity, cur)] = out;
+                    trials += (unsigned int)n;
+                } else {
+                    atomicAdd(&p.flags[0], 1u);
+                    trials += (unsigned int)kMaxTrials;
+                }
+            }
         }
-        i = inext;
+        const unsigned int parked = __ballot_sync(0xffffffffu, park);
+        if (park) {
+            const int q = queued + __popc(parked & lanes_below);
+            s_ut[wib][q] = ut;
+            s_bk[wib][q] = bk;
+            s_eo[wib][q] = cur;
+        }
+        queued += __popc(parked);
+        if (has_next) v_next = add_nu_terms(v_next, nl);
+        // ---- part 2
+        if (has_next) nl = load_nu<MU, OtherDir<MU, 2>::value>(p.links, p.g, xn, lex_pn, p.parity);
+        if (accepted) {
+            p.links[link_index(p.g, MU, p.parity, cur)] =
+                direction_update(a0, ut, philox_rk(make_uint4((uint32_t)cur, p.sweep, sw_dir, 0u), p.rk));
+            trials += 1u;
+        }
+        if (has_next) v_next = add_nu_terms(v_next, nl);
+        __syncwarp();
+        if (queued >= 32) {
+            queued -= 32;
+            retry(queued, 32);
+        }
+        base += stride;
+        cur = nxt;
+        v_cur = v_next;
     }
+    if (queued > 0) retry(0, queued);
     const unsigned int wsum = __reduce_add_sync(0xffffffffu, trials);
-    if ((threadIdx.x & 31) == 0 && wsum)
-        atomicAdd(&p.trial_slots[(2 * MU + p.parity) * kTrialSlots + ((blockIdx.x * (kKpThreads / 32) + (threadIdx.x >> 5)) &
+    if (lane == 0 && wsum)
+        atomicAdd(&p.trial_slots[(2 * MU + p.parity) * kTrialSlots + ((blockIdx.x * kKpWarps + wib) &
                                                                       (kTrialSlots - 1))],
                   (unsigned long long)wsum);
 }

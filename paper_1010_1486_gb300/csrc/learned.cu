@@ -19,6 +19,10 @@
 namespace su2 {
 
 constexpr int kLearnThreads = 256;
+#ifndef SU2_LEARN_MIN_BLOCKS
+#define SU2_LEARN_MIN_BLOCKS 3
+#endif
+constexpr int kLearnMinBlocks = SU2_LEARN_MIN_BLOCKS;  // blocks per SM the register budget is set for
 constexpr int kAcceptSlots = 64;
 
 __global__ void proposal_table_kernel(const float *__restrict__ w, float s_lo, float s_hi, int G,
@@ -63,11 +67,15 @@ __device__ __forceinline__ unsigned int block_sum_u32(unsigned int v)
 }
 
 // One learned phase (MU, parity).  Persistent grid: each thread walks the
-// links i, i + T, i + 2T, ... (T threads in the grid).  The 18 staple links of
-// its next link are loaded before the Metropolis step of the current one, so
-// their latency hides behind that step's arithmetic.
+// links i, i + T, i + 2T, ... (T threads in the grid).  Each loop iteration
+// (three per link) issues the six loads of one nu-group of the next link, does
+// one third of the current link's step, then folds the loaded group into the
+// next link's staple:
+//   part 0  the Philox block, k, U~^dag, the table row, a0' = f(2 u0 - 1);
+//   part 1  a_cur, f^-1(a_cur), the Metropolis test;
+//   part 2  the direction and the store.
 template <int MU>
-__global__ void __launch_bounds__(kLearnThreads) learned_phase_kernel(const LearnedParams p)
+__global__ void __launch_bounds__(kLearnThreads, kLearnMinBlocks) learned_phase_kernel(const LearnedParams p)
 {
     extern __shared__ float s_table[];
     if (*(volatile const unsigned int *)p.gate != 1u) return;
@@ -77,37 +85,47 @@ __global__ void __launch_bounds__(kLearnThreads) learned_phase_kernel(const Lear
     const learned::Proposal pr{s_table, p.G, p.s_lo, p.s_hi, p.mean, p.scale};
     const int stride = gridDim.x * blockDim.x;
     const uint32_t sw = stream_word(kLearned, (uint32_t)p.parity, MU);
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int cur = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned int acc = 0;
-    NuLinks n0, n1, n2;
-    if (i < p.g.vh) {
-        const Coord x = eo_to_coord(p.g, i, p.parity);
+    float4 v_cur = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (cur < p.g.vh) {
+        const Coord x = eo_to_coord(p.g, cur, p.parity);
         const int lex_p = lex_fwd(p.g, x.lex, x.c[MU], MU);
-        n0 = load_nu<MU, OtherDir<MU, 0>::value>(p.links, p.g, x, lex_p, p.parity);
-        n1 = load_nu<MU, OtherDir<MU, 1>::value>(p.links, p.g, x, lex_p, p.parity);
-        n2 = load_nu<MU, OtherDir<MU, 2>::value>(p.links, p.g, x, lex_p, p.parity);
+        v_cur = add_nu_terms(v_cur, load_nu<MU, OtherDir<MU, 0>::value>(p.links, p.g, x, lex_p, p.parity));
+        v_cur = add_nu_terms(v_cur, load_nu<MU, OtherDir<MU, 1>::value>(p.links, p.g, x, lex_p, p.parity));
+        v_cur = add_nu_terms(v_cur, load_nu<MU, OtherDir<MU, 2>::value>(p.links, p.g, x, lex_p, p.parity));
     }
-    while (i < p.g.vh) {
-        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        v = add_nu_terms(v, n0);
-        v = add_nu_terms(v, n1);
-        v = add_nu_terms(v, n2);
-        const size_t li = link_index(p.g, MU, p.parity, i);
-        const float4 old = p.links[li];
-        const int inext = i + stride;
-        if (inext < p.g.vh) {
-            const Coord x = eo_to_coord(p.g, inext, p.parity);
-            const int lex_p = lex_fwd(p.g, x.lex, x.c[MU], MU);
-            n0 = load_nu<MU, OtherDir<MU, 0>::value>(p.links, p.g, x, lex_p, p.parity);
-            n1 = load_nu<MU, OtherDir<MU, 1>::value>(p.links, p.g, x, lex_p, p.parity);
-            n2 = load_nu<MU, OtherDir<MU, 2>::value>(p.links, p.g, x, lex_p, p.parity);
+    while (cur < p.g.vh) {
+        const int nxt = cur + stride;
+        const bool has_next = nxt < p.g.vh;
+        Coord xn;
+        int lex_pn = 0;
+        float4 v_next = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        // ---- part 0
+        NuLinks nl;
+        if (has_next) {
+            xn = eo_to_coord(p.g, nxt, p.parity);
+            lex_pn = lex_fwd(p.g, xn.lex, xn.c[MU], MU);
+            nl = load_nu<MU, OtherDir<MU, 0>::value>(p.links, p.g, xn, lex_pn, p.parity);
         }
-        const uint4 w = philox_rk(make_uint4((uint32_t)i, p.sweep, sw, 0u), p.rk);
-        float4 out;
-        const int a = learned::learned_link(pr, p.beta, v, old, w, out);
-        if (a) p.links[li] = out;
-        acc += (unsigned int)a;
-        i = inext;
+        const size_t li = link_index(p.g, MU, p.parity, cur);
+        const float4 old = p.links[li];
+        const uint4 w = philox_rk(make_uint4((uint32_t)cur, p.sweep, sw, 0u), p.rk);
+        const learned::LearnedDraw r = learned::learned_propose(pr, p.beta, v_cur, uniform01(w.x));
+        if (has_next) v_next = add_nu_terms(v_next, nl);
+        // ---- part 1
+        if (has_next) nl = load_nu<MU, OtherDir<MU, 1>::value>(p.links, p.g, xn, lex_pn, p.parity);
+        const bool accept = learned::learned_accept(r, old, uniform01(w.y));
+        if (has_next) v_next = add_nu_terms(v_next, nl);
+        // ---- part 2
+        if (has_next) nl = load_nu<MU, OtherDir<MU, 2>::value>(p.links, p.g, xn, lex_pn, p.parity);
+        if (accept) {
+            p.links[li] = direction_from_uniforms(r.a_new, r.d.ut, uniform01(w.z), uniform01(w.w));
+            ++acc;
+        }
+        if (has_next) v_next = add_nu_terms(v_next, nl);
+        cur = nxt;
+        v_cur = v_next;
     }
     const unsigned int total = block_sum_u32(acc);
     if (threadIdx.x == 0 && total) {

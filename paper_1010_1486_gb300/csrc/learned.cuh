@@ -202,36 +202,47 @@ struct Proposal {
 // Delta = beta k (a0' - a_cur) + log(sqrt((1 - a0'^2)/(1 - a_cur^2)) f'(z')/f'(z_cur)),
 // a_cur = old U~.  All four uniforms from one Philox block of the learned stream.
 // Returns 1 (out = new link) or 0 (out = old).
+// The step in two parts, so a caller can place other work between them:
+// learned_propose draws a0' and f'(z'); learned_accept decides.
+struct LearnedDraw {
+    DrawSetup d;
+    InterpParams ip;
+    float a_new, fp_new;
+};
+
+__device__ __forceinline__ LearnedDraw learned_propose(const Proposal &pr, float beta, float4 v, float u0)
+{
+    LearnedDraw r;
+    r.d = prepare_draw(v, beta);
+    r.ip = table_params(pr.table, pr.G, pr.s_lo, pr.s_hi, __fmul_rn(__fsub_rn(r.d.bk, pr.mean), pr.scale));
+    r.a_new = spline_forward(r.ip, __fsub_rn(__fmul_rn(2.0f, u0), 1.0f), r.fp_new);
+    return r;
+}
+
+__device__ __forceinline__ bool learned_accept(const LearnedDraw &r, float4 old, float u1)
+{
+    float acur = chain4(old.x, r.d.ut.x, old.y, r.d.ut.y, old.z, r.d.ut.z, old.w, r.d.ut.w);
+    acur = acur < -1.0f ? -1.0f : (acur > 1.0f ? 1.0f : acur);
+    float fp_cur;
+    spline_inverse(r.ip, acur, fp_cur);
+    const float one_cur = __fmaf_rn(-acur, acur, 1.0f);
+    if (!(one_cur > 0.0f)) return true;
+    const float one_new = __fmaf_rn(-r.a_new, r.a_new, 1.0f);
+    const float ratio = __fmul_rn(__fsqrt_rn(__fdiv_rn(one_new, one_cur)), __fdiv_rn(r.fp_new, fp_cur));
+    if (!(ratio > 0.0f)) return false;
+    const float delta = __fmaf_rn(r.d.bk, __fsub_rn(r.a_new, acur), log_series(ratio));
+    return delta >= 0.0f || u1 <= exp_neg(delta);
+}
+
 __device__ __forceinline__ int learned_link(const Proposal &pr, float beta, float4 v, float4 old, uint4 w,
                                             float4 &out)
 {
-    const DrawSetup d = prepare_draw(v, beta);
-    const InterpParams p = table_params(pr.table, pr.G, pr.s_lo, pr.s_hi, __fmul_rn(__fsub_rn(d.bk, pr.mean), pr.scale));
-    const float u0 = uniform01(w.x), u1 = uniform01(w.y), u2 = uniform01(w.z), u3 = uniform01(w.w);
-    float fp_new, fp_cur;
-    const float a_new = spline_forward(p, __fsub_rn(__fmul_rn(2.0f, u0), 1.0f), fp_new);
-    float acur = chain4(old.x, d.ut.x, old.y, d.ut.y, old.z, d.ut.z, old.w, d.ut.w);
-    acur = acur < -1.0f ? -1.0f : (acur > 1.0f ? 1.0f : acur);
-    spline_inverse(p, acur, fp_cur);
-    const float one_cur = __fmaf_rn(-acur, acur, 1.0f);
-    bool accept;
-    if (!(one_cur > 0.0f)) {
-        accept = true;
-    } else {
-        const float one_new = __fmaf_rn(-a_new, a_new, 1.0f);
-        const float ratio = __fmul_rn(__fsqrt_rn(__fdiv_rn(one_new, one_cur)), __fdiv_rn(fp_new, fp_cur));
-        if (!(ratio > 0.0f)) {
-            accept = false;
-        } else {
-            const float delta = __fmaf_rn(d.bk, __fsub_rn(a_new, acur), log_series(ratio));
-            accept = delta >= 0.0f || u1 <= exp_neg(delta);
-        }
-    }
-    if (!accept) {
+    const LearnedDraw r = learned_propose(pr, beta, v, uniform01(w.x));
+    if (!learned_accept(r, old, uniform01(w.y))) {
         out = old;
         return 0;
     }
-    out = direction_from_uniforms(a_new, d.ut, u2, u3);
+    out = direction_from_uniforms(r.a_new, r.d.ut, uniform01(w.z), uniform01(w.w));
     return 1;
 }
 

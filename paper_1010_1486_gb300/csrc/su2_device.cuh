@@ -362,9 +362,11 @@ __device__ __forceinline__ int lex_bwd(const Geom &g, int lex, int c_mu, int mu)
     return c_mu == 0 ? lex + g.wrap[mu] : lex - g.stride[mu];
 }
 
-__device__ __forceinline__ size_t link_index(const Geom &g, int mu, int parity, int eo)
+// 32-bit unsigned: a lattice holds fewer than 2^31 links (checked at
+// creation), so the address is one wide multiply-add of the offset.
+__device__ __forceinline__ uint32_t link_index(const Geom &g, int mu, int parity, int eo)
 {
-    return (size_t)(2 * mu + parity) * (size_t)g.vh + (size_t)eo;
+    return (uint32_t)(2 * mu + parity) * (uint32_t)g.vh + (uint32_t)eo;
 }
 
 }  // namespace su2
