@@ -36,7 +36,8 @@ struct KpParams {
     const unsigned int *gate;  // skip the phase while *gate == 1 (learned sweeps)
 };
 
-// One trial (block t of the KP stream): true and a0 if accepted.
+// One trial (block t of the KP stream): a0 = 1 - 2 u, and whether it is
+// accepted.
 __device__ __forceinline__ bool kp_trial(uint4 w, float two_bk, float &a0)
 {
     float sn, cs;
@@ -44,11 +45,8 @@ __device__ __forceinline__ bool kp_trial(uint4 w, float two_bk, float &a0)
     const float num = __fmaf_rn(__fmul_rn(cs, cs), log_series(uniform01(w.z)), log_series(uniform01(w.x)));
     const float lam2 = __fdiv_rn(-num, two_bk);
     const float r4 = uniform01(w.w);
-    if (lam2 <= 1.0f && __fmul_rn(r4, r4) <= __fsub_rn(1.0f, lam2)) {
-        a0 = __fmaf_rn(-2.0f, lam2, 1.0f);
-        return true;
-    }
-    return false;
+    a0 = __fmaf_rn(-2.0f, lam2, 1.0f);
+    return lam2 <= 1.0f && __fmul_rn(r4, r4) <= __fsub_rn(1.0f, lam2);
 }
 
 constexpr int kKpWarps = kKpThreads / 32;
@@ -60,14 +58,17 @@ constexpr int kRetryCap = 64;  // per warp: at most 31 left over + 32 pushed by 
 // draw, then folds the loaded group into the next round's staple, so 24
 // registers of loads are in flight and the draw's arithmetic covers their
 // latency:
-//   part 0  k, beta k, U~^dag; the first trial's Philox block;
+//   part 0  k, beta k, U~^dag; the Philox blocks of the first trial and of
+//           the direction;
 //   part 1  the first trial (Creutz's method instead if beta k < 2);
 //   part 2  the direction and the store of every accepted link.
 // A link whose first trial is rejected is parked in the warp's retry queue
 // in shared memory (U~^dag, beta k, index).  Once 32 links wait, the whole
 // warp runs their further trials 1, 2, ... together, so no warp spins on one
 // lane's rejections.  Every draw depends only on the link's counters, so the
-// phase computes exactly the one-thread-per-link definition.
+// phase computes exactly the one-thread-per-link definition.  Lanes past the
+// end (last round, next round) work on a clamped index and drop their
+// results, so the main path has no divergent branch.
 template <int MU>
 __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(const KpParams p)
 {
@@ -79,6 +80,7 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
     const int wib = threadIdx.x >> 5;
     const unsigned int lanes_below = (1u << lane) - 1u;
     const int stride = gridDim.x * kKpThreads;
+    const int last = p.g.vh - 1;
     const uint32_t sw_kp = stream_word(kKennedyPendleton, (uint32_t)p.parity, MU);
     const uint32_t sw_dir = stream_word(kDirection, (uint32_t)p.parity, MU);
     unsigned int trials = 0;
@@ -112,57 +114,45 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
     int base = blockIdx.x * kKpThreads + (wib << 5);
     int cur = base + lane;
     float4 v_cur = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (cur < p.g.vh) {
-        const Coord x = eo_to_coord(p.g, cur, p.parity);
+    if (base < p.g.vh) {
+        const Coord x = eo_to_coord(p.g, min(cur, last), p.parity);
         const int lex_p = lex_fwd(p.g, x.lex, x.c[MU], MU);
         v_cur = add_nu_terms(v_cur, load_nu<MU, OtherDir<MU, 0>::value>(p.links, p.g, x, lex_p, p.parity));
         v_cur = add_nu_terms(v_cur, load_nu<MU, OtherDir<MU, 1>::value>(p.links, p.g, x, lex_p, p.parity));
         v_cur = add_nu_terms(v_cur, load_nu<MU, OtherDir<MU, 2>::value>(p.links, p.g, x, lex_p, p.parity));
     }
     while (base < p.g.vh) {  // warp-uniform
-        const bool valid = cur < p.g.vh;
+        const bool valid = cur <= last;
         const int nxt = cur + stride;
-        const bool has_next = nxt < p.g.vh;
-        Coord xn;
-        int lex_pn = 0;
-        float4 v_next = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        const Coord xn = eo_to_coord(p.g, min(nxt, last), p.parity);
+        const int lex_pn = lex_fwd(p.g, xn.lex, xn.c[MU], MU);
         // ---- part 0
-        NuLinks nl;
-        if (has_next) {
-            xn = eo_to_coord(p.g, nxt, p.parity);
-            lex_pn = lex_fwd(p.g, xn.lex, xn.c[MU], MU);
-            nl = load_nu<MU, OtherDir<MU, 0>::value>(p.links, p.g, xn, lex_pn, p.parity);
-        }
+        NuLinks nl = load_nu<MU, OtherDir<MU, 0>::value>(p.links, p.g, xn, lex_pn, p.parity);
         const float k = __fsqrt_rn(qnorm2(v_cur));
         const float bk = __fmul_rn(p.beta, k);
         const bool use_kp = bk >= kKpMinBk;
-        float4 ut = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
-        uint4 w = make_uint4(0u, 0u, 0u, 0u);
-        if (valid && use_kp) {
-            const float inv_k = __fdiv_rn(1.0f, k);
-            ut = make_float4(__fmul_rn(v_cur.x, inv_k), __fmul_rn(-v_cur.y, inv_k), __fmul_rn(-v_cur.z, inv_k),
-                             __fmul_rn(-v_cur.w, inv_k));
-            w = philox_rk(make_uint4((uint32_t)cur, p.sweep, sw_kp, 0u), p.rk);
-        }
-        if (has_next) v_next = add_nu_terms(v_next, nl);
+        const float inv_k = __fdiv_rn(1.0f, k);
+        const float4 ut = make_float4(__fmul_rn(v_cur.x, inv_k), __fmul_rn(-v_cur.y, inv_k),
+                                      __fmul_rn(-v_cur.z, inv_k), __fmul_rn(-v_cur.w, inv_k));
+        uint4 w = make_uint4((uint32_t)cur, p.sweep, sw_kp, 0u);
+        uint4 wd = make_uint4((uint32_t)cur, p.sweep, sw_dir, 0u);
+        philox2_rk(w, wd, p.rk);
+        float4 v_next = add_nu_terms(make_float4(0.0f, 0.0f, 0.0f, 0.0f), nl);
         // ---- part 1
-        if (has_next) nl = load_nu<MU, OtherDir<MU, 1>::value>(p.links, p.g, xn, lex_pn, p.parity);
-        float a0 = 0.0f;
-        bool accepted = false, park = false;
-        float4 out;
-        if (valid) {
-            if (use_kp) {
-                accepted = kp_trial(w, __fmul_rn(2.0f, bk), a0);
-                park = !accepted;
+        nl = load_nu<MU, OtherDir<MU, 1>::value>(p.links, p.g, xn, lex_pn, p.parity);
+        float a0;
+        const bool first_ok = kp_trial(w, __fmul_rn(2.0f, bk), a0);
+        const bool accepted = valid && use_kp && first_ok;
+        const bool park = valid && use_kp && !first_ok;
+        if (valid && !use_kp) {  // beta k < 2: Creutz's method
+            float4 out;
+            const int n = heatbath_draw(v_cur, p.beta, p.rk, (uint32_t)cur, p.sweep, (uint32_t)p.parity, MU, out);
+            if (n > 0) {
+                p.links[link_index(p.g, MU, p.parity, cur)] = out;
+                trials += (unsigned int)n;
             } else {
-                const int n = heatbath_draw(v_cur, p.beta, p.rk, (uint32_t)cur, p.sweep, (uint32_t)p.parity, MU, out);
-                if (n > 0) {
-                    p.links[link_index(p.g, MU, p.parity, cur)] = out;
-                    trials += (unsigned int)n;
-                } else {
-                    atomicAdd(&p.flags[0], 1u);
-                    trials += (unsigned int)kMaxTrials;
-                }
+                atomicAdd(&p.flags[0], 1u);
+                trials += (unsigned int)kMaxTrials;
             }
         }
         const unsigned int parked = __ballot_sync(0xffffffffu, park);
@@ -173,15 +163,13 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
             s_eo[wib][q] = cur;
         }
         queued += __popc(parked);
-        if (has_next) v_next = add_nu_terms(v_next, nl);
+        v_next = add_nu_terms(v_next, nl);
         // ---- part 2
-        if (has_next) nl = load_nu<MU, OtherDir<MU, 2>::value>(p.links, p.g, xn, lex_pn, p.parity);
-        if (accepted) {
-            p.links[link_index(p.g, MU, p.parity, cur)] =
-                direction_update(a0, ut, philox_rk(make_uint4((uint32_t)cur, p.sweep, sw_dir, 0u), p.rk));
-            trials += 1u;
-        }
-        if (has_next) v_next = add_nu_terms(v_next, nl);
+        nl = load_nu<MU, OtherDir<MU, 2>::value>(p.links, p.g, xn, lex_pn, p.parity);
+        const float4 out = direction_update(a0, ut, wd);
+        if (accepted) p.links[link_index(p.g, MU, p.parity, cur)] = out;
+        trials += accepted ? 1u : 0u;
+        v_next = add_nu_terms(v_next, nl);
         __syncwarp();
         if (queued >= 32) {
             queued -= 32;

@@ -85,45 +85,43 @@ __global__ void __launch_bounds__(kLearnThreads, kLearnMinBlocks) learned_phase_
     const learned::Proposal pr{s_table, p.G, p.s_lo, p.s_hi, p.mean, p.scale};
     const int stride = gridDim.x * blockDim.x;
     const uint32_t sw = stream_word(kLearned, (uint32_t)p.parity, MU);
-    int cur = blockIdx.x * blockDim.x + threadIdx.x;
+    const int last = p.g.vh - 1;
+    // Lanes past the end work on a clamped index and drop their results, so
+    // the loop body has no divergent branch.
+    int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+    int cur = base + (threadIdx.x & 31);
     unsigned int acc = 0;
     float4 v_cur = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (cur < p.g.vh) {
-        const Coord x = eo_to_coord(p.g, cur, p.parity);
+    if (base < p.g.vh) {
+        const Coord x = eo_to_coord(p.g, min(cur, last), p.parity);
         const int lex_p = lex_fwd(p.g, x.lex, x.c[MU], MU);
         v_cur = add_nu_terms(v_cur, load_nu<MU, OtherDir<MU, 0>::value>(p.links, p.g, x, lex_p, p.parity));
         v_cur = add_nu_terms(v_cur, load_nu<MU, OtherDir<MU, 1>::value>(p.links, p.g, x, lex_p, p.parity));
         v_cur = add_nu_terms(v_cur, load_nu<MU, OtherDir<MU, 2>::value>(p.links, p.g, x, lex_p, p.parity));
     }
-    while (cur < p.g.vh) {
+    while (base < p.g.vh) {  // warp-uniform
+        const bool valid = cur <= last;
         const int nxt = cur + stride;
-        const bool has_next = nxt < p.g.vh;
-        Coord xn;
-        int lex_pn = 0;
-        float4 v_next = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        const Coord xn = eo_to_coord(p.g, min(nxt, last), p.parity);
+        const int lex_pn = lex_fwd(p.g, xn.lex, xn.c[MU], MU);
         // ---- part 0
-        NuLinks nl;
-        if (has_next) {
-            xn = eo_to_coord(p.g, nxt, p.parity);
-            lex_pn = lex_fwd(p.g, xn.lex, xn.c[MU], MU);
-            nl = load_nu<MU, OtherDir<MU, 0>::value>(p.links, p.g, xn, lex_pn, p.parity);
-        }
-        const size_t li = link_index(p.g, MU, p.parity, cur);
+        NuLinks nl = load_nu<MU, OtherDir<MU, 0>::value>(p.links, p.g, xn, lex_pn, p.parity);
+        const uint32_t li = link_index(p.g, MU, p.parity, min(cur, last));
         const float4 old = p.links[li];
         const uint4 w = philox_rk(make_uint4((uint32_t)cur, p.sweep, sw, 0u), p.rk);
         const learned::LearnedDraw r = learned::learned_propose(pr, p.beta, v_cur, uniform01(w.x));
-        if (has_next) v_next = add_nu_terms(v_next, nl);
+        float4 v_next = add_nu_terms(make_float4(0.0f, 0.0f, 0.0f, 0.0f), nl);
         // ---- part 1
-        if (has_next) nl = load_nu<MU, OtherDir<MU, 1>::value>(p.links, p.g, xn, lex_pn, p.parity);
-        const bool accept = learned::learned_accept(r, old, uniform01(w.y));
-        if (has_next) v_next = add_nu_terms(v_next, nl);
+        nl = load_nu<MU, OtherDir<MU, 1>::value>(p.links, p.g, xn, lex_pn, p.parity);
+        const bool accept = valid && learned::learned_accept(r, old, uniform01(w.y));
+        v_next = add_nu_terms(v_next, nl);
         // ---- part 2
-        if (has_next) nl = load_nu<MU, OtherDir<MU, 2>::value>(p.links, p.g, xn, lex_pn, p.parity);
-        if (accept) {
-            p.links[li] = direction_from_uniforms(r.a_new, r.d.ut, uniform01(w.z), uniform01(w.w));
-            ++acc;
-        }
-        if (has_next) v_next = add_nu_terms(v_next, nl);
+        nl = load_nu<MU, OtherDir<MU, 2>::value>(p.links, p.g, xn, lex_pn, p.parity);
+        const float4 out = direction_from_uniforms(r.a_new, r.d.ut, uniform01(w.z), uniform01(w.w));
+        if (accept) p.links[li] = out;
+        acc += accept ? 1u : 0u;
+        v_next = add_nu_terms(v_next, nl);
+        base += stride;
         cur = nxt;
         v_cur = v_next;
     }

@@ -51,6 +51,22 @@ __device__ __forceinline__ uint4 philox_rk(uint4 c, const RoundKeys &rk)
     return c;
 }
 
+// Two blocks under the same key, round by round: each round key is fetched
+// once for both, and the two independent chains interleave.
+__device__ __forceinline__ void philox2_rk(uint4 &a, uint4 &b, const RoundKeys &rk)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t k0 = rk.k0[round], k1 = rk.k1[round];
+        const uint32_t alo0 = 0xD2511F53u * a.x, ahi0 = __umulhi(0xD2511F53u, a.x);
+        const uint32_t alo1 = 0xCD9E8D57u * a.z, ahi1 = __umulhi(0xCD9E8D57u, a.z);
+        const uint32_t blo0 = 0xD2511F53u * b.x, bhi0 = __umulhi(0xD2511F53u, b.x);
+        const uint32_t blo1 = 0xCD9E8D57u * b.z, bhi1 = __umulhi(0xCD9E8D57u, b.z);
+        a = make_uint4(ahi1 ^ a.y ^ k0, alo1, ahi0 ^ a.w ^ k1, alo0);
+        b = make_uint4(bhi1 ^ b.y ^ k0, blo1, bhi0 ^ b.w ^ k1, blo0);
+    }
+}
+
 // The same generator with the key schedule computed on the fly (for kernels
 // whose key varies per work item, e.g. one seed per lattice of a batch).
 __device__ __forceinline__ uint4 philox_key(uint4 c, uint32_t k0, uint32_t k1)
