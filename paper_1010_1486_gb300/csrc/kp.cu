@@ -115,19 +115,21 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
     int cur = base + lane;
     float4 v_cur = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (base < p.g.vh) {
-        const Coord x = eo_to_coord(p.g, min(cur, last), p.parity);
-        const int lex_p = lex_fwd(p.g, x.lex, x.c[MU], MU);
-        v_cur = add_nu_terms(v_cur, load_nu<MU, OtherDir<MU, 0>::value>(p.links, p.g, x, lex_p, p.parity));
-        v_cur = add_nu_terms(v_cur, load_nu<MU, OtherDir<MU, 1>::value>(p.links, p.g, x, lex_p, p.parity));
-        v_cur = add_nu_terms(v_cur, load_nu<MU, OtherDir<MU, 2>::value>(p.links, p.g, x, lex_p, p.parity));
+        const int e = min(cur, last);
+        const Coord x = eo_to_coord(p.g, e, p.parity);
+        const int e_p = eo_fwd<MU>(p.g, x, e);
+        v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 0>::value>(p.links, p.g, x, e, e_p, p.parity));
+        v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 1>::value>(p.links, p.g, x, e, e_p, p.parity));
+        v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 2>::value>(p.links, p.g, x, e, e_p, p.parity));
     }
     while (base < p.g.vh) {  // warp-uniform
         const bool valid = cur <= last;
         const int nxt = cur + stride;
-        const Coord xn = eo_to_coord(p.g, min(nxt, last), p.parity);
-        const int lex_pn = lex_fwd(p.g, xn.lex, xn.c[MU], MU);
+        const int en = min(nxt, last);
+        const Coord xn = eo_to_coord(p.g, en, p.parity);
+        const int en_p = eo_fwd<MU>(p.g, xn, en);
         // ---- part 0
-        NuLinks nl = load_nu<MU, OtherDir<MU, 0>::value>(p.links, p.g, xn, lex_pn, p.parity);
+        NuLinks nl = load_nu_eo<MU, OtherDir<MU, 0>::value>(p.links, p.g, xn, en, en_p, p.parity);
         const float k = __fsqrt_rn(qnorm2(v_cur));
         const float bk = __fmul_rn(p.beta, k);
         const bool use_kp = bk >= kKpMinBk;
@@ -139,7 +141,7 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
         philox2_rk(w, wd, p.rk);
         float4 v_next = add_nu_terms(make_float4(0.0f, 0.0f, 0.0f, 0.0f), nl);
         // ---- part 1
-        nl = load_nu<MU, OtherDir<MU, 1>::value>(p.links, p.g, xn, lex_pn, p.parity);
+        nl = load_nu_eo<MU, OtherDir<MU, 1>::value>(p.links, p.g, xn, en, en_p, p.parity);
         float a0;
         const bool first_ok = kp_trial(w, __fmul_rn(2.0f, bk), a0);
         const bool accepted = valid && use_kp && first_ok;
@@ -165,7 +167,7 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
         queued += __popc(parked);
         v_next = add_nu_terms(v_next, nl);
         // ---- part 2
-        nl = load_nu<MU, OtherDir<MU, 2>::value>(p.links, p.g, xn, lex_pn, p.parity);
+        nl = load_nu_eo<MU, OtherDir<MU, 2>::value>(p.links, p.g, xn, en, en_p, p.parity);
         const float4 out = direction_update(a0, ut, wd);
         if (accepted) p.links[link_index(p.g, MU, p.parity, cur)] = out;
         trials += accepted ? 1u : 0u;

@@ -93,30 +93,32 @@ __global__ void __launch_bounds__(kLearnThreads, kLearnMinBlocks) learned_phase_
     unsigned int acc = 0;
     float4 v_cur = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (base < p.g.vh) {
-        const Coord x = eo_to_coord(p.g, min(cur, last), p.parity);
-        const int lex_p = lex_fwd(p.g, x.lex, x.c[MU], MU);
-        v_cur = add_nu_terms(v_cur, load_nu<MU, OtherDir<MU, 0>::value>(p.links, p.g, x, lex_p, p.parity));
-        v_cur = add_nu_terms(v_cur, load_nu<MU, OtherDir<MU, 1>::value>(p.links, p.g, x, lex_p, p.parity));
-        v_cur = add_nu_terms(v_cur, load_nu<MU, OtherDir<MU, 2>::value>(p.links, p.g, x, lex_p, p.parity));
+        const int e = min(cur, last);
+        const Coord x = eo_to_coord(p.g, e, p.parity);
+        const int e_p = eo_fwd<MU>(p.g, x, e);
+        v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 0>::value>(p.links, p.g, x, e, e_p, p.parity));
+        v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 1>::value>(p.links, p.g, x, e, e_p, p.parity));
+        v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 2>::value>(p.links, p.g, x, e, e_p, p.parity));
     }
     while (base < p.g.vh) {  // warp-uniform
         const bool valid = cur <= last;
         const int nxt = cur + stride;
-        const Coord xn = eo_to_coord(p.g, min(nxt, last), p.parity);
-        const int lex_pn = lex_fwd(p.g, xn.lex, xn.c[MU], MU);
+        const int en = min(nxt, last);
+        const Coord xn = eo_to_coord(p.g, en, p.parity);
+        const int en_p = eo_fwd<MU>(p.g, xn, en);
         // ---- part 0
-        NuLinks nl = load_nu<MU, OtherDir<MU, 0>::value>(p.links, p.g, xn, lex_pn, p.parity);
+        NuLinks nl = load_nu_eo<MU, OtherDir<MU, 0>::value>(p.links, p.g, xn, en, en_p, p.parity);
         const uint32_t li = link_index(p.g, MU, p.parity, min(cur, last));
         const float4 old = p.links[li];
         const uint4 w = philox_rk(make_uint4((uint32_t)cur, p.sweep, sw, 0u), p.rk);
         const learned::LearnedDraw r = learned::learned_propose(pr, p.beta, v_cur, uniform01(w.x));
         float4 v_next = add_nu_terms(make_float4(0.0f, 0.0f, 0.0f, 0.0f), nl);
         // ---- part 1
-        nl = load_nu<MU, OtherDir<MU, 1>::value>(p.links, p.g, xn, lex_pn, p.parity);
+        nl = load_nu_eo<MU, OtherDir<MU, 1>::value>(p.links, p.g, xn, en, en_p, p.parity);
         const bool accept = valid && learned::learned_accept(r, old, uniform01(w.y));
         v_next = add_nu_terms(v_next, nl);
         // ---- part 2
-        nl = load_nu<MU, OtherDir<MU, 2>::value>(p.links, p.g, xn, lex_pn, p.parity);
+        nl = load_nu_eo<MU, OtherDir<MU, 2>::value>(p.links, p.g, xn, en, en_p, p.parity);
         const float4 out = direction_from_uniforms(r.a_new, r.d.ut, uniform01(w.z), uniform01(w.w));
         if (accept) p.links[li] = out;
         acc += accept ? 1u : 0u;

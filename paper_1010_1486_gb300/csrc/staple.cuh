@@ -64,6 +64,46 @@ __device__ __forceinline__ float4 add_nu_terms(float4 v, const NuLinks &n)
     return qadd(qadd(v, fwd), bwd);
 }
 
+// Even/odd neighbour indices straight from the coordinates.  The strides of
+// y, z, t are even, so (lex +- stride) >> 1 = eo +- stride/2 (and the
+// periodic jump is even too); in x the step depends on the parity of x0.
+// Index of x + nu:
+template <int NU>
+__device__ __forceinline__ int eo_fwd(const Geom &g, const Coord &x, int eo)
+{
+    if (NU == 0) return eo + (x.c[0] & 1) - (x.c[0] == g.ns - 1 ? (g.ns >> 1) : 0);
+    return eo + (x.c[NU] == g.ext[NU] - 1 ? -(g.wrap[NU] >> 1) : (g.stride[NU] >> 1));
+}
+
+// eo(x - nu) - eo(x); the same for x + mu - nu against x + mu (mu != nu:
+// the step to x + mu keeps x0 and its parity, or is in x itself).
+template <int NU>
+__device__ __forceinline__ int eo_bwd_offset(const Geom &g, const Coord &x)
+{
+    if (NU == 0) return (x.c[0] & 1) - 1 + (x.c[0] == 0 ? (g.ns >> 1) : 0);
+    return x.c[NU] == 0 ? (g.wrap[NU] >> 1) : -(g.stride[NU] >> 1);
+}
+
+// load_nu with the indices above; eo = index of x, e_p = index of x + mu.
+template <int MU, int NU>
+__device__ __forceinline__ NuLinks load_nu_eo(const float4 *__restrict__ L, const Geom &g, const Coord &x, int eo,
+                                              int e_p, int parity)
+{
+    const int op = parity ^ 1;
+    const float4 *__restrict__ nu_same = L + (uint32_t)(2 * NU + parity) * (uint32_t)g.vh;
+    const float4 *__restrict__ nu_other = L + (uint32_t)(2 * NU + op) * (uint32_t)g.vh;
+    const float4 *__restrict__ mu_other = L + (uint32_t)(2 * MU + op) * (uint32_t)g.vh;
+    const int off_m = eo_bwd_offset<NU>(g, x);
+    NuLinks n;
+    n.nu_xp = __ldg(nu_other + (uint32_t)e_p);
+    n.mu_xn = __ldg(mu_other + (uint32_t)eo_fwd<NU>(g, x, eo));
+    n.nu_x = __ldg(nu_same + (uint32_t)eo);
+    n.nu_xpm = __ldg(nu_same + (uint32_t)(e_p + off_m));
+    n.mu_xm = __ldg(mu_other + (uint32_t)(eo + off_m));
+    n.nu_xm = __ldg(nu_other + (uint32_t)(eo + off_m));
+    return n;
+}
+
 // The three directions nu != MU in ascending order.
 template <int MU, int J>
 struct OtherDir {
