@@ -86,6 +86,9 @@ def _load():
             "orc_heatbath_sweep_kp": (i64, [i32, i32, f64, u64, u32, P, P, i32]),
             "orc_heatbath_phase_kp": (i64, [i32, i32, f64, u64, u32, i32, i32, P, ctypes.POINTER(i64), i32]),
             "orc_kp_a0_v": (None, [f32, u64, u32, i64, P, P]),
+            "orc_overrelax_link": (None, [P, P]),
+            "orc_overrelax_phase": (None, [i32, i32, i32, i32, P, i32]),
+            "orc_overrelax_sweep": (None, [i32, i32, P, i32]),
             "orc_mlp_forward": (None, [P, f32, P]),
             "orc_spline_params": (None, [P, P]),
             "orc_spline_forward": (f32, [P, f32, P]),
@@ -240,6 +243,23 @@ def heatbath_sweep_kp(ns: int, nt: int, beta: float, seed: int, sweep: int, link
     if err:
         raise RuntimeError(f"{err} links hit the trial cap")
     return trials
+
+
+def overrelax_link(v, u) -> np.ndarray:
+    """U' = U~^dag U^dag U~^dag for staple v (the reflection that keeps Tr UV)."""
+    v = np.ascontiguousarray(v, dtype=np.float32)
+    out = np.array(u, dtype=np.float32, copy=True)
+    _load().orc_overrelax_link(_ptr(v), _ptr(out))
+    return out
+
+
+def overrelax_phase(ns: int, nt: int, mu: int, parity: int, links: np.ndarray, nthreads: int = 1) -> None:
+    _load().orc_overrelax_phase(ns, nt, mu, parity, _ptr(links), nthreads)
+
+
+def overrelax_sweep(ns: int, nt: int, links: np.ndarray, nthreads: int = 1) -> None:
+    """One over-relaxation sweep (mu = 0..3, even then odd), in place."""
+    _load().orc_overrelax_sweep(ns, nt, _ptr(links), nthreads)
 
 
 def kp_a0_many(bk: float, seed: int, n: int, eo0: int = 0):

@@ -734,3 +734,59 @@ void orc_kp_a0_v(float bk, uint64_t seed, uint32_t eo0, int64_t n, float *a0, in
         a0[i] = out[0];
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Over-relaxation: the microcanonical reflection of a link in its staple    */
+/* (Adler, Phys. Rev. D 23 (1981) 2901; Creutz, Phys. Rev. D 36 (1987) 515;  */
+/* Brown and Woch, Phys. Rev. Lett. 58 (1987) 2394).  It is not in the paper: */
+/* it is the usual companion of the Sec. 2 heat bath.  With U~ = V/k,         */
+/*   U' = U~^dag U^dag U~^dag,                                                */
+/* so U' U~ = (U U~)^dag: the heat-bath variable a = U U~ is reflected to     */
+/* a^dag, (1/2) Tr U'V = (1/2) Tr UV (the action is unchanged) and applying   */
+/* the map twice gives U back.  No random numbers.  For k = 0 U~ is the       */
+/* identity, as in the heat bath (the action does not depend on U then).      */
+/* Products left to right: (U~^dag U^dag) U~^dag.                             */
+/* ------------------------------------------------------------------------ */
+void orc_overrelax_link(const float v[4], float u[4])
+{
+    float k = sqrtf(dot4(v[0], v[0], v[1], v[1], v[2], v[2], v[3], v[3]));
+    float ut[4];
+    if (k > 0.0f) {
+        float inv_k = 1.0f / k;
+        ut[0] = v[0] * inv_k;
+        ut[1] = -v[1] * inv_k;
+        ut[2] = -v[2] * inv_k;
+        ut[3] = -v[3] * inv_k;
+    } else {
+        ut[0] = 1.0f; ut[1] = 0.0f; ut[2] = 0.0f; ut[3] = 0.0f;
+    }
+    float ud[4], t[4];
+    quat_dag(u, ud);
+    orc_quat_mul(ut, ud, t);
+    orc_quat_mul(t, ut, u);
+}
+
+/* Every link U_mu(x) with parity(x) = p (links of one phase share no
+ * plaquette, so the order of sites does not matter). */
+void orc_overrelax_phase(int ns, int nt, int mu, int p, float *links, int nthreads)
+{
+    int64_t vol = (int64_t)ns * ns * ns * nt;
+#ifdef _OPENMP
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+#endif
+    for (int64_t s = 0; s < vol; ++s) {
+        if (site_parity(s, ns) != p) continue;
+        float v[4];
+        orc_staple(ns, nt, links, s, mu, v);
+        orc_overrelax_link(v, links + (s * 4 + mu) * 4);
+    }
+    (void)nthreads;
+}
+
+/* One over-relaxation sweep: mu = 0..3, even then odd, as the heat bath. */
+void orc_overrelax_sweep(int ns, int nt, float *links, int nthreads)
+{
+    for (int mu = 0; mu < 4; ++mu)
+        for (int p = 0; p < 2; ++p) orc_overrelax_phase(ns, nt, mu, p, links, nthreads);
+}
