@@ -45,6 +45,8 @@ UNIT = "link updates/s"
 PAPER_RATE = 1.0e6 * LINKS / 86400.0
 BYTES_PER_UPDATE = 128  # reads 3.5 V + writes 0.5 V float4 per phase of V/2 updates
 BYTES_PER_LEARNED_UPDATE = 144  # + the old link of the updated direction and parity
+BYTES_PER_OR_UPDATE = 144  # over-relaxation: the staple links, the old link, the new link
+N_OR = 3  # over-relaxation sweeps after each heat-bath sweep in the compound form
 HB_SOURCES = ["paper_1010_1486_gb300/csrc/heatbath.cu", "paper_1010_1486_gb300/csrc/su2_device.cuh"]
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "hb_phase_48x48x48x48_beta6.md")
 
@@ -316,9 +318,19 @@ def compare_forms(args, dist, lat, su2, torch, stream, tau_int):
     # learned, timed
     su2.su2_learned_generate(lat, 2, 1, 0.7)
     ms_l, (_, _, st_l) = timed(stream, torch, dist, lambda: su2.su2_learned_generate(lat, args.steps, 1, 0.7))
-    su2.su2_set_timing(lat, False)
     learned_phase_s = st_l["kernel_ms"] / max(1, st_l["kernel_launches"]) * 1e-3
     value_learned = dist.reduce(float(st_l["link_updates"]), "sum") / (ms_l * 1e-3)
+    # compound sweeps: one Kennedy-Pendleton heat-bath sweep + N_OR over-relaxation sweeps, timed
+    su2.su2_set_sampler(lat, su2.SU2_SAMPLER_KP)
+    su2.su2_set_overrelax(lat, N_OR)
+    su2.su2_generate(lat, 2, 1, 0)
+    n_cmp = max(1, args.steps // (N_OR + 1))
+    ms_o, (_, _, st_o) = timed(stream, torch, dist, lambda: su2.su2_generate(lat, n_cmp, 1, 0))
+    su2.su2_set_overrelax(lat, 0)
+    su2.su2_set_sampler(lat, su2.SU2_SAMPLER_CREUTZ)
+    su2.su2_set_timing(lat, False)
+    or_phase_s = st_o["overrelax_ms"] / (8 * st_o["overrelax_sweeps"]) * 1e-3
+    compound_per_s = dist.reduce(float(n_cmp), "sum") / (ms_o * 1e-3)
     proposals = st_l["learned_sweeps"] * 4 * VOL
 
     out = {"lattice": "thermalised 48^4, beta = 6.0 (after warm-up, timed steps and %d more sweeps)" % args.therm,
@@ -344,20 +356,41 @@ def compare_forms(args, dist, lat, su2, torch, stream, tau_int):
                        "training": {"pairs": args.learned_pairs, "steps": args.train_steps, "batch": 4096,
                                     "collect_s": t1 - t0, "train_s": t2 - t1,
                                     "loss_first": float(losses[:10].mean()), "loss_last": float(losses[-50:].mean())}}}
-    for form in ("plain", "plain_kennedy_pendleton", "learned"):
+    out["kp_overrelax"] = {
+        "compound_sweep": f"1 Kennedy-Pendleton heat-bath sweep + {N_OR} over-relaxation sweeps",
+        "compound_sweeps_per_s": compound_per_s, "ms_per_compound_sweep": ms_o / n_cmp,
+        "value": compound_per_s * 4 * VOL * (N_OR + 1), "unit": UNIT + " (heat bath + over-relaxation)",
+        "roofline": {"bound": "hbm", "kernel": "or_phase_kernel",
+                     "achieved": BYTES_PER_OR_UPDATE * (VOL // 2) / or_phase_s / 1e9, "peak": peak,
+                     "unit": "GB/s", "avg_launch_us": or_phase_s * 1e6,
+                     "bytes_per_launch": BYTES_PER_OR_UPDATE * (VOL // 2)}}
+    for form in ("plain", "plain_kennedy_pendleton", "learned", "kp_overrelax"):
         r = out[form]["roofline"]
         r["frac"] = r["achieved"] / peak
     if args.tau_sweeps > 0:
         nblk = 8
         per = max(50, args.tau_sweeps // nblk)
-        plain_blocks, learned_blocks, kp_blocks = [], [], []
+        plain_blocks, learned_blocks, kp_blocks, or_blocks = [], [], [], []
+        per_or = max(50, per // (N_OR + 1) * 2)
         for k in range(nblk):
             plain_blocks.append(su2.su2_generate(lat, per, 1, 0)[0].copy())
             learned_blocks.append(su2.su2_learned_generate(lat, per, 1, 0.7)[0].copy())
             su2.su2_set_sampler(lat, su2.SU2_SAMPLER_KP)
             kp_blocks.append(su2.su2_generate(lat, per, 1, 0)[0].copy())
+            su2.su2_set_overrelax(lat, N_OR)
+            or_blocks.append(su2.su2_generate(lat, per_or, 1, 0)[0].copy())
+            su2.su2_set_overrelax(lat, 0)
             su2.su2_set_sampler(lat, su2.SU2_SAMPLER_CREUTZ)
         plain_blocks.append(su2.su2_generate(lat, per, 1, 0)[0].copy())
+        tau_o = np.mean([tau_int(b)[0] for b in or_blocks])
+        out["kp_overrelax"]["tau_int"] = float(tau_o)
+        out["kp_overrelax"]["tau_int_unit"] = "compound sweeps"
+        out["kp_overrelax"]["value_tau_adjusted"] = compound_per_s * 4 * VOL / (2 * tau_o)
+        d_o = np.array([or_blocks[k].mean() - 0.5 * (plain_blocks[k].mean() + plain_blocks[k + 1].mean())
+                        for k in range(nblk)])
+        se_o = d_o.std(ddof=1) / np.sqrt(nblk)
+        out["kp_overrelax"]["plaquette_minus_plain"] = float(d_o.mean())
+        out["kp_overrelax"]["plaquette_sigma"] = float(d_o.mean() / se_o) if se_o > 0 else None
         tau_p = np.mean([tau_int(b)[0] for b in plain_blocks])
         tau_l = np.mean([tau_int(b)[0] for b in learned_blocks])
         tau_k = np.mean([tau_int(b)[0] for b in kp_blocks])
@@ -378,7 +411,9 @@ def compare_forms(args, dist, lat, su2, torch, stream, tau_int):
         out["value_tau_adjusted"] = {"plain": out["plain"]["value_tau_adjusted"],
                                      "plain_kennedy_pendleton": out["plain_kennedy_pendleton"]["value_tau_adjusted"],
                                      "learned": out["learned"]["value_tau_adjusted"],
-                                     "convention": "link updates/s / (2 tau_int(plaquette)), tau_int = 1/2 + sum rho"}
+                                     "kp_overrelax": out["kp_overrelax"]["value_tau_adjusted"],
+                                     "convention": "4V x sweeps/s / (2 tau_int(plaquette)), tau_int = 1/2 + "
+                                                   "sum rho in sweeps (compound sweeps for kp_overrelax)"}
     return out
 
 

@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define SU2_ABI_VERSION 1
+#define SU2_ABI_VERSION 2
 
 typedef struct su2_lattice su2_lattice;
 
@@ -70,8 +70,11 @@ typedef struct {
     uint64_t trials[8];         /* heat-bath a0 trials of phase 2*mu + parity, summed over sweeps */
     uint64_t sampler_failures;  /* links whose draw hit the trial cap                         */
     uint32_t kernel_launches;   /* heat-bath phase launches (8 per sweep)                     */
-    uint32_t timed;             /* 1 if kernel_ms is valid (see su2_set_timing)               */
+    uint32_t timed;             /* 1 if kernel_ms / overrelax_ms are valid (su2_set_timing)   */
     double kernel_ms;           /* summed device time of the heat-bath phase kernels          */
+    uint64_t overrelax_sweeps;  /* over-relaxation sweeps performed (see su2_set_overrelax)   */
+    uint64_t overrelax_updates; /* 4 V per over-relaxation sweep                              */
+    double overrelax_ms;        /* summed device time of the over-relaxation phase kernels    */
 } su2_stats;
 
 /* Resumable state: with the links (su2_get_links) it determines every later sweep. */
@@ -127,6 +130,27 @@ su2_status su2_generate(su2_lattice *lat, int nsweeps, int measure_every, int re
 #define SU2_SAMPLER_CREUTZ 0
 #define SU2_SAMPLER_KP 1
 su2_status su2_set_sampler(su2_lattice *lat, int sampler);
+
+/* Over-relaxation (not in the paper; the usual companion of its heat bath:
+ * Adler, Phys. Rev. D 23 (1981) 2901; Creutz, Phys. Rev. D 36 (1987) 515).
+ * Each link U_mu(x) of a phase is replaced by its reflection in the staple,
+ *   U' = U~^dag U^dag U~^dag,  U~ = V/k  (U~ = 1 if k = 0),
+ * which keeps (1/2) Tr UV, so the action, and is its own inverse; no random
+ * numbers.  Same phase order as the heat bath (mu = 0..3, even then odd).
+ * Products (U~^dag U^dag) U~^dag in binary32 with the heat bath's rounding
+ * contract.  Not ergodic alone: it is interleaved with heat-bath sweeps.
+ *
+ * su2_overrelax_sweep: nsweeps over-relaxation sweeps now (asynchronous; the
+ *   heat-bath sweep counter is not advanced).
+ * su2_overrelax_phase: one phase (tests, diagnostics).
+ * su2_set_overrelax: every later heat-bath sweep of su2_heatbath_sweep and
+ *   su2_generate is followed by n_or over-relaxation sweeps (0 = none, the
+ *   default); su2_stats counts and times them separately.
+ * All three return SU2_E_INVAL for a NULL handle, mu or parity out of range,
+ * nsweeps < 0 or n_or outside 0 ... 64. */
+su2_status su2_overrelax_sweep(su2_lattice *lat, int nsweeps);
+su2_status su2_overrelax_phase(su2_lattice *lat, int mu, int parity);
+su2_status su2_set_overrelax(su2_lattice *lat, int n_or);
 
 /* a <- a / |a| for every link (the links drift from |a| = 1 by rounding). */
 su2_status su2_reunitarize(su2_lattice *lat);

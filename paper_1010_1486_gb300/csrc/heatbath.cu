@@ -276,61 +276,64 @@ su2_status launch_hb_phase(su2_lattice *lat, int mu, int parity, uint32_t sweep,
 }
 
 // ------------------------------------------------------------- timing
-su2_status timing_begin(su2_lattice *lat)
+su2_status timing_begin(su2_lattice *lat, EventLog &log)
 {
     if (!lat->timing) return SU2_OK;
-    while (lat->events.size() < lat->events_used + 2) {
+    while (log.events.size() < log.used + 2) {
         cudaEvent_t e;
         SU2_CUDA(cudaEventCreate(&e));
-        lat->events.push_back(e);
+        log.events.push_back(e);
     }
-    SU2_CUDA(cudaEventRecord(lat->events[lat->events_used], lat->stream));
+    SU2_CUDA(cudaEventRecord(log.events[log.used], lat->stream));
     return SU2_OK;
 }
 
-su2_status timing_end(su2_lattice *lat)
+su2_status timing_end(su2_lattice *lat, EventLog &log)
 {
     if (!lat->timing) return SU2_OK;
-    SU2_CUDA(cudaEventRecord(lat->events[lat->events_used + 1], lat->stream));
-    lat->events_used += 2;
+    SU2_CUDA(cudaEventRecord(log.events[log.used + 1], lat->stream));
+    log.used += 2;
     return SU2_OK;
 }
 
-su2_status timing_read(su2_lattice *lat, double *ms_out)
+su2_status timing_read(su2_lattice *lat, EventLog &log, double *ms_out)
 {
     double ms = 0.0;
-    if (lat->timing && lat->events_used) {
-        SU2_CUDA(cudaEventSynchronize(lat->events[lat->events_used - 1]));
-        for (size_t i = 0; i + 1 < lat->events_used; i += 2) {
+    if (lat->timing && log.used) {
+        SU2_CUDA(cudaEventSynchronize(log.events[log.used - 1]));
+        for (size_t i = 0; i + 1 < log.used; i += 2) {
             float t = 0.0f;
-            SU2_CUDA(cudaEventElapsedTime(&t, lat->events[i], lat->events[i + 1]));
+            SU2_CUDA(cudaEventElapsedTime(&t, log.events[i], log.events[i + 1]));
             ms += t;
         }
     }
     *ms_out = ms;
-    lat->events_used = 0;
+    log.used = 0;
     return SU2_OK;
 }
 
 static su2_status timed_phase(su2_lattice *lat, int mu, int parity, uint32_t sweep)
 {
-    su2_status st = timing_begin(lat);
+    su2_status st = timing_begin(lat, lat->hb_log);
     if (st == SU2_OK) st = launch_hb_phase(lat, mu, parity, sweep);
-    if (st == SU2_OK) st = timing_end(lat);
+    if (st == SU2_OK) st = timing_end(lat, lat->hb_log);
     return st;
 }
 
 static su2_status read_timing(su2_lattice *lat, su2_stats *stats)
 {
-    double ms = 0.0;
-    su2_status st = timing_read(lat, &ms);
+    double ms = 0.0, or_ms = 0.0;
+    su2_status st = timing_read(lat, lat->hb_log, &ms);
+    su2_status st2 = timing_read(lat, lat->or_log, &or_ms);
     if (stats) {
         stats->kernel_ms = ms;
+        stats->overrelax_ms = or_ms;
         stats->timed = lat->timing ? 1u : 0u;
     }
-    return st;
+    return st != SU2_OK ? st : st2;
 }
 
+// One heat-bath sweep, then the lattice's over-relaxation sweeps.
 static su2_status one_sweep(su2_lattice *lat)
 {
     for (int mu = 0; mu < 4; ++mu)
@@ -339,7 +342,7 @@ static su2_status one_sweep(su2_lattice *lat)
             if (st != SU2_OK) return st;
         }
     lat->sweep += 1;
-    return SU2_OK;
+    return lat->overrelax > 0 ? overrelax_sweeps(lat, lat->overrelax) : SU2_OK;
 }
 
 static su2_status ensure_history(su2_lattice *lat, int n)
@@ -371,7 +374,8 @@ su2_status su2_generate(su2_lattice *lat, int nsweeps, int measure_every, int re
     su2_status st = ensure_history(lat, nmeas);
     if (st != SU2_OK) return st;
     if ((st = launch_clear_counters(lat)) != SU2_OK) return st;
-    lat->events_used = 0;
+    lat->hb_log.used = 0;
+    lat->or_log.used = 0;
     int m = 0;
     for (int s = 1; s <= nsweeps; ++s) {
         if ((st = one_sweep(lat)) != SU2_OK) return st;
@@ -390,7 +394,11 @@ su2_status su2_generate(su2_lattice *lat, int nsweeps, int measure_every, int re
                                  cudaMemcpyDeviceToHost, lat->stream));
     if (stats) memset(stats, 0, sizeof *stats);
     st = collect_stats(lat, stats, (uint64_t)nsweeps);
-    if (stats) stats->kernel_launches = (uint32_t)(8 * nsweeps);
+    if (stats) {
+        stats->kernel_launches = (uint32_t)(8 * nsweeps);
+        stats->overrelax_sweeps = (uint64_t)nsweeps * (uint64_t)lat->overrelax;
+        stats->overrelax_updates = stats->overrelax_sweeps * 4ull * (uint64_t)lat->vol;
+    }
     su2_status st2 = read_timing(lat, stats);
     return st != SU2_OK ? st : st2;
 }
@@ -401,10 +409,12 @@ su2_status su2_heatbath_sweep(su2_lattice *lat, int nsweeps, su2_stats *stats)
     if (stats) return su2_generate(lat, nsweeps, 0, 0, nullptr, nullptr, stats);
     DeviceGuard guard(lat->device);
     su2_status st;
-    lat->events_used = 0;
+    lat->hb_log.used = 0;
+    lat->or_log.used = 0;
     for (int s = 0; s < nsweeps; ++s)
         if ((st = one_sweep(lat)) != SU2_OK) return st;
-    if (lat->timing) lat->events_used = 0;
+    lat->hb_log.used = 0;
+    lat->or_log.used = 0;
     return SU2_OK;
 }
 

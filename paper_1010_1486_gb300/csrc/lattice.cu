@@ -378,7 +378,8 @@ su2_status su2_destroy(su2_lattice *lat)
 {
     if (!lat) return SU2_OK;
     DeviceGuard guard(lat->device);
-    for (cudaEvent_t e : lat->events) cudaEventDestroy(e);
+    for (cudaEvent_t e : lat->hb_log.events) cudaEventDestroy(e);
+    for (cudaEvent_t e : lat->or_log.events) cudaEventDestroy(e);
     device_free(lat->staging, lat->staging_bytes, lat->device, lat->stream);
     device_free(lat->learned_block, lat->learned_bytes, lat->device, lat->stream);
     device_free(lat->scratch.history, sizeof(double) * 2 * (size_t)lat->scratch.history_cap, lat->device,

@@ -322,15 +322,15 @@ su2_status su2_learned_generate(su2_lattice *lat, int nsweeps, int measure_every
     const unsigned int ctl0[4] = {1u, 0u, 0u, 0u};
     SU2_CUDA(cudaMemcpyAsync(lat->learned_ctl, ctl0, sizeof ctl0, cudaMemcpyHostToDevice, lat->stream));
     SU2_CUDA(cudaMemsetAsync(lat->accept_slots, 0, sizeof(unsigned long long) * 9 * kAcceptSlots, lat->stream));
-    lat->events_used = 0;
+    lat->hb_log.used = 0;
     const double links = 4.0 * (double)lat->vol;
     int m = 0;
     for (int s = 1; s <= nsweeps; ++s) {
         for (int mu = 0; mu < 4; ++mu)
             for (int parity = 0; parity < 2; ++parity) {
-                if ((st = timing_begin(lat)) != SU2_OK) return st;
+                if ((st = timing_begin(lat, lat->hb_log)) != SU2_OK) return st;
                 if ((st = launch_learned_phase(lat, mu, parity)) != SU2_OK) return st;
-                if ((st = timing_end(lat)) != SU2_OK) return st;
+                if ((st = timing_end(lat, lat->hb_log)) != SU2_OK) return st;
                 if ((st = launch_hb_phase(lat, mu, parity, lat->sweep, lat->learned_ctl)) != SU2_OK) return st;
             }
         learned_decide_kernel<<<1, 32, 0, lat->stream>>>(lat->learned_ctl, lat->accept_slots + 8 * kAcceptSlots,
@@ -357,7 +357,7 @@ su2_status su2_learned_generate(su2_lattice *lat, int nsweeps, int measure_every
     memset(&plain, 0, sizeof plain);
     st = collect_stats(lat, &plain, (uint64_t)nsweeps);
     double kms = 0.0;
-    su2_status st_t = timing_read(lat, &kms);
+    su2_status st_t = timing_read(lat, lat->hb_log, &kms);
     if (st == SU2_OK) st = st_t;
     if (stats) {
         memset(stats, 0, sizeof *stats);

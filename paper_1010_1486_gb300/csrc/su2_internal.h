@@ -31,6 +31,14 @@ struct DeviceScratch {
 
 }  // namespace su2
 
+namespace su2 {
+// CUDA events recorded in pairs around timed kernel launches.
+struct EventLog {
+    std::vector<cudaEvent_t> events;
+    size_t used = 0;
+};
+}  // namespace su2
+
 struct su2_lattice {
     int ns = 0, nt = 0;
     int64_t vol = 0;  // Ns^3 Nt
@@ -50,9 +58,11 @@ struct su2_lattice {
     void *staging = nullptr;  // lex-ordered copy for get/set_links (allocated on demand)
     size_t staging_bytes = 0;
 
+    int overrelax = 0;  // over-relaxation sweeps after each heat-bath sweep
+
     bool timing = false;
-    std::vector<cudaEvent_t> events;  // pairs around timed phase launches
-    size_t events_used = 0;
+    su2::EventLog hb_log;  // heat-bath (and learned) phase launches
+    su2::EventLog or_log;  // over-relaxation phase launches
 
     // learned proposal (allocated by su2_set_proposal)
     void *learned_block = nullptr;
@@ -141,9 +151,12 @@ su2_status launch_polyakov(su2_lattice *lat, double *dst);
 su2_status launch_clear_counters(su2_lattice *lat);
 // CUDA events around a kernel on the lattice's stream (when timing is on),
 // and the summed duration of the recorded pairs (synchronises, then resets).
-su2_status timing_begin(su2_lattice *lat);
-su2_status timing_end(su2_lattice *lat);
-su2_status timing_read(su2_lattice *lat, double *ms);
+su2_status timing_begin(su2_lattice *lat, EventLog &log);
+su2_status timing_end(su2_lattice *lat, EventLog &log);
+su2_status timing_read(su2_lattice *lat, EventLog &log, double *ms);
+// Over-relaxation: one phase, and `n` sweeps (8 phases each, timed into or_log).
+su2_status launch_or_phase(su2_lattice *lat, int mu, int parity);
+su2_status overrelax_sweeps(su2_lattice *lat, int n);
 // Reads and clears the trial counters and flags (synchronises).
 su2_status collect_stats(su2_lattice *lat, su2_stats *stats, uint64_t sweeps);
 

@@ -43,12 +43,15 @@ class su2_stats(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_uint64), ("link_updates", ctypes.c_uint64),
                 ("trials", ctypes.c_uint64 * 8), ("sampler_failures", ctypes.c_uint64),
                 ("kernel_launches", ctypes.c_uint32), ("timed", ctypes.c_uint32),
-                ("kernel_ms", ctypes.c_double)]
+                ("kernel_ms", ctypes.c_double), ("overrelax_sweeps", ctypes.c_uint64),
+                ("overrelax_updates", ctypes.c_uint64), ("overrelax_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {"sweeps": self.sweeps, "link_updates": self.link_updates, "trials": list(self.trials),
                 "sampler_failures": self.sampler_failures, "kernel_launches": self.kernel_launches,
-                "timed": bool(self.timed), "kernel_ms": self.kernel_ms}
+                "timed": bool(self.timed), "kernel_ms": self.kernel_ms,
+                "overrelax_sweeps": self.overrelax_sweeps, "overrelax_updates": self.overrelax_updates,
+                "overrelax_ms": self.overrelax_ms}
 
 
 class su2_learned_stats(ctypes.Structure):
@@ -92,6 +95,9 @@ _SIGS = {
     "su2_device_links": [_P, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_size_t)],
     "su2_set_timing": [_P, _i32],
     "su2_set_sampler": [_P, _i32],
+    "su2_overrelax_sweep": [_P, _i32],
+    "su2_overrelax_phase": [_P, _i32, _i32],
+    "su2_set_overrelax": [_P, _i32],
     "su2_selftest_philox": [_P, _P, ctypes.c_size_t],
     "su2_selftest_math": [_i32, _P, _P, _P, ctypes.c_size_t],
     "su2_plaquette_noalloc": [_P, _i32, _i32, _P, _P],
@@ -283,6 +289,18 @@ def su2_device_links(lat: int):
 
 def su2_set_sampler(lat: int, sampler: int) -> None:
     _check(_lib.su2_set_sampler(lat, int(sampler)), "su2_set_sampler")
+
+
+def su2_overrelax_sweep(lat: int, nsweeps: int = 1) -> None:
+    _check(_lib.su2_overrelax_sweep(lat, nsweeps), "su2_overrelax_sweep")
+
+
+def su2_overrelax_phase(lat: int, mu: int, parity: int) -> None:
+    _check(_lib.su2_overrelax_phase(lat, mu, parity), "su2_overrelax_phase")
+
+
+def su2_set_overrelax(lat: int, n_or: int) -> None:
+    _check(_lib.su2_set_overrelax(lat, int(n_or)), "su2_set_overrelax")
 
 
 def su2_set_timing(lat: int, enable: bool) -> None:

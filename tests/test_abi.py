@@ -28,7 +28,9 @@ def test_every_declared_symbol_is_exported(su2):
         assert hasattr(lib, n), n
     core = {"su2_create", "su2_destroy", "su2_heatbath_sweep", "su2_reunitarize", "su2_plaquette", "su2_polyakov"}
     assert core <= set(names)
-    assert su2.su2_abi_version() == 1
+    assert su2.su2_abi_version() == 2
+    # su2_stats as declared: 8 + 8 + 8*8 + 8 + 4 + 4 + 8 + 8 + 8 + 8 bytes
+    assert ctypes.sizeof(su2.su2_stats) == 128
 
 
 @pytest.mark.parametrize("ns,nt", [(3, 4), (4, 3), (0, 4), (4, 0), (1, 2), (-2, 4), (2000, 2000)])
@@ -53,6 +55,9 @@ def test_null_and_enum_arguments(su2):
     assert lib.su2_get_state(None, None) == 1
     assert lib.su2_plaquette(None, None) == 1
     assert lib.su2_heatbath_sweep(None, 1, None) == 1
+    assert lib.su2_overrelax_sweep(None, 1) == 1
+    assert lib.su2_overrelax_phase(None, 0, 0) == 1
+    assert lib.su2_set_overrelax(None, 1) == 1
     assert lib.su2_destroy(None) == 0
     # allocator hooks must come in pairs
     assert lib.su2_set_allocator(su2.ALLOC_FN(lambda *a: None), su2.FREE_FN(), None) == 1
