@@ -87,6 +87,8 @@ def _load():
             "orc_heatbath_phase_kp": (i64, [i32, i32, f64, u64, u32, i32, i32, P, ctypes.POINTER(i64), i32]),
             "orc_kp_a0_v": (None, [f32, u64, u32, i64, P, P]),
             "orc_overrelax_link": (None, [P, P]),
+            "orc_wilson_loop_at": (f32, [i32, i32, P, i64, i32, i32, i32]),
+            "orc_wilson_loops": (None, [i32, i32, P, i32, i32, P, i32]),
             "orc_overrelax_phase": (None, [i32, i32, i32, i32, P, i32]),
             "orc_overrelax_sweep": (None, [i32, i32, P, i32]),
             "orc_mlp_forward": (None, [P, f32, P]),
@@ -260,6 +262,18 @@ def overrelax_phase(ns: int, nt: int, mu: int, parity: int, links: np.ndarray, n
 def overrelax_sweep(ns: int, nt: int, links: np.ndarray, nthreads: int = 1) -> None:
     """One over-relaxation sweep (mu = 0..3, even then odd), in place."""
     _load().orc_overrelax_sweep(ns, nt, _ptr(links), nthreads)
+
+
+def wilson_loops(ns: int, nt: int, links: np.ndarray, rmax: int, tmax: int, nthreads: int = 1) -> np.ndarray:
+    """W[R-1, T-1]: mean (1/2) Tr of the R x T space-time loops (binary32 per
+    loop, binary64 mean over sites and the three spatial directions)."""
+    out = np.zeros(rmax * tmax, dtype=np.float64)
+    _load().orc_wilson_loops(ns, nt, _ptr(links), rmax, tmax, _ptr(out), nthreads)
+    return out.reshape(rmax, tmax)
+
+
+def wilson_loop_at(ns: int, nt: int, links: np.ndarray, site: int, i: int, R: int, T: int) -> float:
+    return float(_load().orc_wilson_loop_at(ns, nt, _ptr(links), site, i, R, T))
 
 
 def kp_a0_many(bk: float, seed: int, n: int, eo0: int = 0):

@@ -790,3 +790,64 @@ void orc_overrelax_sweep(int ns, int nt, float *links, int nthreads)
     for (int mu = 0; mu < 4; ++mu)
         for (int p = 0; p < 2; ++p) orc_overrelax_phase(ns, nt, mu, p, links, nthreads);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Wilson loops in the space-time planes, the next observables after the    */
+/* plaquette and the Polyakov loop (not in the paper).  For a site x, a      */
+/* spatial direction i and extents R (along i) and T (along t):              */
+/*   S_R(y) = U_i(y) U_i(y+i) ... U_i(y+(R-1)i),                             */
+/*   T_T(y) = U_t(y) U_t(y+t) ... U_t(y+(T-1)t)   (products left to right),  */
+/*   A = S_R(x) T_T(x+R i),  B = T_T(x) S_R(x+T t),                          */
+/*   W = (1/2) Tr A B^dag = A . B   (the four-component dot product),        */
+/* which is the closed loop x -> x+Ri -> x+Ri+Tt -> x+Tt -> x.  Per loop in  */
+/* binary32 with the link-arithmetic contract; the mean over x and i = 0..2  */
+/* in binary64.  out[(R-1) tmax + (T-1)], R = 1..rmax, T = 1..tmax.          */
+/* ------------------------------------------------------------------------ */
+static int64_t site_step(int64_t s, int mu, int n, int ns, int nt)
+{
+    int c[4];
+    site_coords(s, ns, c);
+    int L = extent(ns, nt, mu);
+    c[mu] = (int)(((int64_t)c[mu] + n) % L);
+    return site_index(c, ns);
+}
+
+/* product of the n links U_mu(y) U_mu(y+mu) ... (n >= 1) */
+static void line_product(const float *links, int64_t y, int mu, int n, int ns, int nt, float out[4])
+{
+    memcpy(out, link_at(links, y, mu), 4 * sizeof(float));
+    for (int j = 1; j < n; ++j) {
+        float t[4];
+        orc_quat_mul(out, link_at(links, site_step(y, mu, j, ns, nt), mu), t);
+        memcpy(out, t, sizeof t);
+    }
+}
+
+float orc_wilson_loop_at(int ns, int nt, const float *links, int64_t s, int i, int R, int T)
+{
+    float sr_x[4], tt_xr[4], tt_x[4], sr_xt[4], a[4], b[4];
+    line_product(links, s, i, R, ns, nt, sr_x);
+    line_product(links, site_step(s, i, R, ns, nt), 3, T, ns, nt, tt_xr);
+    line_product(links, s, 3, T, ns, nt, tt_x);
+    line_product(links, site_step(s, 3, T, ns, nt), i, R, ns, nt, sr_xt);
+    orc_quat_mul(sr_x, tt_xr, a);
+    orc_quat_mul(tt_x, sr_xt, b);
+    return dot4(a[0], b[0], a[1], b[1], a[2], b[2], a[3], b[3]);
+}
+
+void orc_wilson_loops(int ns, int nt, const float *links, int rmax, int tmax, double *out, int nthreads)
+{
+    int64_t vol = (int64_t)ns * ns * ns * nt;
+    for (int R = 1; R <= rmax; ++R)
+        for (int T = 1; T <= tmax; ++T) {
+            double acc = 0.0;
+#ifdef _OPENMP
+            if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(static) reduction(+ : acc) num_threads(nthreads)
+#endif
+            for (int64_t s = 0; s < vol; ++s)
+                for (int i = 0; i < 3; ++i) acc += (double)orc_wilson_loop_at(ns, nt, links, s, i, R, T);
+            out[(R - 1) * tmax + (T - 1)] = acc / (3.0 * (double)vol);
+        }
+    (void)nthreads;
+}
