@@ -165,6 +165,18 @@ su2_status su2_plaquette(su2_lattice *lat, double *out);
  * sum.  Synchronous. */
 su2_status su2_polyakov(su2_lattice *lat, double *out);
 
+/* Space-time Wilson loops (not in the paper; the observables after the
+ * plaquette and the Polyakov loop, from which the static potential follows).
+ * For site x, spatial direction i = 0..2 and extents R, T:
+ *   S_R(y) = U_i(y) U_i(y+i) ... U_i(y+(R-1)i),  T_T(y) = U_t(y) ... U_t(y+(T-1)t),
+ *   W = (1/2) Tr [S_R(x) T_T(x+Ri)] [T_T(x) S_R(x+Tt)]^dag,
+ * line products left to right in binary32, the mean over x and i in binary64.
+ * out (host, rmax * tmax doubles) receives W at out[(R-1) tmax + (T-1)] for
+ * R = 1..rmax, T = 1..tmax.  Requires 1 <= rmax <= min(16, Ns) and
+ * 1 <= tmax <= min(64, Nt) (else SU2_E_INVAL).  Synchronous; allocates and
+ * frees a small device buffer. */
+su2_status su2_wilson_loops(su2_lattice *lat, int rmax, int tmax, double *out);
+
 /* Copies all links to / from a host buffer of 16 V floats laid out
  * [lex site][mu][a0..a3].  Synchronous.  set_links does not reunitarize. */
 su2_status su2_get_links(su2_lattice *lat, float *host);

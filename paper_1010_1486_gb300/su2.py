@@ -96,6 +96,7 @@ _SIGS = {
     "su2_set_timing": [_P, _i32],
     "su2_set_sampler": [_P, _i32],
     "su2_overrelax_sweep": [_P, _i32],
+    "su2_wilson_loops": [_P, _i32, _i32, _P],
     "su2_overrelax_phase": [_P, _i32, _i32],
     "su2_set_overrelax": [_P, _i32],
     "su2_selftest_philox": [_P, _P, ctypes.c_size_t],
@@ -289,6 +290,13 @@ def su2_device_links(lat: int):
 
 def su2_set_sampler(lat: int, sampler: int) -> None:
     _check(_lib.su2_set_sampler(lat, int(sampler)), "su2_set_sampler")
+
+
+def su2_wilson_loops(lat: int, rmax: int, tmax: int) -> np.ndarray:
+    """W[R-1, T-1], the mean (1/2) Tr of the R x T space-time Wilson loops."""
+    out = np.zeros(rmax * tmax, dtype=np.float64)
+    _check(_lib.su2_wilson_loops(lat, rmax, tmax, out.ctypes.data_as(ctypes.c_void_p)), "su2_wilson_loops")
+    return out.reshape(rmax, tmax)
 
 
 def su2_overrelax_sweep(lat: int, nsweeps: int = 1) -> None:

@@ -58,6 +58,7 @@ def test_null_and_enum_arguments(su2):
     assert lib.su2_overrelax_sweep(None, 1) == 1
     assert lib.su2_overrelax_phase(None, 0, 0) == 1
     assert lib.su2_set_overrelax(None, 1) == 1
+    assert lib.su2_wilson_loops(None, 1, 1, None) == 1
     assert lib.su2_destroy(None) == 0
     # allocator hooks must come in pairs
     assert lib.su2_set_allocator(su2.ALLOC_FN(lambda *a: None), su2.FREE_FN(), None) == 1
