@@ -56,3 +56,23 @@ def tau_int(series, s_factor: float = 1.5):
     dtau = tau * math.sqrt(2.0 * (2.0 * window + 1.0) / n)
     err_mean = math.sqrt(max(cf, 0.0) / n)
     return tau, dtau, window, err_mean
+
+
+def effective_potential(w) -> np.ndarray:
+    """Static-potential estimates from Wilson loops W[R-1, T-1]:
+    V_eff(R, T) = log(W(R, T) / W(R, T+1)), shape (rmax, tmax - 1).  For large
+    T, W(R, T) ~ C(R) exp(-V(R) T), so V_eff(R, T) -> V(R) (NaN unless both
+    loops are positive)."""
+    w = np.asarray(w, dtype=np.float64)
+    ok = (w[:, :-1] > 0) & (w[:, 1:] > 0)
+    a = np.where(ok, w[:, :-1], 1.0)
+    b = np.where(ok, w[:, 1:], 1.0)
+    return np.where(ok, np.log(a / b), np.nan)
+
+
+def cornell_fit(r, v):
+    """Least-squares fit V(R) = V0 - alpha/R + sigma R; returns (V0, alpha, sigma)."""
+    r = np.asarray(r, dtype=np.float64)
+    a = np.stack([np.ones_like(r), -1.0 / r, r], axis=1)
+    coef, *_ = np.linalg.lstsq(a, np.asarray(v, dtype=np.float64), rcond=None)
+    return tuple(float(c) for c in coef)

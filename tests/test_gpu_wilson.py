@@ -59,3 +59,21 @@ def test_bad_extents(made):
     for rmax, tmax in ((0, 1), (1, 0), (7, 1), (1, 5), (17, 1)):
         with pytest.raises(su2.SU2Error):
             su2.su2_wilson_loops(h, rmax, tmax)
+
+
+def test_static_potential_rises_with_distance(made):
+    """Confinement at beta = 2.5 on 16^4: the effective potential from
+    W(R, T) / W(R, T+1) grows with R."""
+    from paper_1010_1486_gb300.analysis import effective_potential
+
+    h = su2.su2_create(16, 16, 2.5, 12, su2.SU2_COLD)
+    made.append(h)
+    su2.su2_set_sampler(h, su2.SU2_SAMPLER_KP)
+    su2.su2_set_overrelax(h, 2)
+    su2.su2_heatbath_sweep(h, 100)
+    ws = []
+    for _ in range(40):
+        su2.su2_heatbath_sweep(h, 2)
+        ws.append(su2.su2_wilson_loops(h, 4, 4))
+    v = effective_potential(np.mean(ws, axis=0))[:, 1]  # T = 2 -> 3
+    assert np.all(np.isfinite(v)) and np.all(np.diff(v) > 0), v
