@@ -32,213 +32,217 @@ struct HbParams {
     const unsigned int *gate;  // if non-NULL and *gate == 1 the phase is left to the learned kernel
 };
 
-constexpr int kHbWarps = kHbThreads / 32;
+constexpr int kCrThreads = 256;
+constexpr int kCrWarps = kCrThreads / 32;
+constexpr int kCrQueue = 64;  // per warp and queue: at most 31 left over + 32 pushed at once
+#ifndef SU2_HB_MIN_BLOCKS
+#define SU2_HB_MIN_BLOCKS 3
+#endif
+constexpr int kCrMinBlocks = SU2_HB_MIN_BLOCKS;  // blocks per SM the register budget is set for
 
-// One heat-bath phase (mu = MU, sites of parity p.parity).
+// Per-warp shared-memory queues of the phase kernel.
+struct CrQueues {
+    // links still without an accepted a0: U~^dag, beta k, exp(-2 beta k), index, next Philox block
+    float4 r_ut[kCrQueue];
+    float r_bk[kCrQueue], r_e[kCrQueue];
+    int r_eo[kCrQueue], r_blk[kCrQueue];
+    // links with an accepted a0 waiting for their direction and store
+    float4 d_ut[kCrQueue];
+    float d_a0[kCrQueue];
+    int d_eo[kCrQueue];
+};
+
+// One heat-bath phase (mu = MU, sites of parity p.parity), Creutz's sampler.
 //
-// The V/2 sites are cut into rounds of 32 consecutive even/odd indices; warp
-// w takes rounds w, w + W, w + 2W, ... (W warps in the grid), so all warps
-// sweep the lattice together and neighbour links are re-read from L2.  Each
-// warp runs one loop whose iterations interleave three kinds of work:
-//   A  one third of the staple of its next round (the six links of one nu):
-//      the loads are issued first and used at the end of the iteration, so
-//      their latency hides behind B;  after the third part, U~^dag, beta k
-//      and exp(-2 beta k) of the 32 sites go into the warp's ring of R rounds;
-//   B  one Philox block (two Creutz trials) for the pending link each lane
-//      holds; a lane whose link is accepted takes the next pending link of the
-//      ring, so no lane idles while the slowest draw of its round finishes;
-//   C  once every link of the oldest round is accepted, the 32 lanes draw the
-//      directions and store U' = a U~^dag together (coalesced).
-// A link's random numbers depend only on its counter, never on the lane or
-// the iteration that handles it, so the phase computes exactly the
-// one-thread-per-link definition.  Every iteration advances A, B or C, and B
-// ends every link within kMaxTrials trials, so the loop terminates.
-template <int MU, int R>
-__global__ void __launch_bounds__(kHbThreads) hb_phase_kernel(const HbParams p)
+// Warp w of the persistent grid takes the rounds of 32 consecutive links w,
+// w + W, ... (W warps).  Each loop iteration (three per round) issues the six
+// loads of one nu-group of the next round, does one third of the current
+// round's work, then folds the loaded group into the next round's staple:
+//   part 0  k, U~^dag, beta k, exp(-2 beta k); Philox block 0 (trials 0, 1);
+//   part 1  trials 0 and 1; an accepted link goes to the warp's direction
+//           queue, a link with both rejected to its retry queue;
+//   part 2  every 32 links in the direction queue: directions and stores.
+// Whenever 32 links wait for a retry, the whole warp draws their next Philox
+// block (two more trials each); accepted links move to the direction queue,
+// the others go back to the retry queue.  At beta k ~ 30 two trials accept
+// 41% of links, so the lanes stay busy instead of waiting for the slowest
+// lane of a round.  Every draw depends only on the link's counters (trial t
+// in words 2(t&1), 2(t&1)+1 of block t>>1; direction block 0), so the phase
+// computes exactly the one-thread-per-link definition.  Lanes past the end
+// work on a clamped index and drop their results.
+template <int MU>
+__global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(const HbParams p)
 {
     if (p.gate != nullptr && *(volatile const unsigned int *)p.gate == 1u) return;
-    constexpr int Q = 32 * R;
-    __shared__ float4 s_ut[kHbWarps][Q];
-    __shared__ float s_bk[kHbWarps][Q];  // beta k; after acceptance a0 (NaN: trial cap hit)
-    __shared__ float s_e[kHbWarps][Q];
-    __shared__ int s_done[kHbWarps][R];
+    __shared__ CrQueues s_q[kCrWarps];
     const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    float4 *const ut_q = s_ut[wib];
-    float *const bk_q = s_bk[wib];
-    float *const e_q = s_e[wib];
-    int *const done_q = s_done[wib];
+    CrQueues &Q = s_q[threadIdx.x >> 5];
     const unsigned int lanes_below = (1u << lane) - 1u;
-    const int warp_global = blockIdx.x * kHbWarps + wib;
-    const int nwarps = gridDim.x * kHbWarps;
-    const int vh = p.g.vh;
-    const int rounds_total = (vh + 31) >> 5;
-    const int my_rounds = warp_global < rounds_total ? (rounds_total - warp_global + nwarps - 1) / nwarps : 0;
+    const int stride = gridDim.x * kCrThreads;
+    const int last = p.g.vh - 1;
     const uint32_t sw_creutz = stream_word(kCreutz, (uint32_t)p.parity, MU);
     const uint32_t sw_dir = stream_word(kDirection, (uint32_t)p.parity, MU);
+    unsigned int trials = 0;
+    int retry_n = 0, done_n = 0;  // warp-uniform queue lengths
 
-    if (lane < R) done_q[lane] = 0;
-    unsigned int my_trials = 0;
-
-    int a = 0, sub = 0;  // A: rounds produced, part (0..2) of the next one
-    int f = 0;           // C: rounds finalised
-    int produced = 0;    // valid links produced so far (their sequence numbers are 0 .. produced-1)
-    int claim = 0;       // next sequence number to hand out
-    int item = -1;       // B: sequence number of this lane's pending link
-    int item_eo = 0;
-    uint32_t blk = 0;
-    float bk = 0.0f, e = 0.0f, ome = 1.0f;
-    bool haar = false;
-    Coord xa;            // A: site of this lane in round a
-    int lex_pa = 0;
-    float4 va = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-
-    while (true) {
+    auto push_done = [&](bool ok, float4 ut, float a0, int eo) {
+        const unsigned int m = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+            const int q = done_n + __popc(m & lanes_below);
+            Q.d_ut[q] = ut;
+            Q.d_a0[q] = a0;
+            Q.d_eo[q] = eo;
+        }
+        done_n += __popc(m);
+    };
+    auto push_retry = [&](bool again, float4 ut, float bk, float e, int eo, int blk) {
+        const unsigned int m = __ballot_sync(0xffffffffu, again);
+        if (again) {
+            const int q = retry_n + __popc(m & lanes_below);
+            Q.r_ut[q] = ut;
+            Q.r_bk[q] = bk;
+            Q.r_e[q] = e;
+            Q.r_eo[q] = eo;
+            Q.r_blk[q] = blk;
+        }
+        retry_n += __popc(m);
+    };
+    // directions and stores of direction-queue entries [first, first + n)
+    auto direction_pass = [&](int first, int n) {
         __syncwarp();
-        // ---- C: finalise every complete round, oldest first
-        while (f < a) {
-            const int k = warp_global + f * nwarps;
-            const int rsize = min(32, vh - 32 * k);
-            if (done_q[f % R] < rsize) break;
-            if (lane < rsize) {
-                const int slot = (f % R) * 32 + lane;
-                const int eo = 32 * k + lane;
-                const float a0 = bk_q[slot];
-                if (a0 == a0) {
-                    const uint4 d = philox_rk(make_uint4((uint32_t)eo, p.sweep, sw_dir, 0u), p.rk);
-                    p.links[link_index(p.g, MU, p.parity, eo)] = direction_update(a0, ut_q[slot], d);
-                } else {
-                    atomicAdd(&p.flags[0], 1u);
-                }
-            }
-            __syncwarp();
-            if (lane == 0) done_q[f % R] = 0;
-            __syncwarp();
-            ++f;
+        if (lane < n) {
+            const int q = first + lane;
+            const int eo = Q.d_eo[q];
+            const uint4 wd = philox_rk(make_uint4((uint32_t)eo, p.sweep, sw_dir, 0u), p.rk);
+            p.links[link_index(p.g, MU, p.parity, eo)] = direction_update(Q.d_a0[q], Q.d_ut[q], wd);
         }
-        if (f == my_rounds) break;
+        __syncwarp();
+    };
+    auto flush_done = [&]() {
+        while (done_n >= 32) {
+            done_n -= 32;
+            direction_pass(done_n, 32);
+        }
+    };
+    // next Philox block of retry-queue entries [first, first + n)
+    auto retry_pass = [&](int first, int n) {
+        __syncwarp();
+        const bool have = lane < n;
+        float4 ut = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+        float bk = 0.0f, e = 0.0f;
+        int eo = 0, blk = 0;
+        if (have) {
+            const int q = first + lane;
+            ut = Q.r_ut[q];
+            bk = Q.r_bk[q];
+            e = Q.r_e[q];
+            eo = Q.r_eo[q];
+            blk = Q.r_blk[q];
+        }
+        __syncwarp();
+        bool ok = false, again = false;
+        float a0 = 0.0f;
+        if (have) {
+            const uint4 w = philox_rk(make_uint4((uint32_t)eo, p.sweep, sw_creutz, (uint32_t)blk), p.rk);
+            const bool haar = bk < kHaarBelow;
+            const float ome = __fsub_rn(1.0f, e);
+            float c1, c2;
+            const bool ok1 = creutz_trial(uniform01(w.x), uniform01(w.y), bk, e, ome, haar, c1);
+            const bool ok2 = creutz_trial(uniform01(w.z), uniform01(w.w), bk, e, ome, haar, c2);
+            ok = ok1 || ok2;
+            a0 = ok1 ? c1 : c2;
+            if (ok) {
+                trials += (unsigned int)(2 * blk + (ok1 ? 1 : 2));
+            } else if (blk + 1 < kMaxTrials / 2) {
+                again = true;
+            } else {
+                atomicAdd(&p.flags[0], 1u);  // trial cap: the link keeps its old value
+                trials += (unsigned int)kMaxTrials;
+            }
+        }
+        push_retry(again, ut, bk, e, eo, blk + 1);
+        push_done(ok, ut, a0, eo);
+        flush_done();
+    };
 
-        // ---- hand pending links to idle lanes
-        {
-            const unsigned int need = __ballot_sync(0xffffffffu, item < 0);
-            const int avail = produced - claim;
-            if (item < 0) {
-                const int rank = __popc(need & lanes_below);
-                if (rank < avail) {
-                    item = claim + rank;
-                    const int slot = item % Q;
-                    const int k = warp_global + (item >> 5) * nwarps;
-                    item_eo = 32 * k + (item & 31);
-                    blk = 0;
-                    bk = bk_q[slot];
-                    e = e_q[slot];
-                    ome = __fsub_rn(1.0f, e);
-                    haar = bk < kHaarBelow;
-                }
-            }
-            claim += min(__popc(need), avail);
-        }
-
-        const bool do_a = a < my_rounds && a < f + R;
-        const int a_k = warp_global + a * nwarps;
-        const bool a_valid = do_a && 32 * a_k + lane < vh;
-        NuLinks nl;
-        // ---- A (issue): the six links of one nu for this lane's site of round a
-        if (a_valid) {
-            if (sub == 0) {
-                xa = eo_to_coord(p.g, 32 * a_k + lane, p.parity);
-                lex_pa = lex_fwd(p.g, xa.lex, xa.c[MU], MU);
-                va = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            }
-            // the three directions nu != MU, ascending
-            if (sub == 0)
-                nl = load_nu<MU, (MU == 0 ? 1 : 0)>(p.links, p.g, xa, lex_pa, p.parity);
-            else if (sub == 1)
-                nl = load_nu<MU, (MU <= 1 ? 2 : 1)>(p.links, p.g, xa, lex_pa, p.parity);
-            else
-                nl = load_nu<MU, (MU <= 2 ? 3 : 2)>(p.links, p.g, xa, lex_pa, p.parity);
-        }
-
-        // ---- B: one Philox block (two trials) for the pending link
-        if (item >= 0) {
-            const uint4 w = philox_rk(make_uint4((uint32_t)item_eo, p.sweep, sw_creutz, blk), p.rk);
-            float cand;
-            uint32_t t = 0;
-            if (creutz_trial(uniform01(w.x), uniform01(w.y), bk, e, ome, haar, cand))
-                t = 2 * blk + 1;
-            else if (creutz_trial(uniform01(w.z), uniform01(w.w), bk, e, ome, haar, cand))
-                t = 2 * blk + 2;
-            bool finished = false;
-            if (t) {
-                my_trials += t;
-                finished = true;
-            } else if (++blk == (uint32_t)(kMaxTrials / 2)) {
-                cand = __int_as_float(0x7fc00000);  // NaN: trial cap hit, the link keeps its value
-                my_trials += kMaxTrials;
-                finished = true;
-            }
-            if (finished) {
-                bk_q[item % Q] = cand;
-                atomicAdd(&done_q[(item >> 5) % R], 1);
-                item = -1;
-            }
-        }
-
-        // ---- A (use): add the two staple terms of nu; after the third part park the site
-        if (do_a) {
-            if (a_valid) {
-                va = add_nu_terms(va, nl);
-                if (sub == 2) {
-                    const DrawSetup d = prepare_draw(va, p.beta);
-                    const int slot = (a % R) * 32 + lane;
-                    ut_q[slot] = d.ut;
-                    bk_q[slot] = d.bk;
-                    e_q[slot] = d.e;
-                }
-            }
-            if (++sub == 3) {
-                sub = 0;
-                produced += min(32, vh - 32 * a_k);
-                ++a;
-            }
-        }
+    int base = blockIdx.x * kCrThreads + (threadIdx.x & ~31);
+    int cur = base + lane;
+    float4 v_cur = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (base < p.g.vh) {
+        const int e = min(cur, last);
+        const Coord x = eo_to_coord(p.g, e, p.parity);
+        const int e_p = eo_fwd<MU>(p.g, x, e);
+        v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 0>::value>(p.links, p.g, x, e, e_p, p.parity));
+        v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 1>::value>(p.links, p.g, x, e, e_p, p.parity));
+        v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 2>::value>(p.links, p.g, x, e, e_p, p.parity));
     }
-    const unsigned int wsum = __reduce_add_sync(0xffffffffu, my_trials);
+    while (base < p.g.vh) {  // warp-uniform
+        const bool valid = cur <= last;
+        const int nxt = cur + stride;
+        const int en = min(nxt, last);
+        const Coord xn = eo_to_coord(p.g, en, p.parity);
+        const int en_p = eo_fwd<MU>(p.g, xn, en);
+        // ---- part 0
+        NuLinks nl = load_nu_eo<MU, OtherDir<MU, 0>::value>(p.links, p.g, xn, en, en_p, p.parity);
+        const DrawSetup d = prepare_draw(v_cur, p.beta);
+        const uint4 w = philox_rk(make_uint4((uint32_t)cur, p.sweep, sw_creutz, 0u), p.rk);
+        float4 v_next = add_nu_terms(make_float4(0.0f, 0.0f, 0.0f, 0.0f), nl);
+        // ---- part 1
+        nl = load_nu_eo<MU, OtherDir<MU, 1>::value>(p.links, p.g, xn, en, en_p, p.parity);
+        {
+            const bool haar = d.bk < kHaarBelow;
+            const float ome = __fsub_rn(1.0f, d.e);
+            float c1, c2;
+            const bool ok1 = creutz_trial(uniform01(w.x), uniform01(w.y), d.bk, d.e, ome, haar, c1);
+            const bool ok2 = creutz_trial(uniform01(w.z), uniform01(w.w), d.bk, d.e, ome, haar, c2);
+            const bool ok = valid && (ok1 || ok2);
+            trials += ok ? (ok1 ? 1u : 2u) : 0u;
+            push_done(ok, d.ut, ok1 ? c1 : c2, cur);
+            push_retry(valid && !ok1 && !ok2, d.ut, d.bk, d.e, cur, 1);
+        }
+        v_next = add_nu_terms(v_next, nl);
+        // ---- part 2
+        nl = load_nu_eo<MU, OtherDir<MU, 2>::value>(p.links, p.g, xn, en, en_p, p.parity);
+        flush_done();
+        v_next = add_nu_terms(v_next, nl);
+        while (retry_n >= 32) {
+            retry_n -= 32;
+            retry_pass(retry_n, 32);
+        }
+        base += stride;
+        cur = nxt;
+        v_cur = v_next;
+    }
+    while (retry_n > 0) {
+        const int n = min(retry_n, 32);
+        retry_n -= n;
+        retry_pass(retry_n, n);
+    }
+    if (done_n > 0) direction_pass(0, done_n);
+    const unsigned int wsum = __reduce_add_sync(0xffffffffu, trials);
     if (lane == 0 && wsum)
-        atomicAdd(&p.trial_slots[(2 * MU + p.parity) * kTrialSlots + (warp_global & (kTrialSlots - 1))],
+        atomicAdd(&p.trial_slots[(2 * MU + p.parity) * kTrialSlots +
+                                 ((blockIdx.x * kCrWarps + (threadIdx.x >> 5)) & (kTrialSlots - 1))],
                   (unsigned long long)wsum);
 }
 
-// Depth R of each warp's ring (rounds of 32 links in flight).  SU2_HB_QUEUE
-// = 2 | 4 | 8 overrides the default of 8 (tuning).
-static int queue_depth()
-{
-    static const int depth = [] {
-        const char *env = getenv("SU2_HB_QUEUE");
-        const int d = env ? atoi(env) : 8;
-        return (d == 2 || d == 4) ? d : 8;
-    }();
-    return depth;
-}
-
-template <int MU, int R>
+template <int MU>
 static cudaError_t launch_hb(const HbParams &p, int device, cudaStream_t stream)
 {
     static int blocks_per_sm[64] = {};
     static int num_sms[64] = {};
     if (device < 0 || device >= 64) device = 0;
     if (!blocks_per_sm[device]) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[device],
-                                                                      hb_phase_kernel<MU, R>, kHbThreads, 0);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[device], hb_phase_kernel<MU>,
+                                                                      kCrThreads, 0);
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&num_sms[device], cudaDevAttrMultiProcessorCount, device);
         if (e != cudaSuccess) return e;
         if (blocks_per_sm[device] < 1) blocks_per_sm[device] = 1;
     }
-    const int rounds = (p.g.vh + 31) / 32;
-    const int want = (rounds + kHbWarps - 1) / kHbWarps;
+    const int want = (p.g.vh + kCrThreads - 1) / kCrThreads;
     const int grid = std::max(1, std::min(want, blocks_per_sm[device] * num_sms[device]));
-    hb_phase_kernel<MU, R><<<grid, kHbThreads, 0, stream>>>(p);
+    hb_phase_kernel<MU><<<grid, kCrThreads, 0, stream>>>(p);
     return cudaGetLastError();
 }
 
@@ -255,21 +259,12 @@ su2_status launch_hb_phase(su2_lattice *lat, int mu, int parity, uint32_t sweep,
     p.sweep = sweep;
     p.trial_slots = lat->scratch.trials;
     p.flags = lat->scratch.flags;
-    const int R = queue_depth();
     cudaError_t e;
-    switch (R * 4 + mu) {
-    case 8: e = launch_hb<0, 2>(p, lat->device, lat->stream); break;
-    case 9: e = launch_hb<1, 2>(p, lat->device, lat->stream); break;
-    case 10: e = launch_hb<2, 2>(p, lat->device, lat->stream); break;
-    case 11: e = launch_hb<3, 2>(p, lat->device, lat->stream); break;
-    case 16: e = launch_hb<0, 4>(p, lat->device, lat->stream); break;
-    case 17: e = launch_hb<1, 4>(p, lat->device, lat->stream); break;
-    case 18: e = launch_hb<2, 4>(p, lat->device, lat->stream); break;
-    case 19: e = launch_hb<3, 4>(p, lat->device, lat->stream); break;
-    case 32: e = launch_hb<0, 8>(p, lat->device, lat->stream); break;
-    case 33: e = launch_hb<1, 8>(p, lat->device, lat->stream); break;
-    case 34: e = launch_hb<2, 8>(p, lat->device, lat->stream); break;
-    default: e = launch_hb<3, 8>(p, lat->device, lat->stream); break;
+    switch (mu) {
+    case 0: e = launch_hb<0>(p, lat->device, lat->stream); break;
+    case 1: e = launch_hb<1>(p, lat->device, lat->stream); break;
+    case 2: e = launch_hb<2>(p, lat->device, lat->stream); break;
+    default: e = launch_hb<3>(p, lat->device, lat->stream); break;
     }
     SU2_CUDA(e);
     return SU2_OK;
