@@ -47,6 +47,7 @@ BYTES_PER_UPDATE = 128  # reads 3.5 V + writes 0.5 V float4 per phase of V/2 upd
 BYTES_PER_LEARNED_UPDATE = 144  # + the old link of the updated direction and parity
 BYTES_PER_OR_UPDATE = 144  # over-relaxation: the staple links, the old link, the new link
 N_OR = 3  # over-relaxation sweeps after each heat-bath sweep in the compound form
+TRAIN_BATCH = 16384  # training mini-batch of the learned proposal
 HB_SOURCES = ["paper_1010_1486_gb300/csrc/heatbath.cu", "paper_1010_1486_gb300/csrc/su2_device.cuh"]
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "hb_phase_48x48x48x48_beta6.md")
 
@@ -64,7 +65,7 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sample length")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--learned-pairs", type=int, default=1_000_000, help="training pairs (0 = skip the learned form)")
-    ap.add_argument("--train-steps", type=int, default=1500)
+    ap.add_argument("--train-steps", type=int, default=3000, help="Adam steps of each of the two training stages")
     ap.add_argument("--batched-steps", type=int, default=200, help="sweeps of the 64-lattice batch (0 = skip)")
     return ap.parse_args(argv)
 
@@ -296,7 +297,8 @@ def compare_forms(args, dist, lat, su2, torch, stream, tau_int):
     t0 = time.perf_counter()
     pairs = learn.collect(lat, NS, NT, args.learned_pairs, sweeps_between=1)
     t1 = time.perf_counter()
-    w, losses, s_lo, s_hi = learn.train(pairs, steps=args.train_steps, batch=4096, lr=2e-3, seed=11)
+    w, losses, s_lo, s_hi = learn.train(pairs, steps=args.train_steps, batch=TRAIN_BATCH, lr=3e-3, seed=11,
+                                        tail_steps=args.train_steps, tail_lr=3e-4)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     del pairs
@@ -353,7 +355,8 @@ def compare_forms(args, dist, lat, su2, torch, stream, tau_int):
                                     "peak": peak, "unit": "GB/s", "avg_launch_us": learned_phase_s * 1e6,
                                     "bytes_per_launch": BYTES_PER_LEARNED_UPDATE * (VOL // 2)},
                        "gpu_launches": st_l["kernel_launches"] * 2 + args.steps * 3,
-                       "training": {"pairs": args.learned_pairs, "steps": args.train_steps, "batch": 4096,
+                       "training": {"pairs": args.learned_pairs, "steps": 2 * args.train_steps, "batch": TRAIN_BATCH,
+                                    "schedule": f"{args.train_steps} Adam steps at 3e-3, {args.train_steps} at 3e-4",
                                     "collect_s": t1 - t0, "train_s": t2 - t1,
                                     "loss_first": float(losses[:10].mean()), "loss_last": float(losses[-50:].mean())}}}
     out["kp_overrelax"] = {

@@ -77,12 +77,15 @@ __device__ __forceinline__ unsigned int block_sum_u32(unsigned int v)
 template <int MU>
 __global__ void __launch_bounds__(kLearnThreads, kLearnMinBlocks) learned_phase_kernel(const LearnedParams p)
 {
-    extern __shared__ float s_table[];
+    extern __shared__ float2 s_pairs[];
     if (*(volatile const unsigned int *)p.gate != 1u) return;
-    const int n_tab = p.G * learned::kParams;
-    for (int i = threadIdx.x; i < n_tab; i += blockDim.x) s_table[i] = p.table[i];
+    const int n_pairs = (p.G - 1) * learned::kParams;
+    for (int i = threadIdx.x; i < n_pairs; i += blockDim.x) {
+        const float r0 = p.table[i];
+        s_pairs[i] = make_float2(r0, __fsub_rn(p.table[i + learned::kParams], r0));
+    }
     __syncthreads();
-    const learned::Proposal pr{s_table, p.G, p.s_lo, p.s_hi, p.mean, p.scale};
+    const learned::Proposal pr{s_pairs, p.G, p.s_lo, learned::table_inv_ds(p.G, p.s_lo, p.s_hi), p.mean, p.scale};
     const int stride = gridDim.x * blockDim.x;
     const uint32_t sw = stream_word(kLearned, (uint32_t)p.parity, MU);
     const int last = p.g.vh - 1;
@@ -194,7 +197,8 @@ template <typename Kernel>
 static cudaError_t launch_persistent(Kernel kernel, const LearnedParams &p, int want, size_t smem, su2_lattice *lat)
 {
     int per_sm = 0, sms = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kLearnThreads, smem);
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kLearnThreads, smem);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, lat->device);
     if (e != cudaSuccess) return e;
     const int grid = std::max(1, std::min(want, std::max(1, per_sm) * sms));
@@ -220,7 +224,7 @@ static su2_status launch_learned_phase(su2_lattice *lat, int mu, int parity)
     p.gate = lat->learned_ctl;
     p.acc_slots = lat->accept_slots;
     p.sweep_slots = lat->accept_slots + 8 * kAcceptSlots;
-    const size_t smem = sizeof(float) * (size_t)p.G * learned::kParams;
+    const size_t smem = sizeof(float2) * (size_t)(p.G - 1) * learned::kParams;
     const int want = (p.g.vh + kLearnThreads - 1) / kLearnThreads;
     cudaError_t e;
     switch (mu) {

@@ -96,22 +96,30 @@ struct ArrayParams {
     __device__ __forceinline__ float operator()(int i) const { return v[i]; }
 };
 
-// Linear interpolation between two table rows, element by element on demand
-// (p_i = r0_i + f (r1_i - r0_i) as one fused multiply-add), so no per-thread
-// copy of the 27 parameters is needed.
-struct InterpParams {
-    const float *r0, *r1;
+// Linear interpolation between two table rows, element by element on demand:
+// the rows are stored as pairs (r0_i, r1_i - r0_i), so p_i = r0_i + f (r1_i -
+// r0_i) is one 8-byte load and one fused multiply-add, and no per-thread copy
+// of the 27 parameters is needed.
+struct PairParams {
+    const float2 *row;
     float f;
-    __device__ __forceinline__ float operator()(int i) const { return __fmaf_rn(f, __fsub_rn(r1[i], r0[i]), r0[i]); }
+    __device__ __forceinline__ float operator()(int i) const
+    {
+        const float2 q = row[i];
+        return __fmaf_rn(f, q.y, q.x);
+    }
 };
 
+// Largest k in 0..kBins-1 with knot p(base + k) <= v (knot 0 is the lower end,
+// -1): the knots are non-decreasing, so three halvings find it.
 template <class P>
 __device__ __forceinline__ int bin_of(const P &p, int base, float v)
 {
+    static_assert(kBins == 8, "three halvings cover eight bins");
     int k = 0;
-#pragma unroll
-    for (int j = 1; j < kBins; ++j)
-        if (p(base + j) <= v) k = j;
+    if (p(base + 4) <= v) k = 4;
+    if (p(base + k + 2) <= v) k += 2;
+    if (p(base + k + 1) <= v) k += 1;
     return k;
 }
 
@@ -174,26 +182,30 @@ __device__ __forceinline__ float spline_inverse(const P &p, float a, float &fpri
     return __fmaf_rn(xi, w, xk);
 }
 
-// The two table rows around network input s (clamped to the table's range)
-// and the interpolation weight.
-__device__ __forceinline__ InterpParams table_params(const float *table, int G, float s_lo, float s_hi, float s)
+// Row pair around network input s (clamped to the table's range) and the
+// interpolation weight; pairs[j] holds rows j and j+1 as (r_j, r_{j+1} - r_j).
+__device__ __forceinline__ PairParams pair_params(const float2 *pairs, int G, float s_lo, float inv_ds, float s)
 {
-    const float inv_ds = __fdiv_rn((float)(G - 1), __fsub_rn(s_hi, s_lo));
     float u = __fmul_rn(__fsub_rn(s, s_lo), inv_ds);
     u = u < 0.0f ? 0.0f : (u > (float)(G - 1) ? (float)(G - 1) : u);
     int j = (int)floorf(u);
     if (j > G - 2) j = G - 2;
-    InterpParams ip;
-    ip.r0 = table + j * kParams;
-    ip.r1 = ip.r0 + kParams;
-    ip.f = __fsub_rn(u, (float)j);
-    return ip;
+    PairParams pp;
+    pp.row = pairs + j * kParams;
+    pp.f = __fsub_rn(u, (float)j);
+    return pp;
+}
+
+// inv_ds = (G - 1) / (s_hi - s_lo), the grid points per unit of s.
+__device__ __forceinline__ float table_inv_ds(int G, float s_lo, float s_hi)
+{
+    return __fdiv_rn((float)(G - 1), __fsub_rn(s_hi, s_lo));
 }
 
 struct Proposal {
-    const float *table;  // G x 27 (shared or global memory)
+    const float2 *pairs;  // (G - 1) x 27 row pairs (shared memory)
     int G;
-    float s_lo, s_hi, mean, scale;
+    float s_lo, inv_ds, mean, scale;
 };
 
 // Independence-Metropolis update of one link (staple v, current link old):
@@ -206,7 +218,7 @@ struct Proposal {
 // learned_propose draws a0' and f'(z'); learned_accept decides.
 struct LearnedDraw {
     DrawSetup d;
-    InterpParams ip;
+    PairParams ip;
     float a_new, fp_new;
 };
 
@@ -214,7 +226,7 @@ __device__ __forceinline__ LearnedDraw learned_propose(const Proposal &pr, float
 {
     LearnedDraw r;
     r.d = prepare_draw(v, beta);
-    r.ip = table_params(pr.table, pr.G, pr.s_lo, pr.s_hi, __fmul_rn(__fsub_rn(r.d.bk, pr.mean), pr.scale));
+    r.ip = pair_params(pr.pairs, pr.G, pr.s_lo, pr.inv_ds, __fmul_rn(__fsub_rn(r.d.bk, pr.mean), pr.scale));
     r.a_new = spline_forward(r.ip, __fsub_rn(__fmul_rn(2.0f, u0), 1.0f), r.fp_new);
     return r;
 }

@@ -44,15 +44,22 @@ def collect(lat: int, ns: int, nt: int, n_pairs: int, sweeps_between: int = 1, s
     return buf[:n_pairs] if buf.shape[0] > n_pairs else buf
 
 
-def train(pairs, steps: int = 2000, batch: int = 4096, lr: float = 1e-3, seed: int = 0):
+def train(pairs, steps: int = 2000, batch: int = 4096, lr: float = 1e-3, seed: int = 0, tail_steps: int = 0,
+          tail_lr: float | None = None):
     """Trains a proposal on device pairs; returns (weights, losses, s_lo, s_hi)
-    where [s_lo, s_hi] is the range of normalised inputs seen in the data."""
+    where [s_lo, s_hi] is the range of normalised inputs seen in the data.
+    `steps` Adam steps at `lr`, then `tail_steps` more at `tail_lr` (the
+    optimizer state carries over)."""
     w0 = initial_weights(seed)
     tr = su2.su2_trainer_create(w0, seed)
     try:
         n = pairs.shape[0]
         su2.su2_trainer_set_input_scaling(tr, pairs.data_ptr(), n)
         losses = su2.su2_trainer_fit(tr, pairs.data_ptr(), n, steps, batch, lr)
+        if tail_steps > 0:
+            tail = su2.su2_trainer_fit(tr, pairs.data_ptr(), n, tail_steps, batch,
+                                       tail_lr if tail_lr is not None else lr / 10)
+            losses = np.concatenate([losses, tail])
         w = su2.su2_trainer_get_weights(tr)
     finally:
         su2.su2_trainer_destroy(tr)
