@@ -114,29 +114,28 @@ __global__ void hot_start_kernel(float4 *__restrict__ links, Geom g, const Round
     }
 }
 
-// even/odd structure of arrays  <->  [lex site][mu][4]
+// even/odd structure of arrays  <->  [lex site][mu][4].  Thread q takes
+// float4 q of the lexicographic array (site q / 4, direction q % 4), so the
+// lexicographic side -- a staging buffer or, for mapped pinned host memory,
+// the caller's buffer itself read over the host link -- is accessed
+// contiguously.
 template <bool kToLex>
 __global__ void convert_kernel(float4 *__restrict__ eo_links, float4 *__restrict__ lex_links, Geom g)
 {
-    const int64_t vol = 2 * (int64_t)g.vh;
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < vol; s += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t lex = s;
-        int rest = (int)(lex / g.ns);
-        const int x = (int)(lex - (int64_t)rest * g.ns);
-        int y = rest % g.ns;
-        rest /= g.ns;
-        const int z = rest % g.ns;
-        const int t = rest / g.ns;
-        const int parity = (x + y + z + t) & 1;
-        const int eo = (int)(lex >> 1);
-#pragma unroll
-        for (int mu = 0; mu < 4; ++mu) {
-            const size_t e = link_index(g, mu, parity, eo);
-            if (kToLex)
-                lex_links[lex * 4 + mu] = eo_links[e];
-            else
-                eo_links[e] = lex_links[lex * 4 + mu];
-        }
+    const int64_t n = 8 * (int64_t)g.vh;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t site = (uint32_t)(q >> 2);
+        const int mu = (int)(q & 3);
+        const uint32_t r1 = fastdiv(site, g.div_ns);
+        const uint32_t r2 = fastdiv(r1, g.div_ns);
+        const uint32_t t = fastdiv(r2, g.div_ns);
+        const uint32_t ns = (uint32_t)g.ns;
+        const uint32_t coord_sum = (site - r1 * ns) + (r1 - r2 * ns) + (r2 - t * ns) + t;
+        const uint32_t e = link_index(g, mu, (int)(coord_sum & 1u), (int)(site >> 1));
+        if (kToLex)
+            lex_links[q] = eo_links[e];
+        else
+            eo_links[e] = lex_links[q];
     }
 }
 
@@ -405,17 +404,34 @@ static su2_status ensure_staging(su2_lattice *lat)
     return SU2_OK;
 }
 
+// Device address of a host buffer that is page-locked and mapped (e.g.
+// cudaHostAlloc), else NULL.
+static float4 *mapped_host(const void *host)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost && a.devicePointer ? (float4 *)a.devicePointer : nullptr;
+}
+
 su2_status su2_get_links(su2_lattice *lat, float *host)
 {
     if (!lat || !host) return SU2_E_INVAL;
     DeviceGuard guard(lat->device);
-    su2_status st = ensure_staging(lat);
-    if (st != SU2_OK) return st;
-    convert_kernel<true><<<grid_for(lat->vol, 256), 256, 0, lat->stream>>>(lat->links, (float4 *)lat->staging,
-                                                                           geom_of(lat));
-    SU2_CUDA(cudaGetLastError());
-    SU2_CUDA(cudaMemcpyAsync(host, lat->staging, sizeof(float4) * 4 * (size_t)lat->vol, cudaMemcpyDeviceToHost,
-                             lat->stream));
+    const int grid = grid_for(4 * lat->vol, 256, 152 * 16);
+    if (float4 *direct = mapped_host(host)) {
+        convert_kernel<true><<<grid, 256, 0, lat->stream>>>(lat->links, direct, geom_of(lat));
+        SU2_CUDA(cudaGetLastError());
+    } else {
+        su2_status st = ensure_staging(lat);
+        if (st != SU2_OK) return st;
+        convert_kernel<true><<<grid, 256, 0, lat->stream>>>(lat->links, (float4 *)lat->staging, geom_of(lat));
+        SU2_CUDA(cudaGetLastError());
+        SU2_CUDA(cudaMemcpyAsync(host, lat->staging, sizeof(float4) * 4 * (size_t)lat->vol, cudaMemcpyDeviceToHost,
+                                 lat->stream));
+    }
     SU2_CUDA(cudaStreamSynchronize(lat->stream));
     return SU2_OK;
 }
@@ -424,13 +440,18 @@ su2_status su2_set_links(su2_lattice *lat, const float *host)
 {
     if (!lat || !host) return SU2_E_INVAL;
     DeviceGuard guard(lat->device);
-    su2_status st = ensure_staging(lat);
-    if (st != SU2_OK) return st;
-    SU2_CUDA(cudaMemcpyAsync(lat->staging, host, sizeof(float4) * 4 * (size_t)lat->vol, cudaMemcpyHostToDevice,
-                             lat->stream));
-    convert_kernel<false><<<grid_for(lat->vol, 256), 256, 0, lat->stream>>>(lat->links, (float4 *)lat->staging,
-                                                                            geom_of(lat));
-    SU2_CUDA(cudaGetLastError());
+    const int grid = grid_for(4 * lat->vol, 256, 152 * 16);
+    if (float4 *direct = mapped_host(host)) {
+        convert_kernel<false><<<grid, 256, 0, lat->stream>>>(lat->links, direct, geom_of(lat));
+        SU2_CUDA(cudaGetLastError());
+    } else {
+        su2_status st = ensure_staging(lat);
+        if (st != SU2_OK) return st;
+        SU2_CUDA(cudaMemcpyAsync(lat->staging, host, sizeof(float4) * 4 * (size_t)lat->vol, cudaMemcpyHostToDevice,
+                                 lat->stream));
+        convert_kernel<false><<<grid, 256, 0, lat->stream>>>(lat->links, (float4 *)lat->staging, geom_of(lat));
+        SU2_CUDA(cudaGetLastError());
+    }
     SU2_CUDA(cudaStreamSynchronize(lat->stream));
     return SU2_OK;
 }

@@ -100,6 +100,24 @@ def test_set_get_links_roundtrip(lattice):
     assert np.array_equal(lat.links(), links)
 
 
+@pytest.mark.parametrize("ns,nt", [(6, 4), (2, 2), (16, 8)])
+def test_links_through_pinned_host_memory(lattice, ns, nt):
+    """Page-locked host buffers are read and written by the layout kernel
+    directly; the result equals the staged path for pageable buffers."""
+    import torch
+
+    lat = lattice(ns, nt, 2.0, 4)
+    su2.su2_heatbath_sweep(lat.h, 1)
+    pageable = lat.links()
+    pinned = torch.empty((ns ** 3 * nt, 4, 4), dtype=torch.float32, pin_memory=True).numpy()
+    su2.su2_get_links(lat.h, ns, nt, out=pinned)
+    assert np.array_equal(pinned, pageable)
+    rng = np.random.default_rng(5)
+    pinned[...] = rng.normal(size=pinned.shape).astype(np.float32)
+    su2.su2_set_links(lat.h, pinned)
+    assert np.array_equal(lat.links(), pinned)
+
+
 # -------------------------------------------------------------- sweep parity
 def run_parity(lattice, ns, nt, beta, seed, start, sweeps):
     lat = lattice(ns, nt, beta, seed, start)
