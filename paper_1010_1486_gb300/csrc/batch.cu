@@ -16,12 +16,18 @@
 #include <string>
 #include <vector>
 
+#include "creutz_queue.cuh"
 #include "observables.cuh"
 #include "staple.cuh"
 #include "su2_device.cuh"
 #include "su2_internal.h"
 
 namespace su2 {
+
+#ifndef SU2_BATCH_MIN_BLOCKS
+#define SU2_BATCH_MIN_BLOCKS 6
+#endif
+constexpr int kBatchMinBlocks = SU2_BATCH_MIN_BLOCKS;  // blocks per SM the register budget is set for
 
 struct LatDesc {
     Geom g;
@@ -117,14 +123,17 @@ __device__ __forceinline__ int find_owner(const int *__restrict__ prefix, int n,
 }
 
 // One phase (MU, parity) over every lattice: chunks of 32 R consecutive
-// even/odd sites of one lattice; per chunk the warp computes the staples
-// (A), runs the Creutz trials with a lane work queue (B), and draws the
-// directions and stores (C), as in the single-lattice kernel.
+// even/odd sites of one lattice, one warp per chunk, as in the single-lattice
+// kernel: the staple of the next round of 32 sites is loaded one nu-group per
+// stage while the current round is drawn; the first Philox block (trials 0,
+// 1) inline, links with both rejected retried 32 at a time from the warp's
+// retry queue, accepted links given their direction and store 32 at a time;
+// both queues are emptied at the end of the chunk.
 template <int MU, int R>
-__device__ void batch_phase(const BatchParams &bp, int parity, uint32_t sweep, float4 *ut_q, float *bk_q,
-                            float *e_q, unsigned int &my_trials)
+__device__ void batch_phase(const BatchParams &bp, int parity, uint32_t sweep, CrQueues &Q, LatDesc &sd,
+                            unsigned int &my_trials)
 {
-    constexpr int Q = 32 * R;
+    constexpr int C = 32 * R;
     const int lane = threadIdx.x & 31;
     const unsigned int lanes_below = (1u << lane) - 1u;
     const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -133,89 +142,156 @@ __device__ void batch_phase(const BatchParams &bp, int parity, uint32_t sweep, f
     const uint32_t sw_dir = stream_word(kDirection, (uint32_t)parity, MU);
     for (int chunk = warp_global; chunk < bp.total_chunks; chunk += nwarps) {
         const int l = find_owner(bp.chunk_prefix, bp.n, chunk);
-        const LatDesc *d = bp.desc + l;
-        const Geom g = d->g;
-        float4 *const links = d->links;
-        const uint32_t k0 = d->k0, k1 = d->k1;
-        const float beta = d->beta;
-        const int base = (chunk - __ldg(bp.chunk_prefix + l)) * Q;
-        const int n_items = min(Q, g.vh - base);
-
-#pragma unroll 1
-        for (int r = 0; r < R; ++r) {
-            const int j = r * 32 + lane;
-            if (j < n_items) {
-                const Coord x = eo_to_coord(g, base + j, parity);
-                const DrawSetup s = prepare_draw(staple_at<MU>(links, g, x, parity), beta);
-                ut_q[j] = s.ut;
-                bk_q[j] = s.bk;
-                e_q[j] = s.e;
-            }
+        // the lattice's descriptor, staged in the warp's shared slot and read
+        // from there (holding it in registers would crowd out the pipeline)
+        __syncwarp();
+        {
+            constexpr int kWords = (int)(sizeof(LatDesc) / sizeof(unsigned int));
+            const unsigned int *src = (const unsigned int *)(bp.desc + l);
+            unsigned int *dst = (unsigned int *)&sd;
+            for (int i = lane; i < kWords; i += 32) dst[i] = __ldg(src + i);
         }
         __syncwarp();
+        const Geom &g = sd.g;
+        float4 *const links = sd.links;
+        const uint32_t k0 = sd.k0, k1 = sd.k1;
+        const float beta = sd.beta;
+        const int base0 = (chunk - __ldg(bp.chunk_prefix + l)) * C;
+        const int last = min(base0 + C, g.vh) - 1;
+        const int rounds = (last - base0 + 32) >> 5;
+        int retry_n = 0, done_n = 0;
 
-        int item = lane < n_items ? lane : -1;
-        int next = 32;
-        uint32_t blk = 0;
-        float bk = 0.0f, e = 0.0f, ome = 1.0f;
-        bool haar = false;
-        if (item >= 0) {
-            bk = bk_q[item];
-            e = e_q[item];
-            ome = __fsub_rn(1.0f, e);
-            haar = bk < kHaarBelow;
-        }
-        while (__any_sync(0xffffffffu, item >= 0)) {
-            bool done = false;
-            if (item >= 0) {
-                const uint4 w = philox_key(make_uint4((uint32_t)(base + item), sweep, sw_creutz, blk), k0, k1);
-                float cand;
-                uint32_t t = 0;
-                if (creutz_trial(uniform01(w.x), uniform01(w.y), bk, e, ome, haar, cand))
-                    t = 2 * blk + 1;
-                else if (creutz_trial(uniform01(w.z), uniform01(w.w), bk, e, ome, haar, cand))
-                    t = 2 * blk + 2;
-                if (t) {
-                    bk_q[item] = cand;
-                    my_trials += t;
-                    done = true;
-                } else if (++blk == (uint32_t)(kMaxTrials / 2)) {
-                    bk_q[item] = __int_as_float(0x7fc00000);
-                    my_trials += kMaxTrials;
-                    done = true;
-                }
+        auto push_done = [&](bool ok, float4 ut, float a0, int eo) {
+            const unsigned int m = __ballot_sync(0xffffffffu, ok);
+            if (ok) {
+                const int q = done_n + __popc(m & lanes_below);
+                Q.d_ut[q] = ut;
+                Q.d_a0[q] = a0;
+                Q.d_eo[q] = eo;
             }
-            const unsigned int mask = __ballot_sync(0xffffffffu, done);
-            if (done) {
-                const int idx = next + __popc(mask & lanes_below);
-                item = idx < n_items ? idx : -1;
-                blk = 0;
-                if (item >= 0) {
-                    bk = bk_q[item];
-                    e = e_q[item];
-                    ome = __fsub_rn(1.0f, e);
-                    haar = bk < kHaarBelow;
-                }
+            done_n += __popc(m);
+        };
+        auto push_retry = [&](bool again, float4 ut, float bk, float e, int eo, int blk) {
+            const unsigned int m = __ballot_sync(0xffffffffu, again);
+            if (again) {
+                const int q = retry_n + __popc(m & lanes_below);
+                Q.r_ut[q] = ut;
+                Q.r_bk[q] = bk;
+                Q.r_e[q] = e;
+                Q.r_eo[q] = eo;
+                Q.r_blk[q] = blk;
             }
-            next += __popc(mask);
-        }
-        __syncwarp();
-
-#pragma unroll 1
-        for (int r = 0; r < R; ++r) {
-            const int j = r * 32 + lane;
-            if (j < n_items) {
-                const int eo = base + j;
-                const float a0 = bk_q[j];
-                if (a0 == a0) {
-                    const uint4 dw = philox_key(make_uint4((uint32_t)eo, sweep, sw_dir, 0u), k0, k1);
-                    links[link_index(g, MU, parity, eo)] = direction_update(a0, ut_q[j], dw);
+            retry_n += __popc(m);
+        };
+        auto direction_pass = [&](int first, int n) {
+            __syncwarp();
+            if (lane < n) {
+                const int q = first + lane;
+                const int eo = Q.d_eo[q];
+                const uint4 wd = philox_key(make_uint4((uint32_t)eo, sweep, sw_dir, 0u), k0, k1);
+                links[link_index(g, MU, parity, eo)] = direction_update(Q.d_a0[q], Q.d_ut[q], wd);
+            }
+            __syncwarp();
+        };
+        auto flush_done = [&]() {
+            while (done_n >= 32) {
+                done_n -= 32;
+                direction_pass(done_n, 32);
+            }
+        };
+        auto retry_pass = [&](int first, int n) {
+            __syncwarp();
+            const bool have = lane < n;
+            float4 ut = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+            float bk = 0.0f, e = 0.0f;
+            int eo = 0, blk = 0;
+            if (have) {
+                const int q = first + lane;
+                ut = Q.r_ut[q];
+                bk = Q.r_bk[q];
+                e = Q.r_e[q];
+                eo = Q.r_eo[q];
+                blk = Q.r_blk[q];
+            }
+            __syncwarp();
+            bool ok = false, again = false;
+            float a0 = 0.0f;
+            if (have) {
+                const uint4 w = philox_key(make_uint4((uint32_t)eo, sweep, sw_creutz, (uint32_t)blk), k0, k1);
+                const bool haar = bk < kHaarBelow;
+                const float ome = __fsub_rn(1.0f, e);
+                float c1, c2;
+                const bool ok1 = creutz_trial(uniform01(w.x), uniform01(w.y), bk, e, ome, haar, c1);
+                const bool ok2 = creutz_trial(uniform01(w.z), uniform01(w.w), bk, e, ome, haar, c2);
+                ok = ok1 || ok2;
+                a0 = ok1 ? c1 : c2;
+                if (ok) {
+                    my_trials += (unsigned int)(2 * blk + (ok1 ? 1 : 2));
+                } else if (blk + 1 < kMaxTrials / 2) {
+                    again = true;
                 } else {
-                    atomicAdd(&bp.flags[0], 1u);
+                    atomicAdd(&bp.flags[0], 1u);  // trial cap: the link keeps its old value
+                    my_trials += (unsigned int)kMaxTrials;
                 }
             }
+            push_retry(again, ut, bk, e, eo, blk + 1);
+            push_done(ok, ut, a0, eo);
+            flush_done();
+        };
+
+        int cur = base0 + lane;
+        float4 v_cur = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        {
+            const int e = min(cur, last);
+            const Coord x = eo_to_coord(g, e, parity);
+            const int e_p = eo_fwd<MU>(g, x, e);
+            v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 0>::value>(links, g, x, e, e_p, parity));
+            v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 1>::value>(links, g, x, e, e_p, parity));
+            v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 2>::value>(links, g, x, e, e_p, parity));
         }
-        __syncwarp();
+#pragma unroll 1
+        for (int r = 0; r < rounds; ++r) {
+            const bool valid = cur <= last;
+            const int nxt = cur + 32;
+            const int en = min(nxt, last);  // the last round reloads its own links: harmless
+            const Coord xn = eo_to_coord(g, en, parity);
+            const int en_p = eo_fwd<MU>(g, xn, en);
+            // ---- part 0
+            NuLinks nl = load_nu_eo<MU, OtherDir<MU, 0>::value>(links, g, xn, en, en_p, parity);
+            const DrawSetup ds = prepare_draw(v_cur, beta);
+            const uint4 w = philox_key(make_uint4((uint32_t)cur, sweep, sw_creutz, 0u), k0, k1);
+            float4 v_next = add_nu_terms(make_float4(0.0f, 0.0f, 0.0f, 0.0f), nl);
+            // ---- part 1
+            nl = load_nu_eo<MU, OtherDir<MU, 1>::value>(links, g, xn, en, en_p, parity);
+            {
+                const bool haar = ds.bk < kHaarBelow;
+                const float ome = __fsub_rn(1.0f, ds.e);
+                float c1, c2;
+                const bool ok1 = creutz_trial(uniform01(w.x), uniform01(w.y), ds.bk, ds.e, ome, haar, c1);
+                const bool ok2 = creutz_trial(uniform01(w.z), uniform01(w.w), ds.bk, ds.e, ome, haar, c2);
+                const bool ok = valid && (ok1 || ok2);
+                my_trials += ok ? (ok1 ? 1u : 2u) : 0u;
+                push_done(ok, ds.ut, ok1 ? c1 : c2, cur);
+                push_retry(valid && !ok1 && !ok2, ds.ut, ds.bk, ds.e, cur, 1);
+            }
+            v_next = add_nu_terms(v_next, nl);
+            // ---- part 2
+            nl = load_nu_eo<MU, OtherDir<MU, 2>::value>(links, g, xn, en, en_p, parity);
+            flush_done();
+            v_next = add_nu_terms(v_next, nl);
+            while (retry_n >= 32) {
+                retry_n -= 32;
+                retry_pass(retry_n, 32);
+            }
+            cur = nxt;
+            v_cur = v_next;
+        }
+        while (retry_n > 0) {
+            const int n = min(retry_n, 32);
+            retry_n -= n;
+            retry_pass(retry_n, n);
+        }
+        if (done_n > 0) direction_pass(0, done_n);
     }
 }
 
@@ -279,12 +355,10 @@ __device__ void batch_measure_final(const BatchParams &bp, unsigned int slot)
 }
 
 template <int R>
-__global__ void __launch_bounds__(kHbThreads) batch_sweep_kernel(const BatchParams bp)
+__global__ void __launch_bounds__(kHbThreads, kBatchMinBlocks) batch_sweep_kernel(const BatchParams bp)
 {
-    constexpr int Q = 32 * R;
-    __shared__ float4 s_ut[kHbThreads / 32][Q];
-    __shared__ float s_bk[kHbThreads / 32][Q];
-    __shared__ float s_e[kHbThreads / 32][Q];
+    __shared__ CrQueues s_q[kHbThreads / 32];
+    __shared__ LatDesc s_desc[kHbThreads / 32];
     const int wib = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -296,10 +370,10 @@ __global__ void __launch_bounds__(kHbThreads) batch_sweep_kernel(const BatchPara
             const int parity = ph & 1;
             unsigned int my_trials = 0;
             switch (ph >> 1) {
-            case 0: batch_phase<0, R>(bp, parity, sweep, s_ut[wib], s_bk[wib], s_e[wib], my_trials); break;
-            case 1: batch_phase<1, R>(bp, parity, sweep, s_ut[wib], s_bk[wib], s_e[wib], my_trials); break;
-            case 2: batch_phase<2, R>(bp, parity, sweep, s_ut[wib], s_bk[wib], s_e[wib], my_trials); break;
-            default: batch_phase<3, R>(bp, parity, sweep, s_ut[wib], s_bk[wib], s_e[wib], my_trials); break;
+            case 0: batch_phase<0, R>(bp, parity, sweep, s_q[wib], s_desc[wib], my_trials); break;
+            case 1: batch_phase<1, R>(bp, parity, sweep, s_q[wib], s_desc[wib], my_trials); break;
+            case 2: batch_phase<2, R>(bp, parity, sweep, s_q[wib], s_desc[wib], my_trials); break;
+            default: batch_phase<3, R>(bp, parity, sweep, s_q[wib], s_desc[wib], my_trials); break;
             }
             const unsigned int wsum = __reduce_add_sync(0xffffffffu, my_trials);
             if (lane == 0 && wsum)

@@ -1,0 +1,24 @@
+// creutz_queue.cuh -- per-warp shared-memory queues of the Creutz phase
+// kernels (single lattice and batches): links whose first two trials were
+// rejected wait for further Philox blocks; links with an accepted a0 wait for
+// their direction and store, 32 at a time.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace su2 {
+
+constexpr int kCrQueue = 64;  // per warp and queue: at most 31 left over + 32 pushed at once
+
+struct CrQueues {
+    // links still without an accepted a0: U~^dag, beta k, exp(-2 beta k), index, next Philox block
+    float4 r_ut[kCrQueue];
+    float r_bk[kCrQueue], r_e[kCrQueue];
+    int r_eo[kCrQueue], r_blk[kCrQueue];
+    // links with an accepted a0 waiting for their direction and store
+    float4 d_ut[kCrQueue];
+    float d_a0[kCrQueue];
+    int d_eo[kCrQueue];
+};
+
+}  // namespace su2

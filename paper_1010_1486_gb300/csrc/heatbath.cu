@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 
+#include "creutz_queue.cuh"
 #include "staple.cuh"
 #include "su2_device.cuh"
 #include "su2_internal.h"
@@ -34,23 +35,10 @@ struct HbParams {
 
 constexpr int kCrThreads = 256;
 constexpr int kCrWarps = kCrThreads / 32;
-constexpr int kCrQueue = 64;  // per warp and queue: at most 31 left over + 32 pushed at once
 #ifndef SU2_HB_MIN_BLOCKS
 #define SU2_HB_MIN_BLOCKS 3
 #endif
 constexpr int kCrMinBlocks = SU2_HB_MIN_BLOCKS;  // blocks per SM the register budget is set for
-
-// Per-warp shared-memory queues of the phase kernel.
-struct CrQueues {
-    // links still without an accepted a0: U~^dag, beta k, exp(-2 beta k), index, next Philox block
-    float4 r_ut[kCrQueue];
-    float r_bk[kCrQueue], r_e[kCrQueue];
-    int r_eo[kCrQueue], r_blk[kCrQueue];
-    // links with an accepted a0 waiting for their direction and store
-    float4 d_ut[kCrQueue];
-    float d_a0[kCrQueue];
-    int d_eo[kCrQueue];
-};
 
 // One heat-bath phase (mu = MU, sites of parity p.parity), Creutz's sampler.
 //
