@@ -212,7 +212,11 @@ __device__ __forceinline__ float qnorm2(float4 a) { return chain4(a.x, a.x, a.y,
 // ------------------------------------------------------------ heat bath
 constexpr int kMaxTrials = 4096;
 constexpr float kHaarBelow = 1e-6f;  // beta k below this: a0 from the Haar marginal
-constexpr float kExpCutoff = 43.0f;  // beta k above this: exp(-2 beta k) taken as 0
+// beta k above this: exp(-2 beta k) taken as 0.  It changes no draw: for
+// beta k > 17, e = exp(-2 beta k) < 2^-48, so 1 - e rounds to 1 and
+// x = r1 (1 - e) + e rounds to r1 for every uniform r1 >= 2^-24 (half an ulp
+// of r1 is at least 2^-48); the exponential is simply not computed there.
+constexpr float kExpCutoff = 17.0f;
 
 // Normalised staple (Sec. 2): k = |v| = sqrt(det V), U~^dag = v^dag / k
 // (identity if k = 0), bk = beta k, e = exp(-2 beta k) (0 when beta k > 43 or

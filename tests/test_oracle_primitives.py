@@ -160,3 +160,16 @@ def test_quaternion_dagger_inverts_unit_elements():
         assert np.allclose(oracle.quat_mul(a, d), [1, 0, 0, 0], atol=3e-7)
         m = to_matrix(a)
         assert np.allclose(m @ m.conj().T, np.eye(2), atol=1e-6)
+
+
+def test_creutz_variable_ignores_exp_below_cutoff():
+    """The device skips exp(-2 beta k) for beta k > 17: there e < 2^-48, so
+    1 - e rounds to 1 and r1 (1 - e) + e rounds to r1 in binary32 for every
+    uniform r1 = j 2^-24 (the draws are those of the oracle, which keeps e)."""
+    e = float(oracle.expf(np.array([-34.0], np.float32))[0])
+    assert 0.0 < e < 2.0 ** -48
+    assert np.float32(np.float32(1.0) - np.float32(e)) == np.float32(1.0)
+    j = np.concatenate([np.arange(1, 4097), np.arange(2 ** 24 - 4096, 2 ** 24 + 1),
+                        np.random.default_rng(0).integers(1, 2 ** 24, 200_000)])
+    r1 = (j.astype(np.float64) * 2.0 ** -24)
+    assert np.array_equal((r1 + e).astype(np.float32), r1.astype(np.float32))
