@@ -59,7 +59,7 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=20)
-    ap.add_argument("--tau-sweeps", type=int, default=2000,
+    ap.add_argument("--tau-sweeps", type=int, default=4000,
                     help="sweeps per form for tau_int and the plaquette comparison (0 = skip)")
     ap.add_argument("--therm", type=int, default=1500, help="thermalisation sweeps before the form comparison")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sample length")
@@ -385,8 +385,9 @@ def compare_forms(args, dist, lat, su2, torch, stream, tau_int):
             su2.su2_set_overrelax(lat, 0)
             su2.su2_set_sampler(lat, su2.SU2_SAMPLER_CREUTZ)
         plain_blocks.append(su2.su2_generate(lat, per, 1, 0)[0].copy())
-        tau_o = np.mean([tau_int(b)[0] for b in or_blocks])
+        tau_o, dtau_o = tau_int(or_blocks)[:2]
         out["kp_overrelax"]["tau_int"] = float(tau_o)
+        out["kp_overrelax"]["tau_int_err"] = float(dtau_o)
         out["kp_overrelax"]["tau_int_unit"] = "compound sweeps"
         out["kp_overrelax"]["value_tau_adjusted"] = compound_per_s * 4 * VOL / (2 * tau_o)
         d_o = np.array([or_blocks[k].mean() - 0.5 * (plain_blocks[k].mean() + plain_blocks[k + 1].mean())
@@ -394,16 +395,20 @@ def compare_forms(args, dist, lat, su2, torch, stream, tau_int):
         se_o = d_o.std(ddof=1) / np.sqrt(nblk)
         out["kp_overrelax"]["plaquette_minus_plain"] = float(d_o.mean())
         out["kp_overrelax"]["plaquette_sigma"] = float(d_o.mean() / se_o) if se_o > 0 else None
-        tau_p = np.mean([tau_int(b)[0] for b in plain_blocks])
-        tau_l = np.mean([tau_int(b)[0] for b in learned_blocks])
-        tau_k = np.mean([tau_int(b)[0] for b in kp_blocks])
+        # blocks of one form are replicas of its chain: pooled Gamma method
+        tau_p, dtau_p = tau_int(plain_blocks)[:2]
+        tau_l, dtau_l = tau_int(learned_blocks)[:2]
+        tau_k, dtau_k = tau_int(kp_blocks)[:2]
         out["plain_kennedy_pendleton"]["tau_int"] = float(tau_k)
+        out["plain_kennedy_pendleton"]["tau_int_err"] = float(dtau_k)
         out["plain_kennedy_pendleton"]["value_tau_adjusted"] = value_kp / (2 * tau_k)
         d = np.array([learned_blocks[k].mean() - 0.5 * (plain_blocks[k].mean() + plain_blocks[k + 1].mean())
                       for k in range(nblk)])
         se = d.std(ddof=1) / np.sqrt(nblk)
         out["plain"]["tau_int"] = float(tau_p)
+        out["plain"]["tau_int_err"] = float(dtau_p)
         out["learned"]["tau_int"] = float(tau_l)
+        out["learned"]["tau_int_err"] = float(dtau_l)
         out["plain"]["value_tau_adjusted"] = value_plain / (2 * tau_p)
         out["learned"]["value_tau_adjusted"] = value_learned / (2 * tau_l)
         out["plaquette_check"] = {"blocks": nblk, "sweeps_per_block": per,
@@ -416,7 +421,8 @@ def compare_forms(args, dist, lat, su2, torch, stream, tau_int):
                                      "learned": out["learned"]["value_tau_adjusted"],
                                      "kp_overrelax": out["kp_overrelax"]["value_tau_adjusted"],
                                      "convention": "4V x sweeps/s / (2 tau_int(plaquette)), tau_int = 1/2 + "
-                                                   "sum rho in sweeps (compound sweeps for kp_overrelax)"}
+                                                   "sum rho in sweeps (compound sweeps for kp_overrelax), Gamma "
+                                                   "method with the interleaved blocks of a form pooled as replicas"}
     return out
 
 

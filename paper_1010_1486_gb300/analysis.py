@@ -25,14 +25,40 @@ def autocorrelation(series: np.ndarray, tmax: int) -> np.ndarray:
     return acf / (n - np.arange(tmax + 1))
 
 
+def _pooled_autocovariance(replicas, tmax: int) -> np.ndarray:
+    """Gamma(t), t = 0..tmax, of several runs of the same chain (replicas):
+    deviations from the common mean, lag products summed over all runs,
+    divided by the number of pairs (Wolff 2004, Sec. 3.3)."""
+    mean = np.concatenate(replicas).mean()
+    num = np.zeros(tmax + 1)
+    pairs = np.zeros(tmax + 1)
+    for a in replicas:
+        n = a.size
+        d = a - mean
+        nfft = 1 << (2 * n - 1).bit_length()
+        f = np.fft.rfft(d, nfft)
+        acf = np.fft.irfft(f * np.conj(f), nfft)
+        m = min(tmax, n - 1)
+        num[: m + 1] += acf[: m + 1]
+        pairs[: m + 1] += n - np.arange(m + 1)
+    return num / np.maximum(pairs, 1.0)
+
+
 def tau_int(series, s_factor: float = 1.5):
-    """Returns (tau_int, its statistical error, window W, error of the mean)."""
-    a = np.asarray(series, dtype=np.float64)
-    n = a.size
-    if n < 4:
+    """Returns (tau_int, its statistical error, window W, error of the mean).
+    `series` is one run, or a list of runs of the same chain (replicas: their
+    autocovariances are pooled about the common mean before the windowed
+    sum, which avoids the bias of averaging tau_int over short runs)."""
+    if isinstance(series, (list, tuple)):
+        replicas = [np.asarray(r, dtype=np.float64) for r in series]
+    else:
+        replicas = [np.asarray(series, dtype=np.float64)]
+    n = sum(r.size for r in replicas)
+    if min(r.size for r in replicas) < 4:
         raise ValueError("series too short")
-    tmax = min(n // 2, 100000)
-    gamma = autocorrelation(a, tmax)
+    tmax = min(min(r.size for r in replicas) // 2, 100000)
+    gamma = (autocorrelation(replicas[0], tmax) if len(replicas) == 1
+             else _pooled_autocovariance(replicas, tmax))
     if gamma[0] <= 0.0:
         return 0.5, 0.0, 0, 0.0
     rho = gamma / gamma[0]

@@ -124,6 +124,13 @@ def test_tau_int_on_ar1_series():
     tau, dtau, w, err = tau_int(x)
     want = (1 + rho) / (2 * (1 - rho))
     assert abs(tau - want) < max(3 * dtau, 0.05 * want), (tau, dtau, want)
+    # the same chain cut into 16 replicas of 25,000: pooled estimate agrees
+    tau_r, dtau_r, _, _ = tau_int([x[i * 25_000:(i + 1) * 25_000] for i in range(16)])
+    assert abs(tau_r - want) < max(3 * dtau_r, 0.06 * want), (tau_r, want)
+    # short replicas: pooled estimate stays close where averaging per-run estimates is biased low/high
+    reps = [x[i * 250:(i + 1) * 250] for i in range(16)]
+    tau_s, dtau_s, _, _ = tau_int(reps)
+    assert abs(tau_s - want) < 0.35 * want, (tau_s, want)
     # white noise: tau = 1/2
     tau0, _, _, err0 = tau_int(rng.normal(size=100_000))
     assert abs(tau0 - 0.5) < 0.05
