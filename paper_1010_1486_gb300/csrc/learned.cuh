@@ -90,12 +90,7 @@ __device__ __forceinline__ void spline_params(const float (&o)[kOut], float *p)
     for (int i = 0; i <= kBins; ++i) p[2 * (kBins + 1) + i] = __fadd_rn(kMinDer, softplus(o[2 * kBins + i]));
 }
 
-// Parameter accessors: p(i) is spline parameter i (x_0..x_8, y_0..y_8, d_0..d_8).
-struct ArrayParams {
-    const float *v;
-    __device__ __forceinline__ float operator()(int i) const { return v[i]; }
-};
-
+// Parameter accessor: p(i) is spline parameter i (x_0..x_8, y_0..y_8, d_0..d_8).
 // Linear interpolation between two table rows, element by element on demand:
 // the rows are stored as pairs (r0_i, r1_i - r0_i), so p_i = r0_i + f (r1_i -
 // r0_i) is one 8-byte load and one fused multiply-add, and no per-thread copy
@@ -212,10 +207,10 @@ struct Proposal {
 // proposal a0' = f(2 u0 - 1) with density 1/(2 f'), direction from u2, u3;
 // accepted iff u1 <= exp(Delta) (or Delta >= 0) with
 // Delta = beta k (a0' - a_cur) + log(sqrt((1 - a0'^2)/(1 - a_cur^2)) f'(z')/f'(z_cur)),
-// a_cur = old U~.  All four uniforms from one Philox block of the learned stream.
-// Returns 1 (out = new link) or 0 (out = old).
-// The step in two parts, so a caller can place other work between them:
-// learned_propose draws a0' and f'(z'); learned_accept decides.
+// a_cur = old U~.  All four uniforms from one Philox block of the learned
+// stream.  In two parts, so a caller can place other work between them:
+// learned_propose draws a0' and f'(z'); learned_accept decides (a rejected
+// link keeps its value, an accepted one becomes a U~^dag with the direction).
 struct LearnedDraw {
     DrawSetup d;
     PairParams ip;
@@ -244,18 +239,6 @@ __device__ __forceinline__ bool learned_accept(const LearnedDraw &r, float4 old,
     if (!(ratio > 0.0f)) return false;
     const float delta = __fmaf_rn(r.d.bk, __fsub_rn(r.a_new, acur), log_series(ratio));
     return delta >= 0.0f || u1 <= exp_neg(delta);
-}
-
-__device__ __forceinline__ int learned_link(const Proposal &pr, float beta, float4 v, float4 old, uint4 w,
-                                            float4 &out)
-{
-    const LearnedDraw r = learned_propose(pr, beta, v, uniform01(w.x));
-    if (!learned_accept(r, old, uniform01(w.y))) {
-        out = old;
-        return 0;
-    }
-    out = direction_from_uniforms(r.a_new, r.d.ut, uniform01(w.z), uniform01(w.w));
-    return 1;
 }
 
 }  // namespace learned

@@ -33,29 +33,10 @@ __device__ __forceinline__ float4 staple_at(const float4 *__restrict__ L, const 
 
 // Forward and backward staple terms of direction nu (Sec. 2), from the six
 // links they need: U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag and
-// U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu).
+// U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu) (loaded by load_nu_eo below).
 struct NuLinks {
     float4 nu_xp, mu_xn, nu_x, nu_xpm, mu_xm, nu_xm;
 };
-
-template <int MU, int NU>
-__device__ __forceinline__ NuLinks load_nu(const float4 *__restrict__ L, const Geom &g, const Coord &x, int lex_p,
-                                           int parity)
-{
-    constexpr int nu = NU;
-    const int op = parity ^ 1;
-    NuLinks n;
-    const int e_xn = lex_fwd(g, x.lex, x.c[nu], nu) >> 1;
-    const int e_xm = lex_bwd(g, x.lex, x.c[nu], nu) >> 1;
-    const int e_xpm = lex_bwd(g, lex_p, x.c[nu], nu) >> 1;  // x + mu - nu keeps the nu coordinate of x
-    n.nu_xp = __ldg(L + link_index(g, nu, op, lex_p >> 1));
-    n.mu_xn = __ldg(L + link_index(g, MU, op, e_xn));
-    n.nu_x = __ldg(L + link_index(g, nu, parity, x.lex >> 1));
-    n.nu_xpm = __ldg(L + link_index(g, nu, parity, e_xpm));
-    n.mu_xm = __ldg(L + link_index(g, MU, op, e_xm));
-    n.nu_xm = __ldg(L + link_index(g, nu, op, e_xm));
-    return n;
-}
 
 __device__ __forceinline__ float4 add_nu_terms(float4 v, const NuLinks &n)
 {
