@@ -375,6 +375,10 @@ int orc_heatbath_link(float beta, const float v[4], uint64_t seed, uint32_t eo, 
     float e = 0.0f;
     if (!haar && bk <= 43.0f) e = orc_expf(-2.0f * bk);
     float one_minus_e = 1.0f - e;
+    /* a0 = 1 + ln(x)/(beta k) is evaluated as 1 + ln(x) * (1/(beta k)) with
+     * the reciprocal rounded once per link (Sec. 2 fixes the formula, not its
+     * rounding; one division per link instead of one per trial) */
+    float inv_bk = haar ? 0.0f : 1.0f / bk;
 
     float a0 = 0.0f;
     int trials = 0;
@@ -389,7 +393,7 @@ int orc_heatbath_link(float beta, const float v[4], uint64_t seed, uint32_t eo, 
             cand = 2.0f * r1 - 1.0f;
         } else {
             float x = fmaf(r1, one_minus_e, e);
-            cand = 1.0f + orc_logf(x) / bk;
+            cand = 1.0f + orc_logf(x) * inv_bk;
         }
         if (cand < -1.0f) cand = -1.0f;
         if (cand > 1.0f) cand = 1.0f;

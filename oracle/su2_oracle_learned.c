@@ -336,6 +336,7 @@ int64_t orc_collect_pairs(int ns, int nt, double beta, uint64_t seed, uint32_t s
         float e = 0.0f;
         if (!haar && bk <= 43.0f) e = orc_expf(-2.0f * bk);
         const float ome = 1.0f - e;
+        const float inv_bk = haar ? 0.0f : 1.0f / bk; /* as in orc_heatbath_link */
         float a0 = 0.0f, u[4] = {0, 0, 0, 0};
         int got = 0;
         for (int t = 0; t < 4096 && !got; ++t) {
@@ -348,7 +349,7 @@ int64_t orc_collect_pairs(int ns, int nt, double beta, uint64_t seed, uint32_t s
                 for (int i = 0; i < 4; ++i) u[i] = orc_u01(wd[i]);
             }
             const float r1 = u[2 * (t & 1)], r2 = u[2 * (t & 1) + 1];
-            float cand = haar ? 2.0f * r1 - 1.0f : 1.0f + orc_logf(fmaf(r1, ome, e)) / bk;
+            float cand = haar ? 2.0f * r1 - 1.0f : 1.0f + orc_logf(fmaf(r1, ome, e)) * inv_bk;
             cand = cand < -1.0f ? -1.0f : (cand > 1.0f ? 1.0f : cand);
             if (r2 * r2 <= fmaf(-cand, cand, 1.0f)) {
                 a0 = cand;

@@ -11,9 +11,9 @@ namespace su2 {
 constexpr int kCrQueue = 64;  // per warp and queue: at most 31 left over + 32 pushed at once
 
 struct CrQueues {
-    // links still without an accepted a0: U~^dag, beta k, exp(-2 beta k), index, next Philox block
+    // links still without an accepted a0: U~^dag, beta k, 1/(beta k), exp(-2 beta k), index, next Philox block
     float4 r_ut[kCrQueue];
-    float r_bk[kCrQueue], r_e[kCrQueue];
+    float r_bk[kCrQueue], r_ibk[kCrQueue], r_e[kCrQueue];
     int r_eo[kCrQueue], r_blk[kCrQueue];
     // links with an accepted a0 waiting for their direction and store
     float4 d_ut[kCrQueue];

@@ -83,12 +83,13 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
         }
         done_n += __popc(m);
     };
-    auto push_retry = [&](bool again, float4 ut, float bk, float e, int eo, int blk) {
+    auto push_retry = [&](bool again, float4 ut, float bk, float ibk, float e, int eo, int blk) {
         const unsigned int m = __ballot_sync(0xffffffffu, again);
         if (again) {
             const int q = retry_n + __popc(m & lanes_below);
             Q.r_ut[q] = ut;
             Q.r_bk[q] = bk;
+            Q.r_ibk[q] = ibk;
             Q.r_e[q] = e;
             Q.r_eo[q] = eo;
             Q.r_blk[q] = blk;
@@ -117,12 +118,13 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
         __syncwarp();
         const bool have = lane < n;
         float4 ut = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
-        float bk = 0.0f, e = 0.0f;
+        float bk = 0.0f, ibk = 0.0f, e = 0.0f;
         int eo = 0, blk = 0;
         if (have) {
             const int q = first + lane;
             ut = Q.r_ut[q];
             bk = Q.r_bk[q];
+            ibk = Q.r_ibk[q];
             e = Q.r_e[q];
             eo = Q.r_eo[q];
             blk = Q.r_blk[q];
@@ -135,8 +137,8 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
             const bool haar = bk < kHaarBelow;
             const float ome = __fsub_rn(1.0f, e);
             float c1, c2;
-            const bool ok1 = creutz_trial(uniform01(w.x), uniform01(w.y), bk, e, ome, haar, c1);
-            const bool ok2 = creutz_trial(uniform01(w.z), uniform01(w.w), bk, e, ome, haar, c2);
+            const bool ok1 = creutz_trial(uniform01(w.x), uniform01(w.y), ibk, e, ome, haar, c1);
+            const bool ok2 = creutz_trial(uniform01(w.z), uniform01(w.w), ibk, e, ome, haar, c2);
             ok = ok1 || ok2;
             a0 = ok1 ? c1 : c2;
             if (ok) {
@@ -148,7 +150,7 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
                 trials += (unsigned int)kMaxTrials;
             }
         }
-        push_retry(again, ut, bk, e, eo, blk + 1);
+        push_retry(again, ut, bk, ibk, e, eo, blk + 1);
         push_done(ok, ut, a0, eo);
         flush_done();
     };
@@ -181,12 +183,12 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
             const bool haar = d.bk < kHaarBelow;
             const float ome = __fsub_rn(1.0f, d.e);
             float c1, c2;
-            const bool ok1 = creutz_trial(uniform01(w.x), uniform01(w.y), d.bk, d.e, ome, haar, c1);
-            const bool ok2 = creutz_trial(uniform01(w.z), uniform01(w.w), d.bk, d.e, ome, haar, c2);
+            const bool ok1 = creutz_trial(uniform01(w.x), uniform01(w.y), d.ibk, d.e, ome, haar, c1);
+            const bool ok2 = creutz_trial(uniform01(w.z), uniform01(w.w), d.ibk, d.e, ome, haar, c2);
             const bool ok = valid && (ok1 || ok2);
             trials += ok ? (ok1 ? 1u : 2u) : 0u;
             push_done(ok, d.ut, ok1 ? c1 : c2, cur);
-            push_retry(valid && !ok1 && !ok2, d.ut, d.bk, d.e, cur, 1);
+            push_retry(valid && !ok1 && !ok2, d.ut, d.bk, d.ibk, d.e, cur, 1);
         }
         v_next = add_nu_terms(v_next, nl);
         // ---- part 2

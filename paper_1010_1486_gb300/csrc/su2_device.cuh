@@ -225,6 +225,7 @@ struct DrawSetup {
     float4 ut;
     float bk;
     float e;
+    float ibk;  // 1/(beta k), rounded once (0 on the Haar branch)
 };
 
 __device__ __forceinline__ DrawSetup prepare_draw(float4 v, float beta)
@@ -240,20 +241,22 @@ __device__ __forceinline__ DrawSetup prepare_draw(float4 v, float beta)
     d.bk = __fmul_rn(beta, k);
     d.e = 0.0f;
     if (!(d.bk < kHaarBelow) && d.bk <= kExpCutoff) d.e = exp_series(__fmul_rn(-2.0f, d.bk));
+    d.ibk = d.bk < kHaarBelow ? 0.0f : __fdiv_rn(1.0f, d.bk);
     return d;
 }
 
 // One Creutz trial (Phys. Rev. D 21, 2308): candidate a0 = 1 + ln(x)/(beta k),
+// evaluated as 1 + ln(x) ibk with ibk = 1/(beta k) rounded once per link,
 // x = e + r1 (1 - e) uniform in [exp(-2 beta k), 1]; on the Haar branch
 // a0 = 2 r1 - 1.  Clamped to [-1, 1]; accepted iff r2^2 <= 1 - a0^2.
-__device__ __forceinline__ bool creutz_trial(float r1, float r2, float bk, float e, float one_minus_e, bool haar,
+__device__ __forceinline__ bool creutz_trial(float r1, float r2, float ibk, float e, float one_minus_e, bool haar,
                                              float &cand)
 {
     float c;
     if (haar) {
         c = __fsub_rn(__fmul_rn(2.0f, r1), 1.0f);
     } else {
-        c = __fadd_rn(1.0f, __fdiv_rn(log_series(__fmaf_rn(r1, one_minus_e, e)), bk));
+        c = __fadd_rn(1.0f, __fmul_rn(log_series(__fmaf_rn(r1, one_minus_e, e)), ibk));
     }
     c = c < -1.0f ? -1.0f : (c > 1.0f ? 1.0f : c);
     cand = c;
@@ -294,10 +297,10 @@ __device__ __forceinline__ int heatbath_draw(float4 v, float beta, const RoundKe
     for (int b = 0; b < kMaxTrials / 2 && trials == 0; ++b) {
         const uint4 w = philox_rk(make_uint4(eo, sweep, stream_word(kCreutz, parity, mu), (uint32_t)b), rk);
         float cand;
-        if (creutz_trial(uniform01(w.x), uniform01(w.y), s.bk, s.e, ome, haar, cand)) {
+        if (creutz_trial(uniform01(w.x), uniform01(w.y), s.ibk, s.e, ome, haar, cand)) {
             a0 = cand;
             trials = 2 * b + 1;
-        } else if (creutz_trial(uniform01(w.z), uniform01(w.w), s.bk, s.e, ome, haar, cand)) {
+        } else if (creutz_trial(uniform01(w.z), uniform01(w.w), s.ibk, s.e, ome, haar, cand)) {
             a0 = cand;
             trials = 2 * b + 2;
         }
