@@ -19,6 +19,9 @@ struct CrQueues {
     float4 d_ut[kCrQueue];
     float d_a0[kCrQueue];
     int d_eo[kCrQueue];
+    // when the phase measures the plaquette: the link's staple terms of the
+    // directions nu < mu, for the retry and the direction queue
+    float4 r_sp[kCrQueue], d_sp[kCrQueue];
 };
 
 }  // namespace su2

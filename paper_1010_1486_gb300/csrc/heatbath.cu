@@ -11,6 +11,7 @@
 #include <cstring>
 
 #include "creutz_queue.cuh"
+#include "observables.cuh"
 #include "staple.cuh"
 #include "su2_device.cuh"
 #include "su2_internal.h"
@@ -31,6 +32,7 @@ struct HbParams {
     unsigned long long *trial_slots;
     unsigned int *flags;
     const unsigned int *gate;  // if non-NULL and *gate == 1 the phase is left to the learned kernel
+    double *plaq;              // measuring phases: block partials of the plaquettes of planes (nu < mu, mu)
 };
 
 constexpr int kCrThreads = 256;
@@ -58,7 +60,13 @@ constexpr int kCrMinBlocks = SU2_HB_MIN_BLOCKS;  // blocks per SM the register b
 // in words 2(t&1), 2(t&1)+1 of block t>>1; direction block 0), so the phase
 // computes exactly the one-thread-per-link definition.  Lanes past the end
 // work on a clamped index and drop their results.
-template <int MU>
+//
+// MEAS (odd phases of mu = 1, 2, 3 in a sweep that ends with a measurement):
+// with S the staple terms of the directions nu < MU, (1/2) Tr U'S is the sum
+// of the plaquettes of planes (nu, MU) at x and x - nu, so over the odd sites
+// every such plaquette of the final configuration is counted once; the block
+// partial goes to p.plaq[block].
+template <int MU, bool MEAS>
 __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(const HbParams p)
 {
     if (p.gate != nullptr && *(volatile const unsigned int *)p.gate == 1u) return;
@@ -71,19 +79,21 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
     const uint32_t sw_creutz = stream_word(kCreutz, (uint32_t)p.parity, MU);
     const uint32_t sw_dir = stream_word(kDirection, (uint32_t)p.parity, MU);
     unsigned int trials = 0;
+    double plaq = 0.0;
     int retry_n = 0, done_n = 0;  // warp-uniform queue lengths
 
-    auto push_done = [&](bool ok, float4 ut, float a0, int eo) {
+    auto push_done = [&](bool ok, float4 ut, float a0, int eo, float4 sp) {
         const unsigned int m = __ballot_sync(0xffffffffu, ok);
         if (ok) {
             const int q = done_n + __popc(m & lanes_below);
             Q.d_ut[q] = ut;
             Q.d_a0[q] = a0;
             Q.d_eo[q] = eo;
+            if (MEAS) Q.d_sp[q] = sp;
         }
         done_n += __popc(m);
     };
-    auto push_retry = [&](bool again, float4 ut, float bk, float ibk, float e, int eo, int blk) {
+    auto push_retry = [&](bool again, float4 ut, float bk, float ibk, float e, int eo, int blk, float4 sp) {
         const unsigned int m = __ballot_sync(0xffffffffu, again);
         if (again) {
             const int q = retry_n + __popc(m & lanes_below);
@@ -93,6 +103,7 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
             Q.r_e[q] = e;
             Q.r_eo[q] = eo;
             Q.r_blk[q] = blk;
+            if (MEAS) Q.r_sp[q] = sp;
         }
         retry_n += __popc(m);
     };
@@ -103,7 +114,9 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
             const int q = first + lane;
             const int eo = Q.d_eo[q];
             const uint4 wd = philox_rk(make_uint4((uint32_t)eo, p.sweep, sw_dir, 0u), p.rk);
-            p.links[link_index(p.g, MU, p.parity, eo)] = direction_update(Q.d_a0[q], Q.d_ut[q], wd);
+            const float4 out = direction_update(Q.d_a0[q], Q.d_ut[q], wd);
+            p.links[link_index(p.g, MU, p.parity, eo)] = out;
+            if (MEAS) plaq += (double)qmul_re(out, Q.d_sp[q]);
         }
         __syncwarp();
     };
@@ -117,7 +130,7 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
     auto retry_pass = [&](int first, int n) {
         __syncwarp();
         const bool have = lane < n;
-        float4 ut = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+        float4 ut = make_float4(1.0f, 0.0f, 0.0f, 0.0f), sp = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         float bk = 0.0f, ibk = 0.0f, e = 0.0f;
         int eo = 0, blk = 0;
         if (have) {
@@ -128,6 +141,7 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
             e = Q.r_e[q];
             eo = Q.r_eo[q];
             blk = Q.r_blk[q];
+            if (MEAS) sp = Q.r_sp[q];
         }
         __syncwarp();
         bool ok = false, again = false;
@@ -150,21 +164,25 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
                 trials += (unsigned int)kMaxTrials;
             }
         }
-        push_retry(again, ut, bk, ibk, e, eo, blk + 1);
-        push_done(ok, ut, a0, eo);
+        push_retry(again, ut, bk, ibk, e, eo, blk + 1, sp);
+        push_done(ok, ut, a0, eo, sp);
         flush_done();
     };
 
     int base = blockIdx.x * kCrThreads + (threadIdx.x & ~31);
     int cur = base + lane;
     float4 v_cur = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float4 sp_cur = v_cur;  // MEAS: staple terms of nu < MU (the first MU groups)
     if (base < p.g.vh) {
         const int e = min(cur, last);
         const Coord x = eo_to_coord(p.g, e, p.parity);
         const int e_p = eo_fwd<MU>(p.g, x, e);
         v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 0>::value>(p.links, p.g, x, e, e_p, p.parity));
+        if (MU == 1) sp_cur = v_cur;
         v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 1>::value>(p.links, p.g, x, e, e_p, p.parity));
+        if (MU == 2) sp_cur = v_cur;
         v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 2>::value>(p.links, p.g, x, e, e_p, p.parity));
+        if (MU == 3) sp_cur = v_cur;
     }
     while (base < p.g.vh) {  // warp-uniform
         const bool valid = cur <= last;
@@ -177,6 +195,7 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
         const DrawSetup d = prepare_draw(v_cur, p.beta);
         const uint4 w = philox_rk(make_uint4((uint32_t)cur, p.sweep, sw_creutz, 0u), p.rk);
         float4 v_next = add_nu_terms(make_float4(0.0f, 0.0f, 0.0f, 0.0f), nl);
+        float4 sp_next = v_next;
         // ---- part 1
         nl = load_nu_eo<MU, OtherDir<MU, 1>::value>(p.links, p.g, xn, en, en_p, p.parity);
         {
@@ -187,14 +206,16 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
             const bool ok2 = creutz_trial(uniform01(w.z), uniform01(w.w), d.ibk, d.e, ome, haar, c2);
             const bool ok = valid && (ok1 || ok2);
             trials += ok ? (ok1 ? 1u : 2u) : 0u;
-            push_done(ok, d.ut, ok1 ? c1 : c2, cur);
-            push_retry(valid && !ok1 && !ok2, d.ut, d.bk, d.ibk, d.e, cur, 1);
+            push_done(ok, d.ut, ok1 ? c1 : c2, cur, sp_cur);
+            push_retry(valid && !ok1 && !ok2, d.ut, d.bk, d.ibk, d.e, cur, 1, sp_cur);
         }
         v_next = add_nu_terms(v_next, nl);
+        if (MU == 2) sp_next = v_next;
         // ---- part 2
         nl = load_nu_eo<MU, OtherDir<MU, 2>::value>(p.links, p.g, xn, en, en_p, p.parity);
         flush_done();
         v_next = add_nu_terms(v_next, nl);
+        if (MU == 3) sp_next = v_next;
         while (retry_n >= 32) {
             retry_n -= 32;
             retry_pass(retry_n, 32);
@@ -202,6 +223,7 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
         base += stride;
         cur = nxt;
         v_cur = v_next;
+        sp_cur = sp_next;
     }
     while (retry_n > 0) {
         const int n = min(retry_n, 32);
@@ -214,25 +236,29 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
         atomicAdd(&p.trial_slots[(2 * MU + p.parity) * kTrialSlots +
                                  ((blockIdx.x * kCrWarps + (threadIdx.x >> 5)) & (kTrialSlots - 1))],
                   (unsigned long long)wsum);
+    if (MEAS) {
+        const double total = block_sum(plaq);
+        if (threadIdx.x == 0) p.plaq[blockIdx.x] = total;
+    }
 }
 
-template <int MU>
+template <int MU, bool MEAS>
 static cudaError_t launch_hb(const HbParams &p, int device, cudaStream_t stream)
 {
     static int blocks_per_sm[64] = {};
     static int num_sms[64] = {};
     if (device < 0 || device >= 64) device = 0;
     if (!blocks_per_sm[device]) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[device], hb_phase_kernel<MU>,
-                                                                      kCrThreads, 0);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[device],
+                                                                      hb_phase_kernel<MU, MEAS>, kCrThreads, 0);
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&num_sms[device], cudaDevAttrMultiProcessorCount, device);
         if (e != cudaSuccess) return e;
         if (blocks_per_sm[device] < 1) blocks_per_sm[device] = 1;
     }
     const int want = (p.g.vh + kCrThreads - 1) / kCrThreads;
-    const int grid = std::max(1, std::min(want, blocks_per_sm[device] * num_sms[device]));
-    hb_phase_kernel<MU><<<grid, kCrThreads, 0, stream>>>(p);
+    const int grid = std::max(1, std::min(std::min(want, blocks_per_sm[device] * num_sms[device]), kFusedSlots));
+    hb_phase_kernel<MU, MEAS><<<grid, kCrThreads, 0, stream>>>(p);
     return cudaGetLastError();
 }
 
@@ -249,12 +275,21 @@ su2_status launch_hb_phase(su2_lattice *lat, int mu, int parity, uint32_t sweep,
     p.sweep = sweep;
     p.trial_slots = lat->scratch.trials;
     p.flags = lat->scratch.flags;
+    p.plaq = fused_slot(lat, mu, parity, 0);
     cudaError_t e;
-    switch (mu) {
-    case 0: e = launch_hb<0>(p, lat->device, lat->stream); break;
-    case 1: e = launch_hb<1>(p, lat->device, lat->stream); break;
-    case 2: e = launch_hb<2>(p, lat->device, lat->stream); break;
-    default: e = launch_hb<3>(p, lat->device, lat->stream); break;
+    if (p.plaq) {
+        switch (mu) {
+        case 1: e = launch_hb<1, true>(p, lat->device, lat->stream); break;
+        case 2: e = launch_hb<2, true>(p, lat->device, lat->stream); break;
+        default: e = launch_hb<3, true>(p, lat->device, lat->stream); break;
+        }
+    } else {
+        switch (mu) {
+        case 0: e = launch_hb<0, false>(p, lat->device, lat->stream); break;
+        case 1: e = launch_hb<1, false>(p, lat->device, lat->stream); break;
+        case 2: e = launch_hb<2, false>(p, lat->device, lat->stream); break;
+        default: e = launch_hb<3, false>(p, lat->device, lat->stream); break;
+        }
     }
     SU2_CUDA(e);
     return SU2_OK;
@@ -318,15 +353,23 @@ static su2_status read_timing(su2_lattice *lat, su2_stats *stats)
     return st != SU2_OK ? st : st2;
 }
 
-// One heat-bath sweep, then the lattice's over-relaxation sweeps.
+// One heat-bath sweep, then the lattice's over-relaxation sweeps; when the
+// sweep is measured (lat->fused_part set), the last of these sweeps adds the
+// plaquette.
 static su2_status one_sweep(su2_lattice *lat)
 {
+    double *const fused = lat->fused_part;
+    if (lat->overrelax > 0) lat->fused_part = nullptr;
     for (int mu = 0; mu < 4; ++mu)
         for (int parity = 0; parity < 2; ++parity) {
             su2_status st = timed_phase(lat, mu, parity, lat->sweep);
-            if (st != SU2_OK) return st;
+            if (st != SU2_OK) {
+                lat->fused_part = fused;
+                return st;
+            }
         }
     lat->sweep += 1;
+    lat->fused_part = fused;
     return lat->overrelax > 0 ? overrelax_sweeps(lat, lat->overrelax) : SU2_OK;
 }
 
@@ -363,10 +406,20 @@ su2_status su2_generate(su2_lattice *lat, int nsweeps, int measure_every, int re
     lat->or_log.used = 0;
     int m = 0;
     for (int s = 1; s <= nsweeps; ++s) {
-        if ((st = one_sweep(lat)) != SU2_OK) return st;
-        if (reunit_every > 0 && s % reunit_every == 0 && (st = launch_reunitarize(lat)) != SU2_OK) return st;
-        if (measure_every > 0 && s % measure_every == 0) {
-            if ((st = launch_plaquette(lat, lat->scratch.history + m)) != SU2_OK) return st;
+        const bool measure = measure_every > 0 && s % measure_every == 0;
+        const bool reunit = reunit_every > 0 && s % reunit_every == 0;
+        // the plaquette comes out of the sweep itself unless the links are
+        // reunitarized before the measurement
+        const bool fused = measure && !reunit;
+        if (fused && (st = fused_begin(lat)) != SU2_OK) return st;
+        if ((st = one_sweep(lat)) != SU2_OK) {
+            lat->fused_part = nullptr;
+            return st;
+        }
+        if (reunit && (st = launch_reunitarize(lat)) != SU2_OK) return st;
+        if (measure) {
+            st = fused ? fused_finish(lat, lat->scratch.history + m) : launch_plaquette(lat, lat->scratch.history + m);
+            if (st != SU2_OK) return st;
             if ((st = launch_polyakov(lat, lat->scratch.history + lat->scratch.history_cap + m)) != SU2_OK) return st;
             ++m;
         }

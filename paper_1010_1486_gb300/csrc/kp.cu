@@ -10,6 +10,7 @@
 // beta k < 2 are drawn by Creutz's method exactly as the plain kernel does.
 #include <algorithm>
 
+#include "observables.cuh"
 #include "staple.cuh"
 #include "su2_device.cuh"
 #include "su2_internal.h"
@@ -34,6 +35,7 @@ struct KpParams {
     unsigned long long *trial_slots;
     unsigned int *flags;
     const unsigned int *gate;  // skip the phase while *gate == 1 (learned sweeps)
+    double *plaq;              // measuring phases: block partials of the plaquettes of planes (nu < mu, mu)
 };
 
 // One trial (block t of the KP stream): a0 = 1 - 2 u, and whether it is
@@ -68,12 +70,15 @@ constexpr int kRetryCap = 64;  // per warp: at most 31 left over + 32 pushed by 
 // lane's rejections.  Every draw depends only on the link's counters, so the
 // phase computes exactly the one-thread-per-link definition.  Lanes past the
 // end (last round, next round) work on a clamped index and drop their
-// results, so the main path has no divergent branch.
-template <int MU>
+// results, so the main path has no divergent branch.  MEAS: the plaquette
+// contributions (1/2) Tr U'S, S the staple terms of nu < MU, as in the
+// Creutz kernel.
+template <int MU, bool MEAS>
 __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(const KpParams p)
 {
     if (p.gate != nullptr && *(volatile const unsigned int *)p.gate == 1u) return;
     __shared__ float4 s_ut[kKpWarps][kRetryCap];
+    __shared__ float4 s_sp[MEAS ? kKpWarps : 1][kRetryCap];
     __shared__ float s_bk[kKpWarps][kRetryCap];
     __shared__ int s_eo[kKpWarps][kRetryCap];
     const int lane = threadIdx.x & 31;
@@ -84,6 +89,7 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
     const uint32_t sw_kp = stream_word(kKennedyPendleton, (uint32_t)p.parity, MU);
     const uint32_t sw_dir = stream_word(kDirection, (uint32_t)p.parity, MU);
     unsigned int trials = 0;
+    double plaq = 0.0;
     int queued = 0;  // warp-uniform length of the retry queue
 
     // Trials 1, 2, ... of the queue entry of this lane (lane < n), then the
@@ -100,8 +106,10 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
                 if (kp_trial(philox_rk(make_uint4((uint32_t)eo, p.sweep, sw_kp, (uint32_t)t), p.rk), two_bk, a0))
                     break;
             if (t < kMaxTrials) {
-                p.links[link_index(p.g, MU, p.parity, eo)] =
+                const float4 out =
                     direction_update(a0, ut, philox_rk(make_uint4((uint32_t)eo, p.sweep, sw_dir, 0u), p.rk));
+                p.links[link_index(p.g, MU, p.parity, eo)] = out;
+                if (MEAS) plaq += (double)qmul_re(out, s_sp[MEAS ? wib : 0][q]);
                 trials += (unsigned int)(t + 1);
             } else {
                 atomicAdd(&p.flags[0], 1u);  // trial cap: the link keeps its old value
@@ -114,13 +122,17 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
     int base = blockIdx.x * kKpThreads + (wib << 5);
     int cur = base + lane;
     float4 v_cur = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float4 sp_cur = v_cur;  // MEAS: staple terms of nu < MU (the first MU groups)
     if (base < p.g.vh) {
         const int e = min(cur, last);
         const Coord x = eo_to_coord(p.g, e, p.parity);
         const int e_p = eo_fwd<MU>(p.g, x, e);
         v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 0>::value>(p.links, p.g, x, e, e_p, p.parity));
+        if (MU == 1) sp_cur = v_cur;
         v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 1>::value>(p.links, p.g, x, e, e_p, p.parity));
+        if (MU == 2) sp_cur = v_cur;
         v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 2>::value>(p.links, p.g, x, e, e_p, p.parity));
+        if (MU == 3) sp_cur = v_cur;
     }
     while (base < p.g.vh) {  // warp-uniform
         const bool valid = cur <= last;
@@ -140,6 +152,7 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
         uint4 wd = make_uint4((uint32_t)cur, p.sweep, sw_dir, 0u);
         philox2_rk(w, wd, p.rk);
         float4 v_next = add_nu_terms(make_float4(0.0f, 0.0f, 0.0f, 0.0f), nl);
+        float4 sp_next = v_next;
         // ---- part 1
         nl = load_nu_eo<MU, OtherDir<MU, 1>::value>(p.links, p.g, xn, en, en_p, p.parity);
         float a0;
@@ -151,6 +164,7 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
             const int n = heatbath_draw(v_cur, p.beta, p.rk, (uint32_t)cur, p.sweep, (uint32_t)p.parity, MU, out);
             if (n > 0) {
                 p.links[link_index(p.g, MU, p.parity, cur)] = out;
+                if (MEAS) plaq += (double)qmul_re(out, sp_cur);
                 trials += (unsigned int)n;
             } else {
                 atomicAdd(&p.flags[0], 1u);
@@ -163,15 +177,19 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
             s_ut[wib][q] = ut;
             s_bk[wib][q] = bk;
             s_eo[wib][q] = cur;
+            if (MEAS) s_sp[MEAS ? wib : 0][q] = sp_cur;
         }
         queued += __popc(parked);
         v_next = add_nu_terms(v_next, nl);
+        if (MU == 2) sp_next = v_next;
         // ---- part 2
         nl = load_nu_eo<MU, OtherDir<MU, 2>::value>(p.links, p.g, xn, en, en_p, p.parity);
         const float4 out = direction_update(a0, ut, wd);
         if (accepted) p.links[link_index(p.g, MU, p.parity, cur)] = out;
+        if (MEAS && accepted) plaq += (double)qmul_re(out, sp_cur);
         trials += accepted ? 1u : 0u;
         v_next = add_nu_terms(v_next, nl);
+        if (MU == 3) sp_next = v_next;
         __syncwarp();
         if (queued >= 32) {
             queued -= 32;
@@ -180,6 +198,7 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
         base += stride;
         cur = nxt;
         v_cur = v_next;
+        sp_cur = sp_next;
     }
     if (queued > 0) retry(0, queued);
     const unsigned int wsum = __reduce_add_sync(0xffffffffu, trials);
@@ -187,24 +206,28 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
         atomicAdd(&p.trial_slots[(2 * MU + p.parity) * kTrialSlots + ((blockIdx.x * kKpWarps + wib) &
                                                                       (kTrialSlots - 1))],
                   (unsigned long long)wsum);
+    if (MEAS) {
+        const double total = block_sum(plaq);
+        if (threadIdx.x == 0) p.plaq[blockIdx.x] = total;
+    }
 }
 
-template <int MU>
+template <int MU, bool MEAS>
 static cudaError_t launch_kp(const KpParams &p, int device, cudaStream_t stream)
 {
     static int per_sm[64] = {};
     static int sms[64] = {};
     if (device < 0 || device >= 64) device = 0;
     if (!per_sm[device]) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[device], kp_phase_kernel<MU>,
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[device], kp_phase_kernel<MU, MEAS>,
                                                                       kKpThreads, 0);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms[device], cudaDevAttrMultiProcessorCount, device);
         if (e != cudaSuccess) return e;
         per_sm[device] = std::max(1, per_sm[device]);
     }
     const int want = (p.g.vh + kKpThreads - 1) / kKpThreads;
-    const int grid = std::max(1, std::min(want, per_sm[device] * sms[device]));
-    kp_phase_kernel<MU><<<grid, kKpThreads, 0, stream>>>(p);
+    const int grid = std::max(1, std::min(std::min(want, per_sm[device] * sms[device]), kFusedSlots));
+    kp_phase_kernel<MU, MEAS><<<grid, kKpThreads, 0, stream>>>(p);
     return cudaGetLastError();
 }
 
@@ -220,12 +243,21 @@ su2_status launch_kp_phase(su2_lattice *lat, int mu, int parity, uint32_t sweep,
     p.trial_slots = lat->scratch.trials;
     p.flags = lat->scratch.flags;
     p.gate = gate;
+    p.plaq = fused_slot(lat, mu, parity, 0);
     cudaError_t e;
-    switch (mu) {
-    case 0: e = launch_kp<0>(p, lat->device, lat->stream); break;
-    case 1: e = launch_kp<1>(p, lat->device, lat->stream); break;
-    case 2: e = launch_kp<2>(p, lat->device, lat->stream); break;
-    default: e = launch_kp<3>(p, lat->device, lat->stream); break;
+    if (p.plaq) {
+        switch (mu) {
+        case 1: e = launch_kp<1, true>(p, lat->device, lat->stream); break;
+        case 2: e = launch_kp<2, true>(p, lat->device, lat->stream); break;
+        default: e = launch_kp<3, true>(p, lat->device, lat->stream); break;
+        }
+    } else {
+        switch (mu) {
+        case 0: e = launch_kp<0, false>(p, lat->device, lat->stream); break;
+        case 1: e = launch_kp<1, false>(p, lat->device, lat->stream); break;
+        case 2: e = launch_kp<2, false>(p, lat->device, lat->stream); break;
+        default: e = launch_kp<3, false>(p, lat->device, lat->stream); break;
+        }
     }
     SU2_CUDA(e);
     return SU2_OK;

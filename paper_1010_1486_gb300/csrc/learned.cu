@@ -49,6 +49,7 @@ struct LearnedParams {
     const unsigned int *gate;          // runs only while *gate == 1
     unsigned long long *acc_slots;     // [8][64]: accepted links per phase (call total)
     unsigned long long *sweep_slots;   // [64]: accepted links of this sweep
+    double *plaq;                      // measuring phases: block partials of the plaquettes of planes (nu < mu, mu)
 };
 
 __device__ __forceinline__ unsigned int block_sum_u32(unsigned int v)
@@ -74,7 +75,9 @@ __device__ __forceinline__ unsigned int block_sum_u32(unsigned int v)
 //   part 0  the Philox block, k, U~^dag, the table row, a0' = f(2 u0 - 1);
 //   part 1  a_cur, f^-1(a_cur), the Metropolis test;
 //   part 2  the direction and the store.
-template <int MU>
+// MEAS: the plaquette contributions (1/2) Tr U'S of the final link (new or
+// kept), S the staple terms of nu < MU, as in the heat-bath kernels.
+template <int MU, bool MEAS>
 __global__ void __launch_bounds__(kLearnThreads, kLearnMinBlocks) learned_phase_kernel(const LearnedParams p)
 {
     extern __shared__ float2 s_pairs[];
@@ -94,14 +97,19 @@ __global__ void __launch_bounds__(kLearnThreads, kLearnMinBlocks) learned_phase_
     int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31);
     int cur = base + (threadIdx.x & 31);
     unsigned int acc = 0;
+    double plaq = 0.0;
     float4 v_cur = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float4 sp_cur = v_cur;  // MEAS: staple terms of nu < MU (the first MU groups)
     if (base < p.g.vh) {
         const int e = min(cur, last);
         const Coord x = eo_to_coord(p.g, e, p.parity);
         const int e_p = eo_fwd<MU>(p.g, x, e);
         v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 0>::value>(p.links, p.g, x, e, e_p, p.parity));
+        if (MU == 1) sp_cur = v_cur;
         v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 1>::value>(p.links, p.g, x, e, e_p, p.parity));
+        if (MU == 2) sp_cur = v_cur;
         v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 2>::value>(p.links, p.g, x, e, e_p, p.parity));
+        if (MU == 3) sp_cur = v_cur;
     }
     while (base < p.g.vh) {  // warp-uniform
         const bool valid = cur <= last;
@@ -116,25 +124,35 @@ __global__ void __launch_bounds__(kLearnThreads, kLearnMinBlocks) learned_phase_
         const uint4 w = philox_rk(make_uint4((uint32_t)cur, p.sweep, sw, 0u), p.rk);
         const learned::LearnedDraw r = learned::learned_propose(pr, p.beta, v_cur, uniform01(w.x));
         float4 v_next = add_nu_terms(make_float4(0.0f, 0.0f, 0.0f, 0.0f), nl);
+        float4 sp_next = v_next;
         // ---- part 1
         nl = load_nu_eo<MU, OtherDir<MU, 1>::value>(p.links, p.g, xn, en, en_p, p.parity);
         const bool accept = valid && learned::learned_accept(r, old, uniform01(w.y));
         v_next = add_nu_terms(v_next, nl);
+        if (MU == 2) sp_next = v_next;
         // ---- part 2
         nl = load_nu_eo<MU, OtherDir<MU, 2>::value>(p.links, p.g, xn, en, en_p, p.parity);
         const float4 out = direction_from_uniforms(r.a_new, r.d.ut, uniform01(w.z), uniform01(w.w));
         if (accept) p.links[li] = out;
+        if (MEAS && valid) plaq += (double)qmul_re(accept ? out : old, sp_cur);
         acc += accept ? 1u : 0u;
         v_next = add_nu_terms(v_next, nl);
+        if (MU == 3) sp_next = v_next;
         base += stride;
         cur = nxt;
         v_cur = v_next;
+        sp_cur = sp_next;
     }
     const unsigned int total = block_sum_u32(acc);
     if (threadIdx.x == 0 && total) {
         atomicAdd(&p.acc_slots[(2 * MU + p.parity) * kAcceptSlots + (blockIdx.x & (kAcceptSlots - 1))],
                   (unsigned long long)total);
         atomicAdd(&p.sweep_slots[blockIdx.x & (kAcceptSlots - 1)], (unsigned long long)total);
+    }
+    if (MEAS) {
+        __syncthreads();
+        const double ptotal = block_sum(plaq);
+        if (threadIdx.x == 0) p.plaq[blockIdx.x] = ptotal;
     }
 }
 
@@ -201,7 +219,7 @@ static cudaError_t launch_persistent(Kernel kernel, const LearnedParams &p, int 
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kLearnThreads, smem);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, lat->device);
     if (e != cudaSuccess) return e;
-    const int grid = std::max(1, std::min(want, std::max(1, per_sm) * sms));
+    const int grid = std::max(1, std::min(std::min(want, std::max(1, per_sm) * sms), kFusedSlots));
     kernel<<<grid, kLearnThreads, smem, lat->stream>>>(p);
     return cudaGetLastError();
 }
@@ -224,14 +242,23 @@ static su2_status launch_learned_phase(su2_lattice *lat, int mu, int parity)
     p.gate = lat->learned_ctl;
     p.acc_slots = lat->accept_slots;
     p.sweep_slots = lat->accept_slots + 8 * kAcceptSlots;
+    p.plaq = fused_slot(lat, mu, parity, 1);
     const size_t smem = sizeof(float2) * (size_t)(p.G - 1) * learned::kParams;
     const int want = (p.g.vh + kLearnThreads - 1) / kLearnThreads;
     cudaError_t e;
-    switch (mu) {
-    case 0: e = launch_persistent(learned_phase_kernel<0>, p, want, smem, lat); break;
-    case 1: e = launch_persistent(learned_phase_kernel<1>, p, want, smem, lat); break;
-    case 2: e = launch_persistent(learned_phase_kernel<2>, p, want, smem, lat); break;
-    default: e = launch_persistent(learned_phase_kernel<3>, p, want, smem, lat); break;
+    if (p.plaq) {
+        switch (mu) {
+        case 1: e = launch_persistent(learned_phase_kernel<1, true>, p, want, smem, lat); break;
+        case 2: e = launch_persistent(learned_phase_kernel<2, true>, p, want, smem, lat); break;
+        default: e = launch_persistent(learned_phase_kernel<3, true>, p, want, smem, lat); break;
+        }
+    } else {
+        switch (mu) {
+        case 0: e = launch_persistent(learned_phase_kernel<0, false>, p, want, smem, lat); break;
+        case 1: e = launch_persistent(learned_phase_kernel<1, false>, p, want, smem, lat); break;
+        case 2: e = launch_persistent(learned_phase_kernel<2, false>, p, want, smem, lat); break;
+        default: e = launch_persistent(learned_phase_kernel<3, false>, p, want, smem, lat); break;
+        }
     }
     SU2_CUDA(e);
     return SU2_OK;
@@ -330,19 +357,26 @@ su2_status su2_learned_generate(su2_lattice *lat, int nsweeps, int measure_every
     const double links = 4.0 * (double)lat->vol;
     int m = 0;
     for (int s = 1; s <= nsweeps; ++s) {
+        // a measured sweep adds the plaquette through whichever kernel runs
+        // each phase (learned, or the plain fallback)
+        const bool measure = measure_every > 0 && s % measure_every == 0;
+        if (measure && (st = fused_begin(lat)) != SU2_OK) return st;
         for (int mu = 0; mu < 4; ++mu)
             for (int parity = 0; parity < 2; ++parity) {
-                if ((st = timing_begin(lat, lat->hb_log)) != SU2_OK) return st;
-                if ((st = launch_learned_phase(lat, mu, parity)) != SU2_OK) return st;
-                if ((st = timing_end(lat, lat->hb_log)) != SU2_OK) return st;
-                if ((st = launch_hb_phase(lat, mu, parity, lat->sweep, lat->learned_ctl)) != SU2_OK) return st;
+                if ((st = timing_begin(lat, lat->hb_log)) == SU2_OK) st = launch_learned_phase(lat, mu, parity);
+                if (st == SU2_OK) st = timing_end(lat, lat->hb_log);
+                if (st == SU2_OK) st = launch_hb_phase(lat, mu, parity, lat->sweep, lat->learned_ctl);
+                if (st != SU2_OK) {
+                    lat->fused_part = nullptr;
+                    return st;
+                }
             }
         learned_decide_kernel<<<1, 32, 0, lat->stream>>>(lat->learned_ctl, lat->accept_slots + 8 * kAcceptSlots,
                                                          links, min_acceptance);
         SU2_CUDA(cudaGetLastError());
         lat->sweep += 1;
-        if (measure_every > 0 && s % measure_every == 0) {
-            if ((st = launch_plaquette(lat, lat->scratch.history + m)) != SU2_OK) return st;
+        if (measure) {
+            if ((st = fused_finish(lat, lat->scratch.history + m)) != SU2_OK) return st;
             if ((st = launch_polyakov(lat, lat->scratch.history + lat->scratch.history_cap + m)) != SU2_OK) return st;
             ++m;
         }

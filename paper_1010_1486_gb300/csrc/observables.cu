@@ -72,6 +72,36 @@ su2_status launch_plaquette(su2_lattice *lat, double *dst)
     return SU2_OK;
 }
 
+// Ordered sum of the fused-plaquette slot region (one block).
+__global__ void __launch_bounds__(kReduceThreads) fused_plaquette_kernel(const double *__restrict__ part, int n,
+                                                                        double scale, double *__restrict__ dst)
+{
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v += part[i];
+    v = block_sum(v);
+    if (threadIdx.x == 0) *dst = v * scale;
+}
+
+su2_status fused_begin(su2_lattice *lat)
+{
+    if (lat->scratch.partials_cap < kFusedRegion) {
+        set_last_error("reduction scratch too small for the fused plaquette");
+        return SU2_E_INVAL;
+    }
+    SU2_CUDA(cudaMemsetAsync(lat->scratch.partials, 0, sizeof(double) * kFusedRegion, lat->stream));
+    lat->fused_part = lat->scratch.partials;
+    return SU2_OK;
+}
+
+su2_status fused_finish(su2_lattice *lat, double *dst)
+{
+    lat->fused_part = nullptr;
+    fused_plaquette_kernel<<<1, kReduceThreads, 0, lat->stream>>>(lat->scratch.partials, kFusedRegion,
+                                                                 1.0 / (6.0 * (double)lat->vol), dst);
+    SU2_CUDA(cudaGetLastError());
+    return SU2_OK;
+}
+
 su2_status launch_polyakov(su2_lattice *lat, double *dst)
 {
     const Geom g = geom_of(lat);

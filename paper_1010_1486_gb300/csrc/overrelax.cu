@@ -6,6 +6,7 @@
 // the new one, 144 bytes per link update.
 #include <algorithm>
 
+#include "observables.cuh"
 #include "staple.cuh"
 #include "su2_device.cuh"
 #include "su2_internal.h"
@@ -22,6 +23,7 @@ struct OrParams {
     float4 *links;
     Geom g;
     int parity;
+    double *plaq;  // measuring phases: block partials of the plaquettes of planes (nu < mu, mu)
 };
 
 // U~^dag from the staple (identity if k = 0), as the heat bath's setup.
@@ -40,22 +42,29 @@ __device__ __forceinline__ float4 staple_direction(float4 v)
 // update, then folds the loaded group into the next round's staple:
 //   part 0  the old link, U~^dag;  part 1  U~^dag U^dag;  part 2  (...) U~^dag
 //   and the store.  Lanes past the end work on a clamped index and drop their
-// results, so the loop body has no divergent branch.
-template <int MU>
+// results, so the loop body has no divergent branch.  MEAS: the plaquette
+// contributions (1/2) Tr U'S, S the staple terms of nu < MU, as in the
+// heat-bath kernels.
+template <int MU, bool MEAS>
 __global__ void __launch_bounds__(kOrThreads, kOrMinBlocks) or_phase_kernel(const OrParams p)
 {
     const int stride = gridDim.x * kOrThreads;
     const int last = p.g.vh - 1;
     int base = blockIdx.x * kOrThreads + (threadIdx.x & ~31);
     int cur = base + (threadIdx.x & 31);
+    double plaq = 0.0;
     float4 v_cur = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float4 sp_cur = v_cur;  // MEAS: staple terms of nu < MU (the first MU groups)
     if (base < p.g.vh) {
         const int e = min(cur, last);
         const Coord x = eo_to_coord(p.g, e, p.parity);
         const int e_p = eo_fwd<MU>(p.g, x, e);
         v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 0>::value>(p.links, p.g, x, e, e_p, p.parity));
+        if (MU == 1) sp_cur = v_cur;
         v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 1>::value>(p.links, p.g, x, e, e_p, p.parity));
+        if (MU == 2) sp_cur = v_cur;
         v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 2>::value>(p.links, p.g, x, e, e_p, p.parity));
+        if (MU == 3) sp_cur = v_cur;
     }
     while (base < p.g.vh) {  // warp-uniform
         const bool valid = cur <= last;
@@ -69,37 +78,46 @@ __global__ void __launch_bounds__(kOrThreads, kOrMinBlocks) or_phase_kernel(cons
         const float4 old = p.links[li];
         const float4 ut = staple_direction(v_cur);
         float4 v_next = add_nu_terms(make_float4(0.0f, 0.0f, 0.0f, 0.0f), nl);
+        float4 sp_next = v_next;
         // ---- part 1
         nl = load_nu_eo<MU, OtherDir<MU, 1>::value>(p.links, p.g, xn, en, en_p, p.parity);
         const float4 t = qmul(ut, qdag(old));
         v_next = add_nu_terms(v_next, nl);
+        if (MU == 2) sp_next = v_next;
         // ---- part 2
         nl = load_nu_eo<MU, OtherDir<MU, 2>::value>(p.links, p.g, xn, en, en_p, p.parity);
         const float4 out = qmul(t, ut);
         if (valid) p.links[li] = out;
+        if (MEAS && valid) plaq += (double)qmul_re(out, sp_cur);
         v_next = add_nu_terms(v_next, nl);
+        if (MU == 3) sp_next = v_next;
         base += stride;
         cur = nxt;
         v_cur = v_next;
+        sp_cur = sp_next;
+    }
+    if (MEAS) {
+        const double total = block_sum(plaq);
+        if (threadIdx.x == 0) p.plaq[blockIdx.x] = total;
     }
 }
 
-template <int MU>
+template <int MU, bool MEAS>
 static cudaError_t launch_or(const OrParams &p, int device, cudaStream_t stream)
 {
     static int per_sm[64] = {};
     static int sms[64] = {};
     if (device < 0 || device >= 64) device = 0;
     if (!per_sm[device]) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[device], or_phase_kernel<MU>,
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[device], or_phase_kernel<MU, MEAS>,
                                                                       kOrThreads, 0);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms[device], cudaDevAttrMultiProcessorCount, device);
         if (e != cudaSuccess) return e;
         per_sm[device] = std::max(1, per_sm[device]);
     }
     const int want = (p.g.vh + kOrThreads - 1) / kOrThreads;
-    const int grid = std::max(1, std::min(want, per_sm[device] * sms[device]));
-    or_phase_kernel<MU><<<grid, kOrThreads, 0, stream>>>(p);
+    const int grid = std::max(1, std::min(std::min(want, per_sm[device] * sms[device]), kFusedSlots));
+    or_phase_kernel<MU, MEAS><<<grid, kOrThreads, 0, stream>>>(p);
     return cudaGetLastError();
 }
 
@@ -109,12 +127,21 @@ su2_status launch_or_phase(su2_lattice *lat, int mu, int parity)
     p.links = lat->links;
     p.g = geom_of(lat);
     p.parity = parity;
+    p.plaq = fused_slot(lat, mu, parity, 0);
     cudaError_t e;
-    switch (mu) {
-    case 0: e = launch_or<0>(p, lat->device, lat->stream); break;
-    case 1: e = launch_or<1>(p, lat->device, lat->stream); break;
-    case 2: e = launch_or<2>(p, lat->device, lat->stream); break;
-    default: e = launch_or<3>(p, lat->device, lat->stream); break;
+    if (p.plaq) {
+        switch (mu) {
+        case 1: e = launch_or<1, true>(p, lat->device, lat->stream); break;
+        case 2: e = launch_or<2, true>(p, lat->device, lat->stream); break;
+        default: e = launch_or<3, true>(p, lat->device, lat->stream); break;
+        }
+    } else {
+        switch (mu) {
+        case 0: e = launch_or<0, false>(p, lat->device, lat->stream); break;
+        case 1: e = launch_or<1, false>(p, lat->device, lat->stream); break;
+        case 2: e = launch_or<2, false>(p, lat->device, lat->stream); break;
+        default: e = launch_or<3, false>(p, lat->device, lat->stream); break;
+        }
     }
     SU2_CUDA(e);
     return SU2_OK;
@@ -122,14 +149,21 @@ su2_status launch_or_phase(su2_lattice *lat, int mu, int parity)
 
 su2_status overrelax_sweeps(su2_lattice *lat, int n)
 {
-    for (int s = 0; s < n; ++s)
+    double *const fused = lat->fused_part;  // only the last sweep measures
+    for (int s = 0; s < n; ++s) {
+        lat->fused_part = s == n - 1 ? fused : nullptr;
         for (int mu = 0; mu < 4; ++mu)
             for (int parity = 0; parity < 2; ++parity) {
                 su2_status st = timing_begin(lat, lat->or_log);
                 if (st == SU2_OK) st = launch_or_phase(lat, mu, parity);
                 if (st == SU2_OK) st = timing_end(lat, lat->or_log);
-                if (st != SU2_OK) return st;
+                if (st != SU2_OK) {
+                    lat->fused_part = fused;
+                    return st;
+                }
             }
+    }
+    lat->fused_part = fused;
     return SU2_OK;
 }
 

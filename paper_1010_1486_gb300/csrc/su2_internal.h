@@ -16,6 +16,12 @@ namespace su2 {
 constexpr int kTrialSlots = 64;      // trial counters are spread over 64 slots per phase
 constexpr int kReduceThreads = 256;  // block size of the observable kernels
 constexpr int kHbThreads = 128;      // block size of the heat-bath phase kernel (4 warps)
+// Plaquette measured during a sweep: the odd phases of mu = 1, 2, 3 each add
+// the plaquettes of planes (nu, mu), nu < mu, through the new links; block
+// partials go to slots [(mu - 1) * 2 + kind] * kFusedSlots + block (kind 0:
+// heat bath / over-relaxation, 1: learned), zero-filled first.
+constexpr int kFusedSlots = 1024;
+constexpr int kFusedRegion = 6 * kFusedSlots;
 
 // Device scratch of a lattice, carved from one allocation.
 struct DeviceScratch {
@@ -59,6 +65,7 @@ struct su2_lattice {
     size_t staging_bytes = 0;
 
     int overrelax = 0;  // over-relaxation sweeps after each heat-bath sweep
+    double *fused_part = nullptr;  // slot region of the plaquette measured in the current sweep, or NULL
 
     bool timing = false;
     su2::EventLog hb_log;  // heat-bath (and learned) phase launches
@@ -137,6 +144,19 @@ void device_free(void *ptr, size_t bytes, int device, cudaStream_t stream);
 cudaError_t start_links(float4 *links, const Geom &g, bool hot, uint64_t seed, unsigned int *flags,
                         cudaStream_t stream);
 cudaError_t convert_links(float4 *eo_links, float4 *lex_links, const Geom &g, bool to_lex, cudaStream_t stream);
+
+// Block-partial slots of the fused plaquette for phase (mu, parity) and kernel
+// kind, or NULL when that phase does not measure.
+inline double *fused_slot(const su2_lattice *lat, int mu, int parity, int kind)
+{
+    if (!lat->fused_part || parity != 1 || mu < 1) return nullptr;
+    return lat->fused_part + ((mu - 1) * 2 + kind) * kFusedSlots;
+}
+// Zero-fills the slot region and points the lattice at it (the next sweep
+// measures), or detaches it; fused_finish sums the region in index order into
+// *dst (device) scaled to the mean plaquette.
+su2_status fused_begin(su2_lattice *lat);
+su2_status fused_finish(su2_lattice *lat, double *dst);
 
 // Launchers (each enqueues on lat->stream and returns a status of the launch).
 su2_status launch_cold_start(su2_lattice *lat);
