@@ -25,16 +25,18 @@ def autocorrelation(series: np.ndarray, tmax: int) -> np.ndarray:
     return acf / (n - np.arange(tmax + 1))
 
 
-def _pooled_autocovariance(replicas, tmax: int) -> np.ndarray:
+def _pooled_autocovariance(replicas, tmax: int, own_means: bool = False) -> np.ndarray:
     """Gamma(t), t = 0..tmax, of several runs of the same chain (replicas):
-    deviations from the common mean, lag products summed over all runs,
-    divided by the number of pairs (Wolff 2004, Sec. 3.3)."""
+    deviations from the common mean (or, with own_means, from each run's own
+    mean, which keeps a slow drift between runs out of Gamma), lag products
+    summed over all runs, divided by the number of pairs (Wolff 2004,
+    Sec. 3.3)."""
     mean = np.concatenate(replicas).mean()
     num = np.zeros(tmax + 1)
     pairs = np.zeros(tmax + 1)
     for a in replicas:
         n = a.size
-        d = a - mean
+        d = a - (a.mean() if own_means else mean)
         nfft = 1 << (2 * n - 1).bit_length()
         f = np.fft.rfft(d, nfft)
         acf = np.fft.irfft(f * np.conj(f), nfft)
@@ -44,11 +46,13 @@ def _pooled_autocovariance(replicas, tmax: int) -> np.ndarray:
     return num / np.maximum(pairs, 1.0)
 
 
-def tau_int(series, s_factor: float = 1.5):
+def tau_int(series, s_factor: float = 1.5, own_means: bool = False):
     """Returns (tau_int, its statistical error, window W, error of the mean).
     `series` is one run, or a list of runs of the same chain (replicas: their
-    autocovariances are pooled about the common mean before the windowed
-    sum, which avoids the bias of averaging tau_int over short runs)."""
+    autocovariances are pooled before the windowed sum, which avoids the bias
+    of averaging tau_int over short runs; about the common mean, or with
+    own_means about each run's mean, for runs taken at different times of a
+    slowly drifting chain)."""
     if isinstance(series, (list, tuple)):
         replicas = [np.asarray(r, dtype=np.float64) for r in series]
     else:
@@ -58,7 +62,7 @@ def tau_int(series, s_factor: float = 1.5):
         raise ValueError("series too short")
     tmax = min(min(r.size for r in replicas) // 2, 100000)
     gamma = (autocorrelation(replicas[0], tmax) if len(replicas) == 1
-             else _pooled_autocovariance(replicas, tmax))
+             else _pooled_autocovariance(replicas, tmax, own_means))
     if gamma[0] <= 0.0:
         return 0.5, 0.0, 0, 0.0
     rho = gamma / gamma[0]

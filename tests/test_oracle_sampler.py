@@ -131,6 +131,12 @@ def test_tau_int_on_ar1_series():
     reps = [x[i * 250:(i + 1) * 250] for i in range(16)]
     tau_s, dtau_s, _, _ = tau_int(reps)
     assert abs(tau_s - want) < 0.35 * want, (tau_s, want)
+    # replicas taken along a drifting chain: each about its own mean, the
+    # drift between replicas stays out of tau
+    drift = [x[i * 2_000:(i + 1) * 2_000] + 3.0 * i for i in range(16)]
+    tau_d, dtau_d, _, _ = tau_int(drift, own_means=True)
+    assert abs(tau_d - want) < max(3 * dtau_d, 0.1 * want), (tau_d, want)
+    assert tau_int(drift)[0] > 2 * want  # about the common mean the drift looks like correlation
     # white noise: tau = 1/2
     tau0, _, _, err0 = tau_int(rng.normal(size=100_000))
     assert abs(tau0 - 0.5) < 0.05
