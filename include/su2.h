@@ -117,7 +117,12 @@ su2_status su2_heatbath_phase(su2_lattice *lat, int mu, int parity);
  * (0 = never) the plaquette and Polyakov loop are computed on the device and
  * kept; after every `reunit_every`-th sweep (0 = never) the links are
  * reunitarized.  plaq and poly (host, nullable) receive nsweeps/measure_every
- * values each.  Synchronises once at the end. */
+ * values each.  Synchronises once at the end.  The plaquette of a measured
+ * sweep is accumulated by the sweep itself (the odd phases of mu = 1, 2, 3
+ * see every plaquette of the final links once, as (1/2) Tr U'S over the
+ * staple terms S of the directions nu < mu); it equals su2_plaquette on the
+ * same links up to binary32 rounding of the single plaquettes.  A sweep
+ * reunitarized before its measurement uses the separate plaquette pass. */
 su2_status su2_generate(su2_lattice *lat, int nsweeps, int measure_every, int reunit_every, double *plaq,
                         double *poly, su2_stats *stats);
 
