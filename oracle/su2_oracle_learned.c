@@ -124,30 +124,34 @@ static int bin_of(const float *knots9, float v)
 
 /* a = f(z) on bin k with xi = (z - x_k)/w, s = h/w, t = xi(1 - xi):
  * a = y_k + h (s xi^2 + d_k t) / (s + (d_{k+1} + d_k - 2 s) t),
- * f'(z) = s^2 (d_{k+1} xi^2 + 2 s t + d_k (1 - xi)^2) / den^2. */
-static float spline_eval(const float p[LP], int k, float xi, float *fprime)
+ * f'(z) = s^2 (d_{k+1} xi^2 + 2 s t + d_k (1 - xi)^2) / den^2.
+ * Rounding (ours, the formulas are Durkan et al.'s): with r = 1/den rounded
+ * once, a = y_k + num r and f' = (s^2 m) r^2; the caller passes s. */
+static float spline_eval(const float p[LP], int k, float xi, float s, float *fprime)
 {
-    const float *x = p, *y = p + LK + 1, *d = p + 2 * (LK + 1);
-    const float w = x[k + 1] - x[k];
+    const float *y = p + LK + 1, *d = p + 2 * (LK + 1);
     const float h = y[k + 1] - y[k];
-    const float s = h / w;
     const float t = xi * (1.0f - xi);
     const float sigma = (d[k + 1] + d[k]) - 2.0f * s;
     const float den = fmaf(sigma, t, s);
     const float num = h * fmaf(s * xi, xi, d[k] * t);
     const float omx = 1.0f - xi;
     const float m = fmaf(d[k + 1] * xi, xi, fmaf(2.0f * s, t, d[k] * omx * omx));
-    *fprime = (s * s * m) / (den * den);
-    return y[k] + num / den;
+    const float r = 1.0f / den;
+    *fprime = (s * s * m) * (r * r);
+    return y[k] + num * r;
 }
 
+/* xi = (z - x_k) iw and s = h iw with iw = 1/w rounded once. */
 float orc_spline_forward(const float p[LP], float z, float *fprime)
 {
+    const float *y = p + LK + 1;
     const int k = bin_of(p, z);
-    const float w = p[k + 1] - p[k];
-    float xi = (z - p[k]) / w;
+    const float iw = 1.0f / (p[k + 1] - p[k]);
+    const float s = (y[k + 1] - y[k]) * iw;
+    float xi = (z - p[k]) * iw;
     xi = xi < 0.0f ? 0.0f : (xi > 1.0f ? 1.0f : xi);
-    float a = spline_eval(p, k, xi, fprime);
+    float a = spline_eval(p, k, xi, s, fprime);
     return a < -1.0f ? -1.0f : (a > 1.0f ? 1.0f : a);
 }
 
@@ -171,7 +175,7 @@ float orc_spline_inverse(const float p[LP], float a, float *fprime)
     const float denom = -beta - sqrtf(disc);
     float xi = denom != 0.0f ? (2.0f * c) / denom : 0.0f;
     xi = xi < 0.0f ? 0.0f : (xi > 1.0f ? 1.0f : xi);
-    spline_eval(p, k, xi, fprime);
+    spline_eval(p, k, xi, s, fprime);
     return fmaf(xi, w, x[k]);
 }
 
@@ -245,7 +249,8 @@ int orc_learned_link(const float *table, int G, float s_lo, float s_hi, float me
         accept = 1;
     } else {
         const float one_new = fmaf(-a_new, a_new, 1.0f);
-        const float ratio = sqrtf(one_new / one_cur) * (fp_new / fp_cur);
+        /* sqrt((1 - a'^2)/(1 - a^2)) f'(z')/f'(z) as one square root of one quotient */
+        const float ratio = sqrtf((one_new * (fp_new * fp_new)) / (one_cur * (fp_cur * fp_cur)));
         if (!(ratio > 0.0f)) {
             accept = 0;
         } else {

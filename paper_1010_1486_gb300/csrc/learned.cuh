@@ -119,35 +119,38 @@ __device__ __forceinline__ int bin_of(const P &p, int base, float v)
 }
 
 // a = y_k + h (s xi^2 + d_k t)/den, den = s + (d_{k+1} + d_k - 2 s) t, t = xi (1 - xi),
-// f' = s^2 (d_{k+1} xi^2 + 2 s t + d_k (1 - xi)^2) / den^2.
+// f' = s^2 (d_{k+1} xi^2 + 2 s t + d_k (1 - xi)^2) / den^2, evaluated with
+// r = 1/den rounded once: a = y_k + num r, f' = (s^2 m) r^2; the caller gives s.
 template <class P>
-__device__ __forceinline__ float spline_eval(const P &p, int k, float xi, float &fprime)
+__device__ __forceinline__ float spline_eval(const P &p, int k, float xi, float s, float &fprime)
 {
     constexpr int Y = kBins + 1, D = 2 * (kBins + 1);
-    const float w = __fsub_rn(p(k + 1), p(k));
     const float yk = p(Y + k);
     const float h = __fsub_rn(p(Y + k + 1), yk);
     const float dk = p(D + k), dk1 = p(D + k + 1);
-    const float s = __fdiv_rn(h, w);
     const float t = __fmul_rn(xi, __fsub_rn(1.0f, xi));
     const float sigma = __fsub_rn(__fadd_rn(dk1, dk), __fmul_rn(2.0f, s));
     const float den = __fmaf_rn(sigma, t, s);
     const float num = __fmul_rn(h, __fmaf_rn(__fmul_rn(s, xi), xi, __fmul_rn(dk, t)));
     const float omx = __fsub_rn(1.0f, xi);
     const float m = __fmaf_rn(__fmul_rn(dk1, xi), xi, __fmaf_rn(__fmul_rn(2.0f, s), t, __fmul_rn(__fmul_rn(dk, omx), omx)));
-    fprime = __fdiv_rn(__fmul_rn(__fmul_rn(s, s), m), __fmul_rn(den, den));
-    return __fadd_rn(yk, __fdiv_rn(num, den));
+    const float r = __fdiv_rn(1.0f, den);
+    fprime = __fmul_rn(__fmul_rn(__fmul_rn(s, s), m), __fmul_rn(r, r));
+    return __fadd_rn(yk, __fmul_rn(num, r));
 }
 
+// xi = (z - x_k) iw and s = h iw with iw = 1/w rounded once.
 template <class P>
 __device__ __forceinline__ float spline_forward(const P &p, float z, float &fprime)
 {
+    constexpr int Y = kBins + 1;
     const int k = bin_of(p, 0, z);
     const float xk = p(k);
-    const float w = __fsub_rn(p(k + 1), xk);
-    float xi = __fdiv_rn(__fsub_rn(z, xk), w);
+    const float iw = __fdiv_rn(1.0f, __fsub_rn(p(k + 1), xk));
+    const float s = __fmul_rn(__fsub_rn(p(Y + k + 1), p(Y + k)), iw);
+    float xi = __fmul_rn(__fsub_rn(z, xk), iw);
     xi = xi < 0.0f ? 0.0f : (xi > 1.0f ? 1.0f : xi);
-    const float a = spline_eval(p, k, xi, fprime);
+    const float a = spline_eval(p, k, xi, s, fprime);
     return a < -1.0f ? -1.0f : (a > 1.0f ? 1.0f : a);
 }
 
@@ -173,7 +176,7 @@ __device__ __forceinline__ float spline_inverse(const P &p, float a, float &fpri
     const float denom = __fsub_rn(-beta, __fsqrt_rn(disc));
     float xi = denom != 0.0f ? __fdiv_rn(__fmul_rn(2.0f, c), denom) : 0.0f;
     xi = xi < 0.0f ? 0.0f : (xi > 1.0f ? 1.0f : xi);
-    spline_eval(p, k, xi, fprime);
+    spline_eval(p, k, xi, s, fprime);
     return __fmaf_rn(xi, w, xk);
 }
 
@@ -235,7 +238,9 @@ __device__ __forceinline__ bool learned_accept(const LearnedDraw &r, float4 old,
     const float one_cur = __fmaf_rn(-acur, acur, 1.0f);
     if (!(one_cur > 0.0f)) return true;
     const float one_new = __fmaf_rn(-r.a_new, r.a_new, 1.0f);
-    const float ratio = __fmul_rn(__fsqrt_rn(__fdiv_rn(one_new, one_cur)), __fdiv_rn(r.fp_new, fp_cur));
+    // sqrt((1 - a'^2)/(1 - a^2)) f'(z')/f'(z) as one square root of one quotient
+    const float ratio = __fsqrt_rn(__fdiv_rn(__fmul_rn(one_new, __fmul_rn(r.fp_new, r.fp_new)),
+                                             __fmul_rn(one_cur, __fmul_rn(fp_cur, fp_cur))));
     if (!(ratio > 0.0f)) return false;
     const float delta = __fmaf_rn(r.d.bk, __fsub_rn(r.a_new, acur), log_series(ratio));
     return delta >= 0.0f || u1 <= exp_neg(delta);
