@@ -106,3 +106,38 @@ def test_binary32_plaquette_error_against_binary64():
     finally:
         su2.su2_destroy(h)
     assert max(errs_p) < 2e-7 and max(errs_l) < 1e-6, (max(errs_p), max(errs_l))
+
+
+def test_finite_temperature_scan_with_one_learned_proposal():
+    """The 32^3 x 4 scan with the learned proposal and its plain fallback: one
+    network trained on (beta k, a0) pairs pooled over the scan serves every
+    beta; each lattice's learned chain keeps its acceptance above the
+    fallback threshold and reproduces the plain chain's plaquette and |L|."""
+    import torch
+
+    from paper_1010_1486_gb300 import learn
+    from paper_1010_1486_gb300.analysis import tau_int
+
+    ns, nt = 32, 4
+    betas = [2.2, 2.4, 2.6]
+    lats = [su2.su2_create(ns, nt, b, 100 + i, su2.SU2_COLD) for i, b in enumerate(betas)]
+    try:
+        for h in lats:
+            su2.su2_heatbath_sweep(h, 300)
+        pairs = torch.cat([learn.collect(h, ns, nt, 100_000) for h in lats])
+        w, losses, s_lo, s_hi = learn.train(pairs, steps=1500, batch=8192, lr=3e-3, seed=4, tail_steps=1500,
+                                            tail_lr=3e-4)
+        assert losses[-100:].mean() < losses[:100].mean()
+        n = 1200
+        for b, h in zip(betas, lats):
+            su2.su2_set_proposal(h, w, s_lo, s_hi, 256)
+            pl, ll, st = su2.su2_learned_generate(h, n, 1, 0.7)
+            acc = sum(st["accepted"]) / (st["learned_sweeps"] * 4 * ns ** 3 * nt)
+            assert st["learned_sweeps"] == n and acc > 0.85, (b, acc, st["plain_sweeps"])
+            pp, lp, _ = su2.su2_generate(h, n, 1, 0)
+            for lr_, pr_ in ((pl, pp), (np.abs(ll), np.abs(lp))):
+                e = np.hypot(tau_int(lr_)[3], tau_int(pr_)[3])
+                assert abs(lr_.mean() - pr_.mean()) < 5 * e, (b, lr_.mean(), pr_.mean(), e)
+    finally:
+        for h in lats:
+            su2.su2_destroy(h)
