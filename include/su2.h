@@ -122,7 +122,12 @@ su2_status su2_heatbath_phase(su2_lattice *lat, int mu, int parity);
  * see every plaquette of the final links once, as (1/2) Tr U'S over the
  * staple terms S of the directions nu < mu); it equals su2_plaquette on the
  * same links up to binary32 rounding of the single plaquettes.  A sweep
- * reunitarized before its measurement uses the separate plaquette pass. */
+ * reunitarized before its measurement uses the separate plaquette pass.
+ * On a lattice created with a stream (not the legacy default stream) and
+ * with timing off, each sweep is replayed from a CUDA graph captured on first
+ * use (the sweep counter and the measurement slot are kept on the device;
+ * the graph is captured again when the sampler, beta, seed, over-relaxation
+ * or the measurement buffer change); the chain is the same bit for bit. */
 su2_status su2_generate(su2_lattice *lat, int nsweeps, int measure_every, int reunit_every, double *plaq,
                         double *poly, su2_stats *stats);
 

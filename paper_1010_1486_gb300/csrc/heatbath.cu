@@ -29,6 +29,7 @@ struct HbParams {
     int parity;
     float beta;
     uint32_t sweep;
+    const uint32_t *sweep_dev;  // if non-NULL the sweep counter is read here (graph replays)
     unsigned long long *trial_slots;
     unsigned int *flags;
     const unsigned int *gate;  // if non-NULL and *gate == 1 the phase is left to the learned kernel
@@ -71,6 +72,7 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
 {
     if (p.gate != nullptr && *(volatile const unsigned int *)p.gate == 1u) return;
     __shared__ CrQueues s_q[kCrWarps];
+    const uint32_t sweep = p.sweep_dev ? *p.sweep_dev : p.sweep;
     const int lane = threadIdx.x & 31;
     CrQueues &Q = s_q[threadIdx.x >> 5];
     const unsigned int lanes_below = (1u << lane) - 1u;
@@ -113,7 +115,7 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
         if (lane < n) {
             const int q = first + lane;
             const int eo = Q.d_eo[q];
-            const uint4 wd = philox_rk(make_uint4((uint32_t)eo, p.sweep, sw_dir, 0u), p.rk);
+            const uint4 wd = philox_rk(make_uint4((uint32_t)eo, sweep, sw_dir, 0u), p.rk);
             const float4 out = direction_update(Q.d_a0[q], Q.d_ut[q], wd);
             p.links[link_index(p.g, MU, p.parity, eo)] = out;
             if (MEAS) plaq += (double)qmul_re(out, Q.d_sp[q]);
@@ -147,7 +149,7 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
         bool ok = false, again = false;
         float a0 = 0.0f;
         if (have) {
-            const uint4 w = philox_rk(make_uint4((uint32_t)eo, p.sweep, sw_creutz, (uint32_t)blk), p.rk);
+            const uint4 w = philox_rk(make_uint4((uint32_t)eo, sweep, sw_creutz, (uint32_t)blk), p.rk);
             const bool haar = bk < kHaarBelow;
             const float ome = __fsub_rn(1.0f, e);
             float c1, c2;
@@ -193,7 +195,7 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
         // ---- part 0
         NuLinks nl = load_nu_eo<MU, OtherDir<MU, 0>::value>(p.links, p.g, xn, en, en_p, p.parity);
         const DrawSetup d = prepare_draw(v_cur, p.beta);
-        const uint4 w = philox_rk(make_uint4((uint32_t)cur, p.sweep, sw_creutz, 0u), p.rk);
+        const uint4 w = philox_rk(make_uint4((uint32_t)cur, sweep, sw_creutz, 0u), p.rk);
         float4 v_next = add_nu_terms(make_float4(0.0f, 0.0f, 0.0f, 0.0f), nl);
         float4 sp_next = v_next;
         // ---- part 1
@@ -273,6 +275,7 @@ su2_status launch_hb_phase(su2_lattice *lat, int mu, int parity, uint32_t sweep,
     p.parity = parity;
     p.beta = (float)lat->beta;
     p.sweep = sweep;
+    p.sweep_dev = lat->capturing ? lat->d_ctr : nullptr;
     p.trial_slots = lat->scratch.trials;
     p.flags = lat->scratch.flags;
     p.plaq = fused_slot(lat, mu, parity, 0);
@@ -387,6 +390,111 @@ static su2_status ensure_history(su2_lattice *lat, int n)
     return SU2_OK;
 }
 
+// One sweep of su2_generate: the heat bath (and the lattice's over-relaxation
+// sweeps), the reunitarization if due, and the measurement if due.  The
+// plaquette comes out of the sweep itself unless the links are reunitarized
+// before the measurement.  plaq_dst / poly_dst: the measurement slots (when
+// capturing, the bases: the kernels add the device slot index).
+static su2_status sweep_and_measure(su2_lattice *lat, bool measure, bool reunit, double *plaq_dst, double *poly_dst)
+{
+    su2_status st;
+    const bool fused = measure && !reunit;
+    if (fused && (st = fused_begin(lat)) != SU2_OK) return st;
+    if ((st = one_sweep(lat)) != SU2_OK) {
+        lat->fused_part = nullptr;
+        return st;
+    }
+    if (reunit && (st = launch_reunitarize(lat)) != SU2_OK) return st;
+    if (measure) {
+        st = fused ? fused_finish(lat, plaq_dst) : launch_plaquette(lat, plaq_dst);
+        if (st != SU2_OK) return st;
+        if ((st = launch_polyakov(lat, poly_dst)) != SU2_OK) return st;
+    }
+    return SU2_OK;
+}
+
+// Advances the device counters of graph replays: the sweep, and the
+// measurement slot after a measured sweep.
+__global__ void advance_kernel(uint32_t *ctr, int measured)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        ctr[0] += 1u;
+        if (measured) ctr[1] += 1u;
+    }
+}
+
+static uint64_t generation_signature(const su2_lattice *lat)
+{
+    uint64_t h = 1469598103934665603ull;  // FNV-1a over the settings a captured sweep depends on
+    auto mix = [&](uint64_t v) {
+        for (int i = 0; i < 8; ++i) {
+            h ^= (v >> (8 * i)) & 0xffu;
+            h *= 1099511628211ull;
+        }
+    };
+    const float beta = (float)lat->beta;
+    uint32_t bb;
+    memcpy(&bb, &beta, sizeof bb);
+    mix(bb);
+    mix(lat->seed);
+    mix((uint64_t)lat->sampler);
+    mix((uint64_t)lat->overrelax);
+    mix((uint64_t)(uintptr_t)lat->scratch.history);
+    mix((uint64_t)lat->scratch.history_cap);
+    return h | 1ull;  // never 0 (0 marks an empty slot)
+}
+
+// The captured sweep of this variant (captured on first use or after a
+// settings change); *exec = NULL if the stream refused the capture.
+static su2_status generation_graph(su2_lattice *lat, bool measure, bool reunit, cudaGraphExec_t *exec)
+{
+    GenGraph &gg = lat->gen_graph[(measure ? 1 : 0) | (reunit ? 2 : 0)];
+    const uint64_t sig = generation_signature(lat);
+    if (gg.exec && gg.sig == sig) {
+        *exec = gg.exec;
+        return SU2_OK;
+    }
+    if (gg.exec) {
+        cudaGraphExecDestroy(gg.exec);
+        gg.exec = nullptr;
+    }
+    *exec = nullptr;
+    if (cudaStreamBeginCapture(lat->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        lat->graphs_off = true;
+        return SU2_OK;
+    }
+    const uint32_t sweep0 = lat->sweep;
+    lat->capturing = true;
+    su2_status st = sweep_and_measure(lat, measure, reunit, lat->scratch.history,
+                                      lat->scratch.history + lat->scratch.history_cap);
+    if (st == SU2_OK) {
+        advance_kernel<<<1, 32, 0, lat->stream>>>(lat->d_ctr, measure ? 1 : 0);
+        if (cudaGetLastError() != cudaSuccess) st = SU2_E_CUDA;
+    }
+    lat->capturing = false;
+    lat->sweep = sweep0;  // the captured sweep advanced the host counter; the replay does it
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(lat->stream, &graph);
+    if (st != SU2_OK || e != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        lat->graphs_off = true;  // run this lattice eagerly from now on
+        return SU2_OK;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&gg.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        gg.exec = nullptr;
+        cudaGetLastError();
+        lat->graphs_off = true;
+        return SU2_OK;
+    }
+    gg.sig = sig;
+    *exec = gg.exec;
+    return SU2_OK;
+}
+
 }  // namespace su2
 
 using namespace su2;
@@ -404,25 +512,31 @@ su2_status su2_generate(su2_lattice *lat, int nsweeps, int measure_every, int re
     if ((st = launch_clear_counters(lat)) != SU2_OK) return st;
     lat->hb_log.used = 0;
     lat->or_log.used = 0;
+    // Graph replays need a stream that can be captured and no per-launch events.
+    bool graphs = lat->stream != nullptr && !lat->timing && !lat->graphs_off && nsweeps >= 1;
+    if (graphs) {
+        const uint32_t ctr[2] = {lat->sweep, 0u};
+        SU2_CUDA(cudaMemcpyAsync(lat->d_ctr, ctr, sizeof ctr, cudaMemcpyHostToDevice, lat->stream));
+    }
     int m = 0;
     for (int s = 1; s <= nsweeps; ++s) {
         const bool measure = measure_every > 0 && s % measure_every == 0;
         const bool reunit = reunit_every > 0 && s % reunit_every == 0;
-        // the plaquette comes out of the sweep itself unless the links are
-        // reunitarized before the measurement
-        const bool fused = measure && !reunit;
-        if (fused && (st = fused_begin(lat)) != SU2_OK) return st;
-        if ((st = one_sweep(lat)) != SU2_OK) {
-            lat->fused_part = nullptr;
+        if (graphs) {
+            cudaGraphExec_t exec = nullptr;
+            if ((st = generation_graph(lat, measure, reunit, &exec)) != SU2_OK) return st;
+            if (exec) {
+                SU2_CUDA(cudaGraphLaunch(exec, lat->stream));
+                lat->sweep += 1;
+                if (measure) ++m;
+                continue;
+            }
+            graphs = false;  // capture refused: run the rest eagerly
+        }
+        if ((st = sweep_and_measure(lat, measure, reunit, lat->scratch.history + m,
+                                    lat->scratch.history + lat->scratch.history_cap + m)) != SU2_OK)
             return st;
-        }
-        if (reunit && (st = launch_reunitarize(lat)) != SU2_OK) return st;
-        if (measure) {
-            st = fused ? fused_finish(lat, lat->scratch.history + m) : launch_plaquette(lat, lat->scratch.history + m);
-            if (st != SU2_OK) return st;
-            if ((st = launch_polyakov(lat, lat->scratch.history + lat->scratch.history_cap + m)) != SU2_OK) return st;
-            ++m;
-        }
+        if (measure) ++m;
     }
     if (nmeas > 0 && plaq)
         SU2_CUDA(cudaMemcpyAsync(plaq, lat->scratch.history, sizeof(double) * nmeas, cudaMemcpyDeviceToHost,

@@ -32,6 +32,7 @@ struct KpParams {
     int parity;
     float beta;
     uint32_t sweep;
+    const uint32_t *sweep_dev;  // if non-NULL the sweep counter is read here (graph replays)
     unsigned long long *trial_slots;
     unsigned int *flags;
     const unsigned int *gate;  // skip the phase while *gate == 1 (learned sweeps)
@@ -79,6 +80,7 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
     if (p.gate != nullptr && *(volatile const unsigned int *)p.gate == 1u) return;
     __shared__ float4 s_ut[kKpWarps][kRetryCap];
     __shared__ float4 s_sp[MEAS ? kKpWarps : 1][kRetryCap];
+    const uint32_t sweep = p.sweep_dev ? *p.sweep_dev : p.sweep;
     __shared__ float s_bk[kKpWarps][kRetryCap];
     __shared__ int s_eo[kKpWarps][kRetryCap];
     const int lane = threadIdx.x & 31;
@@ -103,11 +105,11 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
             float a0 = 0.0f;
             int t = 1;
             for (; t < kMaxTrials; ++t)
-                if (kp_trial(philox_rk(make_uint4((uint32_t)eo, p.sweep, sw_kp, (uint32_t)t), p.rk), two_bk, a0))
+                if (kp_trial(philox_rk(make_uint4((uint32_t)eo, sweep, sw_kp, (uint32_t)t), p.rk), two_bk, a0))
                     break;
             if (t < kMaxTrials) {
                 const float4 out =
-                    direction_update(a0, ut, philox_rk(make_uint4((uint32_t)eo, p.sweep, sw_dir, 0u), p.rk));
+                    direction_update(a0, ut, philox_rk(make_uint4((uint32_t)eo, sweep, sw_dir, 0u), p.rk));
                 p.links[link_index(p.g, MU, p.parity, eo)] = out;
                 if (MEAS) plaq += (double)qmul_re(out, s_sp[MEAS ? wib : 0][q]);
                 trials += (unsigned int)(t + 1);
@@ -148,8 +150,8 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
         const float inv_k = __fdiv_rn(1.0f, k);
         const float4 ut = make_float4(__fmul_rn(v_cur.x, inv_k), __fmul_rn(-v_cur.y, inv_k),
                                       __fmul_rn(-v_cur.z, inv_k), __fmul_rn(-v_cur.w, inv_k));
-        uint4 w = make_uint4((uint32_t)cur, p.sweep, sw_kp, 0u);
-        uint4 wd = make_uint4((uint32_t)cur, p.sweep, sw_dir, 0u);
+        uint4 w = make_uint4((uint32_t)cur, sweep, sw_kp, 0u);
+        uint4 wd = make_uint4((uint32_t)cur, sweep, sw_dir, 0u);
         philox2_rk(w, wd, p.rk);
         float4 v_next = add_nu_terms(make_float4(0.0f, 0.0f, 0.0f, 0.0f), nl);
         float4 sp_next = v_next;
@@ -161,7 +163,7 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
         const bool park = valid && use_kp && !first_ok;
         if (valid && !use_kp) {  // beta k < 2: Creutz's method
             float4 out;
-            const int n = heatbath_draw(v_cur, p.beta, p.rk, (uint32_t)cur, p.sweep, (uint32_t)p.parity, MU, out);
+            const int n = heatbath_draw(v_cur, p.beta, p.rk, (uint32_t)cur, sweep, (uint32_t)p.parity, MU, out);
             if (n > 0) {
                 p.links[link_index(p.g, MU, p.parity, cur)] = out;
                 if (MEAS) plaq += (double)qmul_re(out, sp_cur);
@@ -240,6 +242,7 @@ su2_status launch_kp_phase(su2_lattice *lat, int mu, int parity, uint32_t sweep,
     p.parity = parity;
     p.beta = (float)lat->beta;
     p.sweep = sweep;
+    p.sweep_dev = lat->capturing ? lat->d_ctr : nullptr;
     p.trial_slots = lat->scratch.trials;
     p.flags = lat->scratch.flags;
     p.gate = gate;

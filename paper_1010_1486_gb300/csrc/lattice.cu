@@ -329,7 +329,9 @@ su2_status su2_create(int ns, int nt, double beta, uint64_t seed, su2_start star
     const size_t result_bytes = align256(sizeof(double) * 4);
     const size_t trials_bytes = align256(sizeof(unsigned long long) * 8 * kTrialSlots);
     const size_t flags_bytes = align256(sizeof(unsigned int) * 4);
-    lat->block_bytes = links_bytes + partials_bytes + ticket_bytes + result_bytes + trials_bytes + flags_bytes;
+    const size_t ctr_bytes = align256(sizeof(uint32_t) * 2);
+    lat->block_bytes =
+        links_bytes + partials_bytes + ticket_bytes + result_bytes + trials_bytes + flags_bytes + ctr_bytes;
     lat->block = device_alloc(lat->block_bytes, dev, lat->stream);
     if (!lat->block) {
         delete lat;
@@ -349,9 +351,11 @@ su2_status su2_create(int ns, int nt, double beta, uint64_t seed, su2_start star
     lat->scratch.trials = (unsigned long long *)p;
     p += trials_bytes;
     lat->scratch.flags = (unsigned int *)p;
+    p += flags_bytes;
+    lat->d_ctr = (uint32_t *)p;
 
     st = SU2_OK;
-    if (cudaMemsetAsync(lat->scratch.ticket, 0, ticket_bytes + result_bytes + trials_bytes + flags_bytes,
+    if (cudaMemsetAsync(lat->scratch.ticket, 0, ticket_bytes + result_bytes + trials_bytes + flags_bytes + ctr_bytes,
                         lat->stream) != cudaSuccess)
         st = cuda_fail(cudaGetLastError(), "cudaMemsetAsync");
     if (st == SU2_OK) st = (start == SU2_HOT) ? launch_hot_start(lat) : launch_cold_start(lat);
@@ -379,6 +383,8 @@ su2_status su2_destroy(su2_lattice *lat)
     DeviceGuard guard(lat->device);
     for (cudaEvent_t e : lat->hb_log.events) cudaEventDestroy(e);
     for (cudaEvent_t e : lat->or_log.events) cudaEventDestroy(e);
+    for (GenGraph &gg : lat->gen_graph)
+        if (gg.exec) cudaGraphExecDestroy(gg.exec);
     device_free(lat->staging, lat->staging_bytes, lat->device, lat->stream);
     device_free(lat->learned_block, lat->learned_bytes, lat->device, lat->stream);
     device_free(lat->scratch.history, sizeof(double) * 2 * (size_t)lat->scratch.history_cap, lat->device,

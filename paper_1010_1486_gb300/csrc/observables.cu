@@ -14,10 +14,12 @@
 
 namespace su2 {
 
+// dst (+ *idx when idx is given: the measurement slot of a graph replay)
 __global__ void __launch_bounds__(kReduceThreads, 4) plaquette_kernel(const float4 *__restrict__ L, Geom g,
                                                                    double *__restrict__ partials,
                                                                    unsigned int *__restrict__ ticket,
-                                                                   double *__restrict__ dst)
+                                                                   double *__restrict__ dst,
+                                                                   const uint32_t *__restrict__ idx)
 {
     double acc = 0.0;
     const int64_t vol = 2 * (int64_t)g.vh;
@@ -30,14 +32,15 @@ __global__ void __launch_bounds__(kReduceThreads, 4) plaquette_kernel(const floa
         acc += (double)site_plaquette(L, g, x, eo, parity);
     }
     const double total = block_sum(acc);
-    finish_reduction(total, partials, ticket, dst, 1.0 / (6.0 * (double)vol));
+    finish_reduction(total, partials, ticket, idx ? dst + *idx : dst, 1.0 / (6.0 * (double)vol));
 }
 
 // (1/2) Tr of U_3(x,0) U_3(x,1) ... U_3(x,Nt-1), multiplied left to right.
 __global__ void __launch_bounds__(kReduceThreads) polyakov_kernel(const float4 *__restrict__ L, Geom g,
                                                                   double *__restrict__ partials,
                                                                   unsigned int *__restrict__ ticket,
-                                                                  double *__restrict__ dst)
+                                                                  double *__restrict__ dst,
+                                                                  const uint32_t *__restrict__ idx)
 {
     double acc = 0.0;
     for (int xs = blockIdx.x * blockDim.x + threadIdx.x; xs < g.vs; xs += gridDim.x * blockDim.x) {
@@ -55,7 +58,7 @@ __global__ void __launch_bounds__(kReduceThreads) polyakov_kernel(const float4 *
         acc += (double)p.x;
     }
     const double total = block_sum(acc);
-    finish_reduction(total, partials, ticket, dst, 1.0 / (double)g.vs);
+    finish_reduction(total, partials, ticket, idx ? dst + *idx : dst, 1.0 / (double)g.vs);
 }
 
 su2_status launch_plaquette(su2_lattice *lat, double *dst)
@@ -67,19 +70,21 @@ su2_status launch_plaquette(su2_lattice *lat, double *dst)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, lat->device);
     const int grid = grid_for(lat->vol, kReduceThreads, std::min(lat->scratch.partials_cap, 4 * sms));
     plaquette_kernel<<<grid, kReduceThreads, 0, lat->stream>>>(lat->links, g, lat->scratch.partials,
-                                                               lat->scratch.ticket, dst);
+                                                               lat->scratch.ticket, dst,
+                                                               lat->capturing ? lat->d_ctr + 1 : nullptr);
     SU2_CUDA(cudaGetLastError());
     return SU2_OK;
 }
 
 // Ordered sum of the fused-plaquette slot region (one block).
 __global__ void __launch_bounds__(kReduceThreads) fused_plaquette_kernel(const double *__restrict__ part, int n,
-                                                                        double scale, double *__restrict__ dst)
+                                                                        double scale, double *__restrict__ dst,
+                                                                        const uint32_t *__restrict__ idx)
 {
     double v = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) v += part[i];
     v = block_sum(v);
-    if (threadIdx.x == 0) *dst = v * scale;
+    if (threadIdx.x == 0) *(idx ? dst + *idx : dst) = v * scale;
 }
 
 su2_status fused_begin(su2_lattice *lat)
@@ -97,7 +102,8 @@ su2_status fused_finish(su2_lattice *lat, double *dst)
 {
     lat->fused_part = nullptr;
     fused_plaquette_kernel<<<1, kReduceThreads, 0, lat->stream>>>(lat->scratch.partials, kFusedRegion,
-                                                                 1.0 / (6.0 * (double)lat->vol), dst);
+                                                                 1.0 / (6.0 * (double)lat->vol), dst,
+                                                                 lat->capturing ? lat->d_ctr + 1 : nullptr);
     SU2_CUDA(cudaGetLastError());
     return SU2_OK;
 }
@@ -107,7 +113,8 @@ su2_status launch_polyakov(su2_lattice *lat, double *dst)
     const Geom g = geom_of(lat);
     const int grid = grid_for(g.vs, kReduceThreads, 152 * 8);
     polyakov_kernel<<<grid, kReduceThreads, 0, lat->stream>>>(lat->links, g, lat->scratch.partials,
-                                                              lat->scratch.ticket + 1, dst);
+                                                              lat->scratch.ticket + 1, dst,
+                                                              lat->capturing ? lat->d_ctr + 1 : nullptr);
     SU2_CUDA(cudaGetLastError());
     return SU2_OK;
 }

@@ -43,6 +43,13 @@ struct EventLog {
     std::vector<cudaEvent_t> events;
     size_t used = 0;
 };
+
+// One sweep of su2_generate captured as a CUDA graph; `sig` identifies the
+// settings it was captured with (sampler, beta, seed, over-relaxation, buffers).
+struct GenGraph {
+    cudaGraphExec_t exec = nullptr;
+    uint64_t sig = 0;
+};
 }  // namespace su2
 
 struct su2_lattice {
@@ -66,6 +73,10 @@ struct su2_lattice {
 
     int overrelax = 0;  // over-relaxation sweeps after each heat-bath sweep
     double *fused_part = nullptr;  // slot region of the plaquette measured in the current sweep, or NULL
+    bool capturing = false;        // launches are being captured into a generation graph
+    bool graphs_off = false;       // a capture failed once: generate eagerly
+    uint32_t *d_ctr = nullptr;     // device: [0] sweep counter, [1] measurement slot (graph replays)
+    su2::GenGraph gen_graph[4];    // captured sweeps, variant = (measured) | (reunitarized) << 1
 
     bool timing = false;
     su2::EventLog hb_log;  // heat-bath (and learned) phase launches
