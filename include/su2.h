@@ -210,8 +210,12 @@ su2_status su2_set_timing(su2_lattice *lat, int enable);
 /* Self-tests of device building blocks (they launch kernels):
  * su2_selftest_philox: n rows of host input ck[6 n] = (key0, key1, c0, c1, c2,
  *   c3) -> out[4 n] Philox4x32-10 words.
- * su2_selftest_math: which = 0 log, 1 exp, 2 sin/cos of 2 pi x; n inputs
- *   x[n] -> y[n] (and y2[n] = cos for which = 2; else y2 may be NULL). */
+ * su2_selftest_math: which = 0 log, 1 exp, 2 sin/cos of 2 pi x, 3 the
+ *   hardware base-2 logarithm that screens Creutz trials; n inputs x[n] ->
+ *   y[n] (and y2[n] = cos for which = 2).  which = 4: x holds n quadruples
+ *   (r1, r2, 1/(beta k), exp(-2 beta k)); y[i] = the screen's verdict (0
+ *   reject, 1 accept, 2 undecided), y2[i] = the exact test's (0 or 1).  y2
+ *   may be NULL unless which is 2 or 4. */
 su2_status su2_selftest_philox(const uint32_t *ck, uint32_t *out, size_t n);
 su2_status su2_selftest_math(int which, const float *x, float *y, float *y2, size_t n);
 

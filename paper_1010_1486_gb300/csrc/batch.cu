@@ -126,8 +126,9 @@ __device__ __forceinline__ int find_owner(const int *__restrict__ prefix, int n,
 // even/odd sites of one lattice, one warp per chunk, as in the single-lattice
 // kernel: the staple of the next round of 32 sites is loaded one nu-group per
 // stage while the current round is drawn; the first Philox block (trials 0,
-// 1) inline, links with both rejected retried 32 at a time from the warp's
-// retry queue, accepted links given their direction and store 32 at a time;
+// 1, screened) inline, links with both rejected retried 32 at a time from the
+// warp's retry queue, accepted links given their a0, direction and store 32
+// at a time;
 // both queues are emptied at the end of the chunk.
 template <int MU, int R>
 __device__ void batch_phase(const BatchParams &bp, int parity, uint32_t sweep, CrQueues &Q, LatDesc &sd,
@@ -161,22 +162,22 @@ __device__ void batch_phase(const BatchParams &bp, int parity, uint32_t sweep, C
         const int rounds = (last - base0 + 32) >> 5;
         int retry_n = 0, done_n = 0;
 
-        auto push_done = [&](bool ok, float4 ut, float a0, int eo) {
+        auto push_done = [&](bool ok, float4 ut, float val, float ibk, int eo) {
             const unsigned int m = __ballot_sync(0xffffffffu, ok);
             if (ok) {
                 const int q = done_n + __popc(m & lanes_below);
                 Q.d_ut[q] = ut;
-                Q.d_a0[q] = a0;
+                Q.d_val[q] = val;
+                Q.d_ibk[q] = ibk;
                 Q.d_eo[q] = eo;
             }
             done_n += __popc(m);
         };
-        auto push_retry = [&](bool again, float4 ut, float bk, float ibk, float e, int eo, int blk) {
+        auto push_retry = [&](bool again, float4 ut, float ibk, float e, int eo, int blk) {
             const unsigned int m = __ballot_sync(0xffffffffu, again);
             if (again) {
                 const int q = retry_n + __popc(m & lanes_below);
                 Q.r_ut[q] = ut;
-                Q.r_bk[q] = bk;
                 Q.r_ibk[q] = ibk;
                 Q.r_e[q] = e;
                 Q.r_eo[q] = eo;
@@ -190,7 +191,8 @@ __device__ void batch_phase(const BatchParams &bp, int parity, uint32_t sweep, C
                 const int q = first + lane;
                 const int eo = Q.d_eo[q];
                 const uint4 wd = philox_key(make_uint4((uint32_t)eo, sweep, sw_dir, 0u), k0, k1);
-                links[link_index(g, MU, parity, eo)] = direction_update(Q.d_a0[q], Q.d_ut[q], wd);
+                links[link_index(g, MU, parity, eo)] =
+                    direction_update(deferred_a0(Q.d_val[q], Q.d_ibk[q]), Q.d_ut[q], wd);
             }
             __syncwarp();
         };
@@ -204,40 +206,34 @@ __device__ void batch_phase(const BatchParams &bp, int parity, uint32_t sweep, C
             __syncwarp();
             const bool have = lane < n;
             float4 ut = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
-            float bk = 0.0f, ibk = 0.0f, e = 0.0f;
+            float ibk = 1.0f, e = 0.0f;
             int eo = 0, blk = 0;
             if (have) {
                 const int q = first + lane;
                 ut = Q.r_ut[q];
-                bk = Q.r_bk[q];
                 ibk = Q.r_ibk[q];
                 e = Q.r_e[q];
                 eo = Q.r_eo[q];
                 blk = Q.r_blk[q];
             }
             __syncwarp();
-            bool ok = false, again = false;
-            float a0 = 0.0f;
-            if (have) {
-                const uint4 w = philox_key(make_uint4((uint32_t)eo, sweep, sw_creutz, (uint32_t)blk), k0, k1);
-                const bool haar = bk < kHaarBelow;
-                const float ome = __fsub_rn(1.0f, e);
-                float c1, c2;
-                const bool ok1 = creutz_trial(uniform01(w.x), uniform01(w.y), ibk, e, ome, haar, c1);
-                const bool ok2 = creutz_trial(uniform01(w.z), uniform01(w.w), ibk, e, ome, haar, c2);
-                ok = ok1 || ok2;
-                a0 = ok1 ? c1 : c2;
-                if (ok) {
-                    my_trials += (unsigned int)(2 * blk + (ok1 ? 1 : 2));
-                } else if (blk + 1 < kMaxTrials / 2) {
+            const uint4 w = philox_key(make_uint4((uint32_t)eo, sweep, sw_creutz, (uint32_t)blk), k0, k1);
+            bool first_ok;
+            float val;
+            const bool ok = creutz_pair(w, ibk, e, have, first_ok, val) && have;
+            bool again = false;
+            if (ok) {
+                my_trials += (unsigned int)(2 * blk + (first_ok ? 1 : 2));
+            } else if (have) {
+                if (blk + 1 < kMaxTrials / 2) {
                     again = true;
                 } else {
                     atomicAdd(&bp.flags[0], 1u);  // trial cap: the link keeps its old value
                     my_trials += (unsigned int)kMaxTrials;
                 }
             }
-            push_retry(again, ut, bk, ibk, e, eo, blk + 1);
-            push_done(ok, ut, a0, eo);
+            push_retry(again, ut, ibk, e, eo, blk + 1);
+            push_done(ok, ut, val, ibk, eo);
             flush_done();
         };
 
@@ -266,15 +262,13 @@ __device__ void batch_phase(const BatchParams &bp, int parity, uint32_t sweep, C
             // ---- part 1
             nl = load_nu_eo<MU, OtherDir<MU, 1>::value>(links, g, xn, en, en_p, parity);
             {
-                const bool haar = ds.bk < kHaarBelow;
-                const float ome = __fsub_rn(1.0f, ds.e);
-                float c1, c2;
-                const bool ok1 = creutz_trial(uniform01(w.x), uniform01(w.y), ds.ibk, ds.e, ome, haar, c1);
-                const bool ok2 = creutz_trial(uniform01(w.z), uniform01(w.w), ds.ibk, ds.e, ome, haar, c2);
-                const bool ok = valid && (ok1 || ok2);
-                my_trials += ok ? (ok1 ? 1u : 2u) : 0u;
-                push_done(ok, ds.ut, ok1 ? c1 : c2, cur);
-                push_retry(valid && !ok1 && !ok2, ds.ut, ds.bk, ds.ibk, ds.e, cur, 1);
+                bool first_ok;
+                float val;
+                const bool acc = creutz_pair(w, ds.ibk, ds.e, valid, first_ok, val);
+                const bool ok = valid && acc;
+                my_trials += ok ? (first_ok ? 1u : 2u) : 0u;
+                push_done(ok, ds.ut, val, ds.ibk, cur);
+                push_retry(valid && !acc, ds.ut, ds.ibk, ds.e, cur, 1);
             }
             v_next = add_nu_terms(v_next, nl);
             // ---- part 2

@@ -50,9 +50,11 @@ constexpr int kCrMinBlocks = SU2_HB_MIN_BLOCKS;  // blocks per SM the register b
 // loads of one nu-group of the next round, does one third of the current
 // round's work, then folds the loaded group into the next round's staple:
 //   part 0  k, U~^dag, beta k, exp(-2 beta k); Philox block 0 (trials 0, 1);
-//   part 1  trials 0 and 1; an accepted link goes to the warp's direction
-//           queue, a link with both rejected to its retry queue;
-//   part 2  every 32 links in the direction queue: directions and stores.
+//   part 1  trials 0 and 1, screened (creutz_pair); an accepted link goes to
+//           the warp's direction queue, a link with both rejected to its
+//           retry queue;
+//   part 2  every 32 links in the direction queue: a0 (the one exact log of
+//           the link), directions and stores.
 // Whenever 32 links wait for a retry, the whole warp draws their next Philox
 // block (two more trials each); accepted links move to the direction queue,
 // the others go back to the retry queue.  At beta k ~ 30 two trials accept
@@ -84,23 +86,23 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
     double plaq = 0.0;
     int retry_n = 0, done_n = 0;  // warp-uniform queue lengths
 
-    auto push_done = [&](bool ok, float4 ut, float a0, int eo, float4 sp) {
+    auto push_done = [&](bool ok, float4 ut, float val, float ibk, int eo, float4 sp) {
         const unsigned int m = __ballot_sync(0xffffffffu, ok);
         if (ok) {
             const int q = done_n + __popc(m & lanes_below);
             Q.d_ut[q] = ut;
-            Q.d_a0[q] = a0;
+            Q.d_val[q] = val;
+            Q.d_ibk[q] = ibk;
             Q.d_eo[q] = eo;
             if (MEAS) Q.d_sp[q] = sp;
         }
         done_n += __popc(m);
     };
-    auto push_retry = [&](bool again, float4 ut, float bk, float ibk, float e, int eo, int blk, float4 sp) {
+    auto push_retry = [&](bool again, float4 ut, float ibk, float e, int eo, int blk, float4 sp) {
         const unsigned int m = __ballot_sync(0xffffffffu, again);
         if (again) {
             const int q = retry_n + __popc(m & lanes_below);
             Q.r_ut[q] = ut;
-            Q.r_bk[q] = bk;
             Q.r_ibk[q] = ibk;
             Q.r_e[q] = e;
             Q.r_eo[q] = eo;
@@ -116,7 +118,7 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
             const int q = first + lane;
             const int eo = Q.d_eo[q];
             const uint4 wd = philox_rk(make_uint4((uint32_t)eo, sweep, sw_dir, 0u), p.rk);
-            const float4 out = direction_update(Q.d_a0[q], Q.d_ut[q], wd);
+            const float4 out = direction_update(deferred_a0(Q.d_val[q], Q.d_ibk[q]), Q.d_ut[q], wd);
             p.links[link_index(p.g, MU, p.parity, eo)] = out;
             if (MEAS) plaq += (double)qmul_re(out, Q.d_sp[q]);
         }
@@ -133,12 +135,11 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
         __syncwarp();
         const bool have = lane < n;
         float4 ut = make_float4(1.0f, 0.0f, 0.0f, 0.0f), sp = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        float bk = 0.0f, ibk = 0.0f, e = 0.0f;
+        float ibk = 1.0f, e = 0.0f;
         int eo = 0, blk = 0;
         if (have) {
             const int q = first + lane;
             ut = Q.r_ut[q];
-            bk = Q.r_bk[q];
             ibk = Q.r_ibk[q];
             e = Q.r_e[q];
             eo = Q.r_eo[q];
@@ -146,28 +147,23 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
             if (MEAS) sp = Q.r_sp[q];
         }
         __syncwarp();
-        bool ok = false, again = false;
-        float a0 = 0.0f;
-        if (have) {
-            const uint4 w = philox_rk(make_uint4((uint32_t)eo, sweep, sw_creutz, (uint32_t)blk), p.rk);
-            const bool haar = bk < kHaarBelow;
-            const float ome = __fsub_rn(1.0f, e);
-            float c1, c2;
-            const bool ok1 = creutz_trial(uniform01(w.x), uniform01(w.y), ibk, e, ome, haar, c1);
-            const bool ok2 = creutz_trial(uniform01(w.z), uniform01(w.w), ibk, e, ome, haar, c2);
-            ok = ok1 || ok2;
-            a0 = ok1 ? c1 : c2;
-            if (ok) {
-                trials += (unsigned int)(2 * blk + (ok1 ? 1 : 2));
-            } else if (blk + 1 < kMaxTrials / 2) {
+        const uint4 w = philox_rk(make_uint4((uint32_t)eo, sweep, sw_creutz, (uint32_t)blk), p.rk);
+        bool first_ok;
+        float val;
+        const bool ok = creutz_pair(w, ibk, e, have, first_ok, val) && have;
+        bool again = false;
+        if (ok) {
+            trials += (unsigned int)(2 * blk + (first_ok ? 1 : 2));
+        } else if (have) {
+            if (blk + 1 < kMaxTrials / 2) {
                 again = true;
             } else {
                 atomicAdd(&p.flags[0], 1u);  // trial cap: the link keeps its old value
                 trials += (unsigned int)kMaxTrials;
             }
         }
-        push_retry(again, ut, bk, ibk, e, eo, blk + 1, sp);
-        push_done(ok, ut, a0, eo, sp);
+        push_retry(again, ut, ibk, e, eo, blk + 1, sp);
+        push_done(ok, ut, val, ibk, eo, sp);
         flush_done();
     };
 
@@ -201,15 +197,13 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
         // ---- part 1
         nl = load_nu_eo<MU, OtherDir<MU, 1>::value>(p.links, p.g, xn, en, en_p, p.parity);
         {
-            const bool haar = d.bk < kHaarBelow;
-            const float ome = __fsub_rn(1.0f, d.e);
-            float c1, c2;
-            const bool ok1 = creutz_trial(uniform01(w.x), uniform01(w.y), d.ibk, d.e, ome, haar, c1);
-            const bool ok2 = creutz_trial(uniform01(w.z), uniform01(w.w), d.ibk, d.e, ome, haar, c2);
-            const bool ok = valid && (ok1 || ok2);
-            trials += ok ? (ok1 ? 1u : 2u) : 0u;
-            push_done(ok, d.ut, ok1 ? c1 : c2, cur, sp_cur);
-            push_retry(valid && !ok1 && !ok2, d.ut, d.bk, d.ibk, d.e, cur, 1, sp_cur);
+            bool first_ok;
+            float val;
+            const bool acc = creutz_pair(w, d.ibk, d.e, valid, first_ok, val);
+            const bool ok = valid && acc;
+            trials += ok ? (first_ok ? 1u : 2u) : 0u;
+            push_done(ok, d.ut, val, d.ibk, cur, sp_cur);
+            push_retry(valid && !acc, d.ut, d.ibk, d.e, cur, 1, sp_cur);
         }
         v_next = add_nu_terms(v_next, nl);
         if (MU == 2) sp_next = v_next;

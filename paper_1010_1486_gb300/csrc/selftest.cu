@@ -27,6 +27,16 @@ __global__ void math_selftest_kernel(int which, const float *__restrict__ x, flo
             y[i] = log_series(x[i]);
         } else if (which == 1) {
             y[i] = exp_series(x[i]);
+        } else if (which == 3) {
+            y[i] = __log2f(x[i]);
+        } else if (which == 4) {
+            // quadruple (r1, r2, 1/(beta k), exp(-2 beta k)): the screen's
+            // verdict and the exact test's
+            const float r1 = x[4 * i], r2 = x[4 * i + 1], ibk = x[4 * i + 2], e = x[4 * i + 3];
+            const float ome = __fsub_rn(1.0f, e);
+            y[i] = (float)creutz_screen(__fmaf_rn(r1, ome, e), r2, make_screen(ibk));
+            float c;
+            y2[i] = creutz_trial(r1, r2, ibk, e, ome, ibk == 0.0f, c) ? 1.0f : 0.0f;
         } else {
             float s, c;
             sincos_2pi(x[i], s, c);
@@ -86,9 +96,10 @@ su2_status su2_selftest_philox(const uint32_t *ck, uint32_t *out, size_t n)
 
 su2_status su2_selftest_math(int which, const float *x, float *y, float *y2, size_t n)
 {
-    if (!x || !y || which < 0 || which > 2 || (which == 2 && !y2)) return SU2_E_INVAL;
+    const bool two = which == 2 || which == 4;
+    if (!x || !y || which < 0 || which > 4 || (two && !y2)) return SU2_E_INVAL;
     if (n == 0) return SU2_OK;
-    return run_with_buffers(x, 4 * n, y, 4 * n, which == 2 ? y2 : nullptr, which == 2 ? 4 * n : 0,
+    return run_with_buffers(x, (which == 4 ? 16 : 4) * n, y, 4 * n, two ? y2 : nullptr, two ? 4 * n : 0,
                             [which, n](char *in, char *o, char *o2, cudaStream_t s) {
                                 math_selftest_kernel<<<grid_for((int64_t)n, 256), 256, 0, s>>>(
                                     which, (const float *)in, (float *)o, (float *)o2, n);

@@ -263,6 +263,97 @@ __device__ __forceinline__ bool creutz_trial(float r1, float r2, float ibk, floa
     return __fmul_rn(r2, r2) <= __fmaf_rn(-c, c, 1.0f);
 }
 
+// ------------------------------------------- screened Creutz trials
+// The exact test above accepts iff A <= R, with A = r2^2, R = 1 - c^2,
+// c = clamp(1 + L ibk, -1, 1), L = log_series(x).  With t = -L ibk, R lies
+// within 2.4e-7 + 1.3e-7 t of g(t) = max(t (2 - t), 0): c = 1 - t up to two
+// roundings of numbers bounded by 2, g is 2-Lipschitz, and c clamps to -1
+// exactly where 1 - t < -1, i.e. where g vanishes.  The screen estimates
+// t~ = -lg2(x) ln2 ibk with the hardware base-2 logarithm (__log2f: absolute
+// error <= 2^-22 for x in [1/2, 1], relative <= 2.4e-7 below), and log_series
+// has |L - ln x| <= 1e-6 |ln x| + 1e-7; both bounds hold for every float x in
+// [2^-25, 1], the range x = e + r1 (1 - e) takes.  So
+// |t - t~| <= 2.7e-7 ibk + 1.4e-6 t~ and |R - g(t~)| <= 3e-7 + 5.4e-7 ibk +
+// 3e-6 t~, and with the slack 2e-6 + 4e-6 ibk + 2e-5 t~ (more than six times
+// that) a trial with A > g(t~) + slack is rejected and one with
+// A < g(t~) - slack accepted by the exact test as well.  Only the trials in
+// between (about one in 10^5 at beta k ~ 30) need the exact test, and an
+// accepted trial needs its exact a0 only once, when the link gets its
+// direction.  On the Haar branch (ibk = 0) the slack is infinite: every trial
+// goes to the exact test.
+enum : int { kScreenReject = 0, kScreenAccept = 1, kScreenUndecided = 2 };
+
+struct CreutzScreen {
+    float ln2_ibk;  // ln 2 / (beta k)
+    float slack0;   // 2e-6 + 4e-6 ibk (infinite on the Haar branch)
+};
+
+__device__ __forceinline__ CreutzScreen make_screen(float ibk)
+{
+    CreutzScreen s;
+    s.ln2_ibk = __fmul_rn(0.693147182f, ibk);
+    s.slack0 = ibk == 0.0f ? __int_as_float(0x7f800000) : __fmaf_rn(4e-6f, ibk, 2e-6f);
+    return s;
+}
+
+__device__ __forceinline__ int creutz_screen(float x, float r2, const CreutzScreen &s)
+{
+    const float tt = __fmul_rn(-__log2f(x), s.ln2_ibk);
+    const float g = fmaxf(__fmaf_rn(-tt, tt, __fadd_rn(tt, tt)), 0.0f);
+    const float slack = __fmaf_rn(2e-5f, tt, s.slack0);
+    const float a = __fmul_rn(r2, r2);
+    if (a > __fadd_rn(g, slack)) return kScreenReject;
+    if (a < __fsub_rn(g, slack)) return kScreenAccept;
+    return kScreenUndecided;
+}
+
+// The a0 of an accepted Creutz-branch trial from its x: the candidate that
+// creutz_trial forms, operation for operation.
+__device__ __forceinline__ float creutz_a0(float x, float ibk)
+{
+    const float c = __fadd_rn(1.0f, __fmul_rn(log_series(x), ibk));
+    return c < -1.0f ? -1.0f : (c > 1.0f ? 1.0f : c);
+}
+
+// The value a link waiting for its direction carries: x of the accepted trial
+// (ibk > 0), or a0 itself on the Haar branch (ibk = 0).
+__device__ __forceinline__ float deferred_a0(float val, float ibk)
+{
+    const float a = creutz_a0(val, ibk);
+    return ibk == 0.0f ? val : a;
+}
+
+// Both trials of one Creutz Philox block w (words 0, 1 then 2, 3), with the
+// verdicts of creutz_trial.  Returns whether either accepts; `first` whether
+// the first did, `val` what deferred_a0 turns into the accepted a0.  Every
+// lane of the warp calls it together; lanes with live = false only keep the
+// warp converged (their undecided trials do not force the exact branch).
+__device__ __forceinline__ bool creutz_pair(uint4 w, float ibk, float e, bool live, bool &first, float &val)
+{
+    const CreutzScreen s = make_screen(ibk);
+    const float ome = __fsub_rn(1.0f, e);
+    const float r1a = uniform01(w.x), r2a = uniform01(w.y);
+    const float r1b = uniform01(w.z), r2b = uniform01(w.w);
+    float va = __fmaf_rn(r1a, ome, e), vb = __fmaf_rn(r1b, ome, e);
+    int sa = creutz_screen(va, r2a, s);
+    int sb = creutz_screen(vb, r2b, s);
+    if (__any_sync(0xffffffffu, live && (sa == kScreenUndecided || sb == kScreenUndecided))) {
+        const bool haar = ibk == 0.0f;
+        float c;
+        if (sa == kScreenUndecided) {
+            sa = creutz_trial(r1a, r2a, ibk, e, ome, haar, c) ? kScreenAccept : kScreenReject;
+            if (haar) va = c;
+        }
+        if (sb == kScreenUndecided) {
+            sb = creutz_trial(r1b, r2b, ibk, e, ome, haar, c) ? kScreenAccept : kScreenReject;
+            if (haar) vb = c;
+        }
+    }
+    first = sa == kScreenAccept;
+    val = first ? va : vb;
+    return first || sb == kScreenAccept;
+}
+
 // Vector part uniform on the sphere of radius sqrt(1 - a0^2): c = 2 u0 - 1,
 // phi = 2 pi u1 (direction block 0); returns U' = a U~^dag.
 __device__ __forceinline__ float4 direction_from_uniforms(float a0, float4 ut, float uc, float uphi)

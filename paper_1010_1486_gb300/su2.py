@@ -323,12 +323,17 @@ def su2_selftest_philox(ck: np.ndarray) -> np.ndarray:
 
 
 def su2_selftest_math(which: int, x: np.ndarray):
+    """which = 4 takes x of shape (n, 4): rows (r1, r2, 1/(beta k), exp(-2 beta k))."""
     x = np.ascontiguousarray(x, dtype=np.float32)
-    y = np.empty_like(x)
-    y2 = np.empty_like(x) if which == 2 else None
+    n = x.shape[0] if which == 4 else x.size
+    y = np.empty(n, dtype=np.float32)
+    y2 = np.empty(n, dtype=np.float32) if which in (2, 4) else None
     _check(_lib.su2_selftest_math(which, _host_ptr(x), _host_ptr(y), _host_ptr(y2) if y2 is not None else None,
-                                  x.size), "su2_selftest_math")
-    return (y, y2) if which == 2 else y
+                                  n), "su2_selftest_math")
+    if which != 4:
+        y = y.reshape(x.shape)
+        y2 = y2.reshape(x.shape) if y2 is not None else None
+    return (y, y2) if y2 is not None else y
 
 
 def su2_plaquette_noalloc(links_ptr: int, ns: int, nt: int, out_ptr: int, stream=None) -> None:
