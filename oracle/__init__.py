@@ -59,6 +59,7 @@ def _load():
         sig = {
             "orc_philox4x32_10": (None, [P, P, P]),
             "orc_u01": (f32, [u32]),
+            "orc_u01_log": (f32, [u32]),
             "orc_logf": (f32, [f32]),
             "orc_expf": (f32, [f32]),
             "orc_logf_v": (None, [P, P, i64]),
@@ -141,6 +142,12 @@ def philox4x32_10(ctr, key) -> np.ndarray:
 
 def u01(x: int) -> float:
     return _load().orc_u01(x)
+
+
+def u01_log(x: int) -> float:
+    """The uniform in [2^-33, 1] that feeds a logarithm (Creutz's x, the
+    Kennedy-Pendleton exponentials)."""
+    return _load().orc_u01_log(x)
 
 
 def logf(x) -> np.ndarray:

@@ -68,23 +68,42 @@ void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint3
 }
 
 /* The top 24 bits of a 32-bit word, shifted into (0, 1]: ((x>>8)+1) 2^-24.
- * Exact in binary32; never 0, so log() below is always finite. */
+ * Exact in binary32; never 0. */
 float orc_u01(uint32_t x)
 {
     return (float)((x >> 8) + 1u) * (1.0f / 16777216.0f);
+}
+
+/* The uniform that feeds a logarithm: x 2^-32 + 2^-33 from the whole word,
+ * (float)x rounded to nearest, then one fused multiply-add, so the value is
+ * in [2^-33, 1] and exact ((2x + 1) 2^-33) for x < 2^23.  Creutz's method
+ * takes x uniform on [exp(-2 beta k), 1] (Sec. 2): with the 24-bit uniform
+ * above, -ln x would stop at 24 ln 2 = 16.6, cutting away the law's tail
+ * beta k (1 - a0) > 16.6 (2.8e-7 of its mass at large beta k, enough to lift
+ * the plaquette at beta = 6 by about 4e-7); from the whole word the cut is at
+ * 33 ln 2 = 22.9 (mass 6e-10). */
+float orc_u01_log(uint32_t x)
+{
+    return fmaf((float)x, 0x1p-32f, 0x1p-33f);
 }
 
 /* Counter layout: c0 = even/odd site index, c1 = sweep, c2 = (stream kind << 3)
  * | (parity << 2) | mu, c3 = block number within the stream.  Key = seed. */
 enum { ORC_KIND_CREUTZ = 0, ORC_KIND_DIRECTION = 1, ORC_KIND_HOTSTART = 2, ORC_KIND_LEARNED = 3 };
 
-static void draw_block(uint64_t seed, uint32_t eo, uint32_t sweep, int kind, int parity, int mu,
-                       uint32_t block, float u[4])
+static void draw_words(uint64_t seed, uint32_t eo, uint32_t sweep, int kind, int parity, int mu,
+                       uint32_t block, uint32_t w[4])
 {
     uint32_t ctr[4] = {eo, sweep, ((uint32_t)kind << 3) | ((uint32_t)parity << 2) | (uint32_t)mu, block};
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
-    uint32_t w[4];
     orc_philox4x32_10(ctr, key, w);
+}
+
+static void draw_block(uint64_t seed, uint32_t eo, uint32_t sweep, int kind, int parity, int mu,
+                       uint32_t block, float u[4])
+{
+    uint32_t w[4];
+    draw_words(seed, eo, sweep, kind, parity, mu, block, w);
     for (int i = 0; i < 4; ++i) u[i] = orc_u01(w[i]);
 }
 
@@ -383,11 +402,11 @@ int orc_heatbath_link(float beta, const float v[4], uint64_t seed, uint32_t eo, 
     float a0 = 0.0f;
     int trials = 0;
     int accepted = 0;
-    float u[4];
+    uint32_t w[4];
     for (int t = 0; t < ORC_MAX_TRIALS; ++t) {
-        if ((t & 1) == 0) draw_block(seed, eo, sweep, ORC_KIND_CREUTZ, parity, mu, (uint32_t)(t >> 1), u);
-        float r1 = u[2 * (t & 1)];
-        float r2 = u[2 * (t & 1) + 1];
+        if ((t & 1) == 0) draw_words(seed, eo, sweep, ORC_KIND_CREUTZ, parity, mu, (uint32_t)(t >> 1), w);
+        float r1 = orc_u01_log(w[2 * (t & 1)]); /* the argument of the log */
+        float r2 = orc_u01(w[2 * (t & 1) + 1]);
         float cand;
         if (haar) {
             cand = 2.0f * r1 - 1.0f;
@@ -663,8 +682,10 @@ int orc_heatbath_link_kp(float beta, const float v[4], uint64_t seed, uint32_t e
     float a0 = 0.0f;
     int trials = 0;
     for (int t = 0; t < ORC_MAX_TRIALS; ++t) {
-        float u[4];
-        draw_block(seed, eo, sweep, ORC_KIND_KP, parity, mu, (uint32_t)t, u);
+        uint32_t w[4];
+        draw_words(seed, eo, sweep, ORC_KIND_KP, parity, mu, (uint32_t)t, w);
+        /* words 0 and 2 feed logarithms */
+        const float u[4] = {orc_u01_log(w[0]), orc_u01(w[1]), orc_u01_log(w[2]), orc_u01(w[3])};
         float sn, cs;
         orc_sincos2pi(u[1], &sn, &cs);
         const float num = fmaf(cs * cs, orc_logf(u[2]), orc_logf(u[0]));

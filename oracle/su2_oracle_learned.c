@@ -31,6 +31,7 @@
 /* from su2_oracle.c */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 float orc_u01(uint32_t x);
+float orc_u01_log(uint32_t x);
 float orc_logf(float x);
 float orc_expf(float y);
 void orc_sincos2pi(float u, float *s, float *c);
@@ -351,7 +352,11 @@ int64_t orc_collect_pairs(int ns, int nt, double beta, uint64_t seed, uint32_t s
                 uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
                 uint32_t wd[4];
                 orc_philox4x32_10(ctr, key, wd);
-                for (int i = 0; i < 4; ++i) u[i] = orc_u01(wd[i]);
+                /* words 0 and 2 feed the logarithm, as in orc_heatbath_link */
+                u[0] = orc_u01_log(wd[0]);
+                u[1] = orc_u01(wd[1]);
+                u[2] = orc_u01_log(wd[2]);
+                u[3] = orc_u01(wd[3]);
             }
             const float r1 = u[2 * (t & 1)], r2 = u[2 * (t & 1) + 1];
             float cand = haar ? 2.0f * r1 - 1.0f : 1.0f + orc_logf(fmaf(r1, ome, e)) * inv_bk;

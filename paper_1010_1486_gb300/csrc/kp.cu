@@ -45,7 +45,7 @@ __device__ __forceinline__ bool kp_trial(uint4 w, float two_bk, float &a0)
 {
     float sn, cs;
     sincos_2pi(uniform01(w.y), sn, cs);
-    const float num = __fmaf_rn(__fmul_rn(cs, cs), log_series(uniform01(w.z)), log_series(uniform01(w.x)));
+    const float num = __fmaf_rn(__fmul_rn(cs, cs), log_series(uniform_log(w.z)), log_series(uniform_log(w.x)));
     const float lam2 = __fdiv_rn(-num, two_bk);
     const float r4 = uniform01(w.w);
     a0 = __fmaf_rn(-2.0f, lam2, 1.0f);

@@ -197,11 +197,11 @@ __global__ void __launch_bounds__(kLearnThreads) collect_kernel(const float4 *__
     for (int b = 0; b < kMaxTrials / 2; ++b) {
         const uint4 w = philox_rk(make_uint4((uint32_t)eo, sweep, sw, (uint32_t)b), rk);
         float cand;
-        if (creutz_trial(uniform01(w.x), uniform01(w.y), d.ibk, d.e, ome, haar, cand)) {
+        if (creutz_trial(uniform_log(w.x), uniform01(w.y), d.ibk, d.e, ome, haar, cand)) {
             a0 = cand;
             break;
         }
-        if (creutz_trial(uniform01(w.z), uniform01(w.w), d.ibk, d.e, ome, haar, cand)) {
+        if (creutz_trial(uniform_log(w.z), uniform01(w.w), d.ibk, d.e, ome, haar, cand)) {
             a0 = cand;
             break;
         }

@@ -90,6 +90,17 @@ __device__ __forceinline__ float uniform01(uint32_t w)
     return __fmul_rn(__uint2float_rn((w >> 8) + 1u), 5.9604644775390625e-8f);
 }
 
+// Uniform for the argument of a logarithm: w 2^-32 + 2^-33 from the whole
+// word (w rounded to nearest, then one fused multiply-add), in [2^-33, 1].
+// Creutz's x is uniform on [exp(-2 beta k), 1] (Sec. 2); from 24 bits -ln x
+// would stop at 16.6 and cut away the law's tail beta k (1 - a0) > 16.6
+// (2.8e-7 of its mass at large beta k, about +4e-7 on the plaquette at
+// beta = 6); from the whole word the cut is at 22.9 (mass 6e-10).
+__device__ __forceinline__ float uniform_log(uint32_t w)
+{
+    return __fmaf_rn(__uint2float_rn(w), 0x1p-32f, 0x1p-33f);
+}
+
 // Counter of a draw: (even/odd site index, sweep, (kind << 3) | (parity << 2) | mu, block).
 enum StreamKind : uint32_t { kCreutz = 0, kDirection = 1, kHotStart = 2, kLearned = 3 };
 
@@ -272,7 +283,7 @@ __device__ __forceinline__ bool creutz_trial(float r1, float r2, float ibk, floa
 // t~ = -lg2(x) ln2 ibk with the hardware base-2 logarithm (__log2f: absolute
 // error <= 2^-22 for x in [1/2, 1], relative <= 2.4e-7 below), and log_series
 // has |L - ln x| <= 1e-6 |ln x| + 1e-7; both bounds hold for every float x in
-// [2^-25, 1], the range x = e + r1 (1 - e) takes.  So
+// [2^-34, 1], the range x = e + r1 (1 - e) takes (r1 >= 2^-33).  So
 // |t - t~| <= 2.7e-7 ibk + 1.4e-6 t~ and |R - g(t~)| <= 3e-7 + 5.4e-7 ibk +
 // 3e-6 t~, and with the slack 2e-6 + 4e-6 ibk + 2e-5 t~ (more than six times
 // that) a trial with A > g(t~) + slack is rejected and one with
@@ -332,8 +343,8 @@ __device__ __forceinline__ bool creutz_pair(uint4 w, float ibk, float e, bool li
 {
     const CreutzScreen s = make_screen(ibk);
     const float ome = __fsub_rn(1.0f, e);
-    const float r1a = uniform01(w.x), r2a = uniform01(w.y);
-    const float r1b = uniform01(w.z), r2b = uniform01(w.w);
+    const float r1a = uniform_log(w.x), r2a = uniform01(w.y);
+    const float r1b = uniform_log(w.z), r2b = uniform01(w.w);
     float va = __fmaf_rn(r1a, ome, e), vb = __fmaf_rn(r1b, ome, e);
     int sa = creutz_screen(va, r2a, s);
     int sb = creutz_screen(vb, r2b, s);
@@ -388,10 +399,10 @@ __device__ __forceinline__ int heatbath_draw(float4 v, float beta, const RoundKe
     for (int b = 0; b < kMaxTrials / 2 && trials == 0; ++b) {
         const uint4 w = philox_rk(make_uint4(eo, sweep, stream_word(kCreutz, parity, mu), (uint32_t)b), rk);
         float cand;
-        if (creutz_trial(uniform01(w.x), uniform01(w.y), s.ibk, s.e, ome, haar, cand)) {
+        if (creutz_trial(uniform_log(w.x), uniform01(w.y), s.ibk, s.e, ome, haar, cand)) {
             a0 = cand;
             trials = 2 * b + 1;
-        } else if (creutz_trial(uniform01(w.z), uniform01(w.w), s.ibk, s.e, ome, haar, cand)) {
+        } else if (creutz_trial(uniform_log(w.z), uniform01(w.w), s.ibk, s.e, ome, haar, cand)) {
             a0 = cand;
             trials = 2 * b + 2;
         }

@@ -73,6 +73,27 @@ def test_u01_is_exact_and_in_half_open_unit_interval():
         assert oracle.u01(x) == ((x >> 8) + 1) * 2.0 ** -24
 
 
+def test_u01_log_reaches_2_to_minus_33_and_rounds_once():
+    """The uniform under a logarithm is w 2^-32 + 2^-33 with w rounded to the
+    nearest binary32 first: exact (2w + 1) 2^-33 below 2^23, in [2^-33, 1],
+    non-decreasing in w, so -ln x reaches 33 ln 2 = 22.9 instead of the 16.6 of
+    a 24-bit uniform (the Creutz proposal of Sec. 2 keeps its tail down to
+    beta k (1 - a0) = 22.9)."""
+    assert oracle.u01_log(0) == 2.0 ** -33
+    assert oracle.u01_log(0xFFFFFFFF) == 1.0
+    for x in [1, 2, 1000, (1 << 23) - 1]:
+        assert oracle.u01_log(x) == (2 * x + 1) * 2.0 ** -33
+    rng = np.random.default_rng(4)
+    w = np.sort(rng.integers(0, 1 << 32, 20000, dtype=np.uint64))
+    got = np.array([oracle.u01_log(int(x)) for x in w])
+    # float32(w) exactly in float64, times 2^-32, plus 2^-33 is exact in float64,
+    # so one rounding to float32 reproduces the fused multiply-add
+    want = (w.astype(np.float32).astype(np.float64) * 2.0 ** -32 + 2.0 ** -33).astype(np.float32)
+    assert np.array_equal(got.astype(np.float32), want)
+    assert np.all(np.diff(got) >= 0.0)
+    assert -np.log(oracle.u01_log(0)) > 22.8
+
+
 def _ulp_err(got32, exact64):
     ref32 = np.abs(exact64).astype(np.float32)
     ulp = np.spacing(ref32).astype(np.float64)
