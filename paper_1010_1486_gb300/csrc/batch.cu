@@ -2,7 +2,9 @@
 // swept together: one persistent cooperative launch per sweep runs the eight
 // even/odd phases of every lattice (Sec. 2 update, Sec. 4 schedule) with a
 // grid-wide barrier between phases, then the plaquette and Polyakov loop of
-// every lattice (Sec. 4), each reduced in a fixed order.  With a user stream
+// every lattice (Sec. 4), each reduced in a fixed order.  In a measuring
+// sweep the plaquette comes from the odd phases of mu = 1, 2, 3 (as in the
+// single-lattice sweep) and only the Polyakov loop reads the links again.  With a user stream
 // the launch is captured once into a CUDA graph and replayed per sweep.
 //
 // Each lattice follows exactly the single-lattice chain: same Philox
@@ -49,11 +51,17 @@ struct BatchParams {
     const LatDesc *desc;        // [n]
     const int *chunk_prefix;    // [n + 1]: first heat-bath chunk of each lattice
     const int *mround_prefix;   // [n + 1]: first measurement round of each lattice
+    const int *chunk_owner;     // [total_chunks]: lattice of each chunk
+    const int *mround_owner;    // [total_mrounds]: lattice of each measurement round
+    const int2 *poly_rounds;    // [total_poly_rounds]: (measurement round, lattice) of the Polyakov rounds
     int n;
     int total_chunks;
     int total_mrounds;
+    int total_poly_rounds;
     int do_sweep;               // run the eight phases
     int measure;                // then the plaquette and Polyakov loop
+    int fused;                  // do_sweep && measure: the plaquette comes from the sweep
+    double *chunk_partials;     // [3][total_chunks]: fused plaquette partials of phases (mu, odd), mu = 1, 2, 3
     unsigned int *sweep;        // sweep counter: read at start, advanced at the end
     unsigned int *meas_index;   // next history slot
     double *round_partials;     // [total_mrounds]
@@ -108,29 +116,26 @@ __device__ bool grid_barrier(BarrierState *bar, unsigned long long timeout_ns)
     return ok != 0;
 }
 
-// Largest l in [0, n) with prefix[l] <= x (prefix[0] = 0, increasing).
-__device__ __forceinline__ int find_owner(const int *__restrict__ prefix, int n, int x)
+__device__ __forceinline__ double warp_sum(double v)
 {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(prefix + mid) <= x)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    return v;
 }
 
 // One phase (MU, parity) over every lattice: chunks of 32 R consecutive
-// even/odd sites of one lattice, one warp per chunk, as in the single-lattice
+// even/odd sites of one lattice; each warp takes a contiguous range of
+// chunks and sweeps each lattice's part of it as in the single-lattice
 // kernel: the staple of the next round of 32 sites is loaded one nu-group per
 // stage while the current round is drawn; the first Philox block (trials 0,
 // 1, screened) inline, links with both rejected retried 32 at a time from the
 // warp's retry queue, accepted links given their a0, direction and store 32
-// at a time;
-// both queues are emptied at the end of the chunk.
-template <int MU, int R>
+// at a time; both queues are emptied at the end of the lattice's part.  MEAS
+// (odd phases of mu = 1, 2, 3 in a measuring sweep): the part's sum of
+// (1/2) Tr U'S, S the staple terms of nu < MU, goes to the slot of its first
+// chunk in bp.chunk_partials (its other chunks get zeros); over the three
+// phases every plaquette of the final configuration is counted once.
+template <int MU, int R, bool MEAS>
 __device__ void batch_phase(const BatchParams &bp, int parity, uint32_t sweep, CrQueues &Q, LatDesc &sd,
                             unsigned int &my_trials)
 {
@@ -141,8 +146,15 @@ __device__ void batch_phase(const BatchParams &bp, int parity, uint32_t sweep, C
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t sw_creutz = stream_word(kCreutz, (uint32_t)parity, MU);
     const uint32_t sw_dir = stream_word(kDirection, (uint32_t)parity, MU);
-    for (int chunk = warp_global; chunk < bp.total_chunks; chunk += nwarps) {
-        const int l = find_owner(bp.chunk_prefix, bp.n, chunk);
+    // the warp's contiguous range of chunks (sizes differ by at most one);
+    // each run of chunks of one lattice is one segment: one pipeline start and
+    // one queue drain per segment
+    const int per = bp.total_chunks / nwarps, extra = bp.total_chunks % nwarps;
+    const int c_end = warp_global * per + min(warp_global, extra) + per + (warp_global < extra ? 1 : 0);
+    for (int chunk = warp_global * per + min(warp_global, extra); chunk < c_end;) {
+        const int l = __ldg(bp.chunk_owner + chunk);
+        const int lat_c0 = __ldg(bp.chunk_prefix + l);
+        const int seg_end = min(c_end, __ldg(bp.chunk_prefix + l + 1));
         // the lattice's descriptor, staged in the warp's shared slot and read
         // from there (holding it in registers would crowd out the pipeline)
         __syncwarp();
@@ -157,12 +169,13 @@ __device__ void batch_phase(const BatchParams &bp, int parity, uint32_t sweep, C
         float4 *const links = sd.links;
         const uint32_t k0 = sd.k0, k1 = sd.k1;
         const float beta = sd.beta;
-        const int base0 = (chunk - __ldg(bp.chunk_prefix + l)) * C;
-        const int last = min(base0 + C, g.vh) - 1;
+        const int base0 = (chunk - lat_c0) * C;
+        const int last = min((seg_end - lat_c0) * C, g.vh) - 1;
         const int rounds = (last - base0 + 32) >> 5;
         int retry_n = 0, done_n = 0;
+        double plaq = 0.0;
 
-        auto push_done = [&](bool ok, float4 ut, float val, float ibk, int eo) {
+        auto push_done = [&](bool ok, float4 ut, float val, float ibk, int eo, float4 sp) {
             const unsigned int m = __ballot_sync(0xffffffffu, ok);
             if (ok) {
                 const int q = done_n + __popc(m & lanes_below);
@@ -170,10 +183,11 @@ __device__ void batch_phase(const BatchParams &bp, int parity, uint32_t sweep, C
                 Q.d_val[q] = val;
                 Q.d_ibk[q] = ibk;
                 Q.d_eo[q] = eo;
+                if (MEAS) Q.d_sp[q] = sp;
             }
             done_n += __popc(m);
         };
-        auto push_retry = [&](bool again, float4 ut, float ibk, float e, int eo, int blk) {
+        auto push_retry = [&](bool again, float4 ut, float ibk, float e, int eo, int blk, float4 sp) {
             const unsigned int m = __ballot_sync(0xffffffffu, again);
             if (again) {
                 const int q = retry_n + __popc(m & lanes_below);
@@ -182,6 +196,7 @@ __device__ void batch_phase(const BatchParams &bp, int parity, uint32_t sweep, C
                 Q.r_e[q] = e;
                 Q.r_eo[q] = eo;
                 Q.r_blk[q] = blk;
+                if (MEAS) Q.r_sp[q] = sp;
             }
             retry_n += __popc(m);
         };
@@ -191,8 +206,9 @@ __device__ void batch_phase(const BatchParams &bp, int parity, uint32_t sweep, C
                 const int q = first + lane;
                 const int eo = Q.d_eo[q];
                 const uint4 wd = philox_key(make_uint4((uint32_t)eo, sweep, sw_dir, 0u), k0, k1);
-                links[link_index(g, MU, parity, eo)] =
-                    direction_update(deferred_a0(Q.d_val[q], Q.d_ibk[q]), Q.d_ut[q], wd);
+                const float4 out = direction_update(deferred_a0(Q.d_val[q], Q.d_ibk[q]), Q.d_ut[q], wd);
+                links[link_index(g, MU, parity, eo)] = out;
+                if (MEAS) plaq += (double)qmul_re(out, Q.d_sp[q]);
             }
             __syncwarp();
         };
@@ -205,7 +221,7 @@ __device__ void batch_phase(const BatchParams &bp, int parity, uint32_t sweep, C
         auto retry_pass = [&](int first, int n) {
             __syncwarp();
             const bool have = lane < n;
-            float4 ut = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+            float4 ut = make_float4(1.0f, 0.0f, 0.0f, 0.0f), sp = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             float ibk = 1.0f, e = 0.0f;
             int eo = 0, blk = 0;
             if (have) {
@@ -215,6 +231,7 @@ __device__ void batch_phase(const BatchParams &bp, int parity, uint32_t sweep, C
                 e = Q.r_e[q];
                 eo = Q.r_eo[q];
                 blk = Q.r_blk[q];
+                if (MEAS) sp = Q.r_sp[q];
             }
             __syncwarp();
             const uint4 w = philox_key(make_uint4((uint32_t)eo, sweep, sw_creutz, (uint32_t)blk), k0, k1);
@@ -232,20 +249,24 @@ __device__ void batch_phase(const BatchParams &bp, int parity, uint32_t sweep, C
                     my_trials += (unsigned int)kMaxTrials;
                 }
             }
-            push_retry(again, ut, ibk, e, eo, blk + 1);
-            push_done(ok, ut, val, ibk, eo);
+            push_retry(again, ut, ibk, e, eo, blk + 1, sp);
+            push_done(ok, ut, val, ibk, eo, sp);
             flush_done();
         };
 
         int cur = base0 + lane;
         float4 v_cur = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        float4 sp_cur = v_cur;  // MEAS: staple terms of nu < MU (the first MU groups)
         {
             const int e = min(cur, last);
             const Coord x = eo_to_coord(g, e, parity);
             const int e_p = eo_fwd<MU>(g, x, e);
             v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 0>::value>(links, g, x, e, e_p, parity));
+            if (MU == 1) sp_cur = v_cur;
             v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 1>::value>(links, g, x, e, e_p, parity));
+            if (MU == 2) sp_cur = v_cur;
             v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 2>::value>(links, g, x, e, e_p, parity));
+            if (MU == 3) sp_cur = v_cur;
         }
 #pragma unroll 1
         for (int r = 0; r < rounds; ++r) {
@@ -259,6 +280,7 @@ __device__ void batch_phase(const BatchParams &bp, int parity, uint32_t sweep, C
             const DrawSetup ds = prepare_draw(v_cur, beta);
             const uint4 w = philox_key(make_uint4((uint32_t)cur, sweep, sw_creutz, 0u), k0, k1);
             float4 v_next = add_nu_terms(make_float4(0.0f, 0.0f, 0.0f, 0.0f), nl);
+            float4 sp_next = v_next;
             // ---- part 1
             nl = load_nu_eo<MU, OtherDir<MU, 1>::value>(links, g, xn, en, en_p, parity);
             {
@@ -267,20 +289,23 @@ __device__ void batch_phase(const BatchParams &bp, int parity, uint32_t sweep, C
                 const bool acc = creutz_pair(w, ds.ibk, ds.e, valid, first_ok, val);
                 const bool ok = valid && acc;
                 my_trials += ok ? (first_ok ? 1u : 2u) : 0u;
-                push_done(ok, ds.ut, val, ds.ibk, cur);
-                push_retry(valid && !acc, ds.ut, ds.ibk, ds.e, cur, 1);
+                push_done(ok, ds.ut, val, ds.ibk, cur, sp_cur);
+                push_retry(valid && !acc, ds.ut, ds.ibk, ds.e, cur, 1, sp_cur);
             }
             v_next = add_nu_terms(v_next, nl);
+            if (MU == 2) sp_next = v_next;
             // ---- part 2
             nl = load_nu_eo<MU, OtherDir<MU, 2>::value>(links, g, xn, en, en_p, parity);
             flush_done();
             v_next = add_nu_terms(v_next, nl);
+            if (MU == 3) sp_next = v_next;
             while (retry_n >= 32) {
                 retry_n -= 32;
                 retry_pass(retry_n, 32);
             }
             cur = nxt;
             v_cur = v_next;
+            sp_cur = sp_next;
         }
         while (retry_n > 0) {
             const int n = min(retry_n, 32);
@@ -288,28 +313,38 @@ __device__ void batch_phase(const BatchParams &bp, int parity, uint32_t sweep, C
             retry_pass(retry_n, n);
         }
         if (done_n > 0) direction_pass(0, done_n);
+        if (MEAS) {
+            // the segment's sum in the slot of its first chunk, zeros in the others
+            const double total = warp_sum(plaq);
+            for (int c = chunk + lane; c < seg_end; c += 32)
+                bp.chunk_partials[(MU - 1) * bp.total_chunks + c] = c == chunk ? total : 0.0;
+        }
+        chunk = seg_end;
     }
 }
 
-__device__ __forceinline__ double warp_sum(double v)
-{
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    return v;
-}
-
 // Per round of 32 sites (or 32 Polyakov lines) of one lattice: the warp's
-// fp64 sum of the binary32 per-site values, in a fixed order.
+// fp64 sum of the binary32 per-site values, in a fixed order.  After a fused
+// sweep only the Polyakov rounds run.
 __device__ void batch_measure_rounds(const BatchParams &bp)
 {
     const int lane = threadIdx.x & 31;
     const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int mr = warp_global; mr < bp.total_mrounds; mr += nwarps) {
-        const int l = find_owner(bp.mround_prefix, bp.n, mr);
+    const int items = bp.fused ? bp.total_poly_rounds : bp.total_mrounds;
+    for (int it = warp_global; it < items; it += nwarps) {
+        int mr, l;
+        if (bp.fused) {
+            const int2 pr = __ldg(bp.poly_rounds + it);
+            mr = pr.x;
+            l = pr.y;
+        } else {
+            mr = it;
+            l = __ldg(bp.mround_owner + it);
+        }
         const LatDesc *d = bp.desc + l;
-        const Geom g = d->g;
         const int local = mr - __ldg(bp.mround_prefix + l);
+        const Geom g = d->g;
         double val = 0.0;
         if (local < d->nplaq_rounds) {
             const int s = local * 32 + lane;
@@ -327,7 +362,8 @@ __device__ void batch_measure_rounds(const BatchParams &bp)
     }
 }
 
-// Per lattice: sums of its round partials in index order -> history slot.
+// Per lattice: sums of its round partials (after a fused sweep, of its chunk
+// partials of the three measuring phases) in index order -> history slot.
 __device__ void batch_measure_final(const BatchParams &bp, unsigned int slot)
 {
     const int lane = threadIdx.x & 31;
@@ -338,8 +374,16 @@ __device__ void batch_measure_final(const BatchParams &bp, unsigned int slot)
         const int r0 = __ldg(bp.mround_prefix + l);
         const int np = d->nplaq_rounds, nl = d->npoly_rounds;
         double sp = 0.0, sl = 0.0;
-        for (int r = lane; r < np; r += 32) sp += ((volatile double *)bp.round_partials)[r0 + r];
-        for (int r = lane; r < nl; r += 32) sl += ((volatile double *)bp.round_partials)[r0 + np + r];
+        // the partials were written by other blocks before the grid barrier and
+        // not read by this one: loads through L2 (__ldcg) see them
+        if (bp.fused) {
+            const int c0 = __ldg(bp.chunk_prefix + l), c1 = __ldg(bp.chunk_prefix + l + 1);
+            for (int k = 0; k < 3; ++k)
+                for (int c = c0 + lane; c < c1; c += 32) sp += __ldcg(bp.chunk_partials + k * bp.total_chunks + c);
+        } else {
+            for (int r = lane; r < np; r += 32) sp += __ldcg(bp.round_partials + r0 + r);
+        }
+        for (int r = lane; r < nl; r += 32) sl += __ldcg(bp.round_partials + r0 + np + r);
         sp = warp_sum(sp);
         sl = warp_sum(sl);
         if (lane == 0) {
@@ -360,16 +404,27 @@ __global__ void __launch_bounds__(kHbThreads, kBatchMinBlocks) batch_sweep_kerne
     const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t sweep = *(volatile unsigned int *)bp.sweep;
     const unsigned int slot = *(volatile unsigned int *)bp.meas_index;
+    const bool fused = bp.fused && (int)slot < bp.history_cap;
     bool ok = true;
     if (bp.do_sweep) {
         for (int ph = 0; ph < 8 && ok; ++ph) {
             const int parity = ph & 1;
             unsigned int my_trials = 0;
+            const bool meas = fused && parity == 1;
             switch (ph >> 1) {
-            case 0: batch_phase<0, R>(bp, parity, sweep, s_q[wib], s_desc[wib], my_trials); break;
-            case 1: batch_phase<1, R>(bp, parity, sweep, s_q[wib], s_desc[wib], my_trials); break;
-            case 2: batch_phase<2, R>(bp, parity, sweep, s_q[wib], s_desc[wib], my_trials); break;
-            default: batch_phase<3, R>(bp, parity, sweep, s_q[wib], s_desc[wib], my_trials); break;
+            case 0: batch_phase<0, R, false>(bp, parity, sweep, s_q[wib], s_desc[wib], my_trials); break;
+            case 1:
+                if (meas) batch_phase<1, R, true>(bp, parity, sweep, s_q[wib], s_desc[wib], my_trials);
+                else batch_phase<1, R, false>(bp, parity, sweep, s_q[wib], s_desc[wib], my_trials);
+                break;
+            case 2:
+                if (meas) batch_phase<2, R, true>(bp, parity, sweep, s_q[wib], s_desc[wib], my_trials);
+                else batch_phase<2, R, false>(bp, parity, sweep, s_q[wib], s_desc[wib], my_trials);
+                break;
+            default:
+                if (meas) batch_phase<3, R, true>(bp, parity, sweep, s_q[wib], s_desc[wib], my_trials);
+                else batch_phase<3, R, false>(bp, parity, sweep, s_q[wib], s_desc[wib], my_trials);
+                break;
             }
             const unsigned int wsum = __reduce_add_sync(0xffffffffu, my_trials);
             if (lane == 0 && wsum)
@@ -435,6 +490,11 @@ struct su2_batch {
     int *d_chunk_prefix = nullptr;
     int *d_mround_prefix = nullptr;
     double *d_partials = nullptr;
+    double *d_chunk_partials = nullptr;  // [3][chunks at queue depth 2, the most]
+    int *d_chunk_owner = nullptr;        // [chunks at queue depth 2]
+    int *d_mround_owner = nullptr;       // [total_mrounds]
+    int2 *d_poly_rounds = nullptr;       // [total_poly_rounds]
+    int total_poly_rounds = 0;
     BarrierState *d_bar = nullptr;
     unsigned int *d_counters = nullptr;  // [0] sweep, [1] measurement index, [2..] flags
     unsigned long long *d_trials = nullptr;
@@ -479,7 +539,12 @@ su2_status set_depth(su2_batch *b, int R, int grid)
 {
     std::vector<int> prefix(b->n + 1, 0);
     for (int l = 0; l < b->n; ++l) prefix[l + 1] = prefix[l] + (b->geom[l].vh + 32 * R - 1) / (32 * R);
+    std::vector<int> owner(prefix[b->n]);
+    for (int l = 0; l < b->n; ++l)
+        for (int c = prefix[l]; c < prefix[l + 1]; ++c) owner[c] = l;
     SU2_CUDA(cudaMemcpyAsync(b->d_chunk_prefix, prefix.data(), sizeof(int) * (b->n + 1), cudaMemcpyHostToDevice,
+                             b->stream));
+    SU2_CUDA(cudaMemcpyAsync(b->d_chunk_owner, owner.data(), sizeof(int) * owner.size(), cudaMemcpyHostToDevice,
                              b->stream));
     SU2_CUDA(cudaStreamSynchronize(b->stream));
     b->total_chunks = prefix[b->n];
@@ -495,14 +560,20 @@ BatchParams params_of(const su2_batch *b, int do_sweep, int measure)
     p.desc = b->d_desc;
     p.chunk_prefix = b->d_chunk_prefix;
     p.mround_prefix = b->d_mround_prefix;
+    p.chunk_owner = b->d_chunk_owner;
+    p.mround_owner = b->d_mround_owner;
+    p.poly_rounds = b->d_poly_rounds;
     p.n = b->n;
     p.total_chunks = b->total_chunks;
     p.total_mrounds = b->total_mrounds;
+    p.total_poly_rounds = b->total_poly_rounds;
     p.do_sweep = do_sweep;
     p.measure = measure;
     p.sweep = b->d_counters;
     p.meas_index = b->d_counters + 1;
     p.round_partials = b->d_partials;
+    p.fused = do_sweep && measure;
+    p.chunk_partials = b->d_chunk_partials;
     p.history = b->d_history;
     p.history_cap = b->history_cap;
     p.bar = b->d_bar;
@@ -654,9 +725,11 @@ su2_status su2_batch_create(int n, const int *ns, const int *nt, const double *b
     b->beta.assign(beta, beta + n);
     b->seed.assign(seed, seed + n);
     size_t off = 0;
+    size_t max_chunks = 0;  // chunks of 64 sites (queue depth 2)
     std::vector<int> mprefix(n + 1, 0);
     for (int l = 0; l < n; ++l) {
         const Geom g = make_geom(ns[l], nt[l]);
+        max_chunks += ((size_t)g.vh + 63) / 64;
         b->geom.push_back(g);
         b->link_offset.push_back(off);
         off += (8 * (size_t)g.vh + 15) & ~(size_t)15;  // keep each lattice 256-byte aligned
@@ -669,10 +742,24 @@ su2_status su2_batch_create(int n, const int *ns, const int *nt, const double *b
     const size_t desc_bytes = align256(sizeof(LatDesc) * n);
     const size_t prefix_bytes = align256(sizeof(int) * (n + 1));
     const size_t partial_bytes = align256(sizeof(double) * b->total_mrounds);
+    const size_t chunk_bytes = align256(sizeof(double) * 3 * max_chunks);
+    std::vector<int> mowner(b->total_mrounds);
+    std::vector<int2> poly_rounds;
+    for (int l = 0; l < n; ++l) {
+        const int np = (2 * b->geom[l].vh + 31) / 32;
+        for (int r = mprefix[l]; r < mprefix[l + 1]; ++r) {
+            mowner[r] = l;
+            if (r - mprefix[l] >= np) poly_rounds.push_back(make_int2(r, l));
+        }
+    }
+    b->total_poly_rounds = (int)poly_rounds.size();
+    const size_t owner_bytes = align256(sizeof(int) * max_chunks) + align256(sizeof(int) * b->total_mrounds) +
+                               align256(sizeof(int2) * poly_rounds.size());
     const size_t bar_bytes = align256(sizeof(BarrierState));
     const size_t counter_bytes = align256(sizeof(unsigned int) * 8);
     const size_t trial_bytes = align256(sizeof(unsigned long long) * 8 * kTrialSlots);
-    b->block_bytes = links_bytes + desc_bytes + 2 * prefix_bytes + partial_bytes + bar_bytes + counter_bytes + trial_bytes;
+    b->block_bytes = links_bytes + desc_bytes + 2 * prefix_bytes + partial_bytes + chunk_bytes + owner_bytes +
+                     bar_bytes + counter_bytes + trial_bytes;
     b->block = device_alloc(b->block_bytes, dev, b->stream);
     if (!b->block) {
         delete b;
@@ -690,6 +777,14 @@ su2_status su2_batch_create(int n, const int *ns, const int *nt, const double *b
     p += prefix_bytes;
     b->d_partials = (double *)p;
     p += partial_bytes;
+    b->d_chunk_partials = (double *)p;
+    p += chunk_bytes;
+    b->d_chunk_owner = (int *)p;
+    p += align256(sizeof(int) * max_chunks);
+    b->d_mround_owner = (int *)p;
+    p += align256(sizeof(int) * b->total_mrounds);
+    b->d_poly_rounds = (int2 *)p;
+    p += align256(sizeof(int2) * poly_rounds.size());
     b->d_bar = (BarrierState *)p;
     p += bar_bytes;
     b->d_counters = (unsigned int *)p;
@@ -711,6 +806,12 @@ su2_status su2_batch_create(int n, const int *ns, const int *nt, const double *b
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_mround_prefix, mprefix.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice,
                             b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_mround_owner, mowner.data(), sizeof(int) * mowner.size(), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess && !poly_rounds.empty())
+        e = cudaMemcpyAsync(b->d_poly_rounds, poly_rounds.data(), sizeof(int2) * poly_rounds.size(),
+                            cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bar, 0, bar_bytes + counter_bytes + trial_bytes, b->stream);
     for (int l = 0; l < n && e == cudaSuccess; ++l)
         e = start_links(b->links + b->link_offset[l], b->geom[l], start == SU2_HOT, seed[l], b->d_counters + 2,

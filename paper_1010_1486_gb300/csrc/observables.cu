@@ -43,20 +43,8 @@ __global__ void __launch_bounds__(kReduceThreads) polyakov_kernel(const float4 *
                                                                   const uint32_t *__restrict__ idx)
 {
     double acc = 0.0;
-    for (int xs = blockIdx.x * blockDim.x + threadIdx.x; xs < g.vs; xs += gridDim.x * blockDim.x) {
-        int rest = xs / g.ns;
-        const int x = xs - rest * g.ns;
-        const int y = rest % g.ns;
-        const int z = rest / g.ns;
-        const int p0 = (x + y + z) & 1;
-        float4 p = __ldg(L + link_index(g, 3, p0, xs >> 1));
-#pragma unroll 4
-        for (int t = 1; t < g.nt; ++t) {
-            const int64_t lex = (int64_t)t * g.vs + xs;
-            p = qmul(p, __ldg(L + link_index(g, 3, (p0 + t) & 1, (int)(lex >> 1))));
-        }
-        acc += (double)p.x;
-    }
+    for (int xs = blockIdx.x * blockDim.x + threadIdx.x; xs < g.vs; xs += gridDim.x * blockDim.x)
+        acc += (double)site_polyakov(L, g, xs);
     const double total = block_sum(acc);
     finish_reduction(total, partials, ticket, idx ? dst + *idx : dst, 1.0 / (double)g.vs);
 }
