@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define SU2_ABI_VERSION 2
+#define SU2_ABI_VERSION 3
 
 typedef struct su2_lattice su2_lattice;
 
@@ -192,6 +192,28 @@ su2_status su2_wilson_loops(su2_lattice *lat, int rmax, int tmax, double *out);
 su2_status su2_get_links(su2_lattice *lat, float *host);
 su2_status su2_set_links(su2_lattice *lat, const float *host);
 
+/* Asynchronous forms, for pipelines that keep several configurations in
+ * flight (one lattice handle, with its own stream, per configuration): each
+ * call only enqueues its work on the lattice's stream and returns.
+ * - su2_set_links_async / su2_get_links_async: the host buffer as in
+ *   su2_set_links / su2_get_links.  The links pass through the lattice's
+ *   device staging buffer (16 V floats, allocated on first use) and the copy
+ *   engines, so one lattice's transfers run beside another lattice's sweeps.
+ *   The host buffer must stay valid (and, for set, unchanged) until su2_sync.
+ *   Page-locked host memory makes the copies asynchronous; pageable memory
+ *   works but the driver stages it synchronously.
+ * - su2_generate_async: su2_generate without the statistics.  plaq / poly
+ *   (host, nullable, nsweeps/measure_every values each, page-locked for an
+ *   asynchronous copy) hold their values after su2_sync.
+ * - su2_sync: waits for the lattice's stream.  Returns SU2_E_SAMPLER (and
+ *   clears the flag) if a heat-bath draw hit its trial cap since the last
+ *   synchronous statistics read, SU2_E_CUDA on a device error. */
+su2_status su2_set_links_async(su2_lattice *lat, const float *host);
+su2_status su2_get_links_async(su2_lattice *lat, float *host);
+su2_status su2_generate_async(su2_lattice *lat, int nsweeps, int measure_every, int reunit_every, double *plaq,
+                              double *poly);
+su2_status su2_sync(su2_lattice *lat);
+
 /* Resumable state (sweep counter, seed, beta).  set_state requires matching extents. */
 su2_status su2_get_state(const su2_lattice *lat, su2_state *out);
 su2_status su2_set_state(su2_lattice *lat, const su2_state *in);
@@ -331,7 +353,8 @@ su2_status su2_batch_polyakov(su2_batch *b, double *out_n);
 /* Links of lattice i in the layout of su2_get_links. */
 su2_status su2_batch_get_links(su2_batch *b, int i, float *host);
 
-/* Launch configuration: queue depth (pending links per lane: 2, 4 or 8) and
+/* Launch configuration: queue depth (2, 4 or 8: the work is split into chunks
+ * of 32 x depth sites, and each warp takes a contiguous range of chunks) and
  * grid (blocks of 128 threads; <= 0 or too large = all co-resident blocks).
  * su2_batch_autotune times every depth with the full and the half grid over
  * `sweeps` sweeps, restores the links and sweep counter, and keeps the fastest. */

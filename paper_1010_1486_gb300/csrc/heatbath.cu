@@ -407,6 +407,14 @@ static su2_status sweep_and_measure(su2_lattice *lat, bool measure, bool reunit,
     return SU2_OK;
 }
 
+// Sets the device sweep counter and measurement slot from kernel parameters
+// (no host memory is read when it runs, so enqueueing it never waits).
+__global__ void set_counters_kernel(uint32_t *ctr, uint32_t sweep)
+{
+    ctr[0] = sweep;
+    ctr[1] = 0u;
+}
+
 // Advances the device counters of graph replays: the sweep, and the
 // measurement slot after a measured sweep.
 __global__ void advance_kernel(uint32_t *ctr, int measured)
@@ -489,28 +497,29 @@ static su2_status generation_graph(su2_lattice *lat, bool measure, bool reunit, 
     return SU2_OK;
 }
 
-}  // namespace su2
-
-using namespace su2;
-
-extern "C" {
-
-su2_status su2_generate(su2_lattice *lat, int nsweeps, int measure_every, int reunit_every, double *plaq,
-                        double *poly, su2_stats *stats)
+// Enqueues nsweeps sweeps with their measurements and reunitarizations, and
+// the copies of the measurement history to plaq / poly, on the lattice's
+// stream.  clear_flags: start from cleared sampler flags (the synchronous
+// call reads them back; the asynchronous one leaves them for su2_sync).
+static su2_status generate_enqueue(su2_lattice *lat, int nsweeps, int measure_every, int reunit_every,
+                                   double *plaq, double *poly, bool clear_flags)
 {
-    if (!lat || nsweeps < 0 || measure_every < 0 || reunit_every < 0) return SU2_E_INVAL;
-    DeviceGuard guard(lat->device);
     const int nmeas = measure_every > 0 ? nsweeps / measure_every : 0;
     su2_status st = ensure_history(lat, nmeas);
     if (st != SU2_OK) return st;
-    if ((st = launch_clear_counters(lat)) != SU2_OK) return st;
+    if (clear_flags) {
+        if ((st = launch_clear_counters(lat)) != SU2_OK) return st;
+    } else {
+        SU2_CUDA(cudaMemsetAsync(lat->scratch.trials, 0, sizeof(unsigned long long) * 8 * kTrialSlots,
+                                 lat->stream));
+    }
     lat->hb_log.used = 0;
     lat->or_log.used = 0;
     // Graph replays need a stream that can be captured and no per-launch events.
     bool graphs = lat->stream != nullptr && !lat->timing && !lat->graphs_off && nsweeps >= 1;
     if (graphs) {
-        const uint32_t ctr[2] = {lat->sweep, 0u};
-        SU2_CUDA(cudaMemcpyAsync(lat->d_ctr, ctr, sizeof ctr, cudaMemcpyHostToDevice, lat->stream));
+        set_counters_kernel<<<1, 1, 0, lat->stream>>>(lat->d_ctr, lat->sweep);
+        SU2_CUDA(cudaGetLastError());
     }
     int m = 0;
     for (int s = 1; s <= nsweeps; ++s) {
@@ -538,6 +547,22 @@ su2_status su2_generate(su2_lattice *lat, int nsweeps, int measure_every, int re
     if (nmeas > 0 && poly)
         SU2_CUDA(cudaMemcpyAsync(poly, lat->scratch.history + lat->scratch.history_cap, sizeof(double) * nmeas,
                                  cudaMemcpyDeviceToHost, lat->stream));
+    return SU2_OK;
+}
+
+}  // namespace su2
+
+using namespace su2;
+
+extern "C" {
+
+su2_status su2_generate(su2_lattice *lat, int nsweeps, int measure_every, int reunit_every, double *plaq,
+                        double *poly, su2_stats *stats)
+{
+    if (!lat || nsweeps < 0 || measure_every < 0 || reunit_every < 0) return SU2_E_INVAL;
+    DeviceGuard guard(lat->device);
+    su2_status st = generate_enqueue(lat, nsweeps, measure_every, reunit_every, plaq, poly, true);
+    if (st != SU2_OK) return st;
     if (stats) memset(stats, 0, sizeof *stats);
     st = collect_stats(lat, stats, (uint64_t)nsweeps);
     if (stats) {
@@ -547,6 +572,14 @@ su2_status su2_generate(su2_lattice *lat, int nsweeps, int measure_every, int re
     }
     su2_status st2 = read_timing(lat, stats);
     return st != SU2_OK ? st : st2;
+}
+
+su2_status su2_generate_async(su2_lattice *lat, int nsweeps, int measure_every, int reunit_every, double *plaq,
+                              double *poly)
+{
+    if (!lat || nsweeps < 0 || measure_every < 0 || reunit_every < 0) return SU2_E_INVAL;
+    DeviceGuard guard(lat->device);
+    return generate_enqueue(lat, nsweeps, measure_every, reunit_every, plaq, poly, false);
 }
 
 su2_status su2_heatbath_sweep(su2_lattice *lat, int nsweeps, su2_stats *stats)

@@ -462,6 +462,54 @@ su2_status su2_set_links(su2_lattice *lat, const float *host)
     return SU2_OK;
 }
 
+// Asynchronous forms: the links always go through the staging buffer and the
+// copy engines, so a transfer of one lattice runs beside the sweep kernels of
+// another lattice on its own stream (a conversion kernel reading mapped host
+// memory would need SMs that a persistent sweep holds).
+su2_status su2_set_links_async(su2_lattice *lat, const float *host)
+{
+    if (!lat || !host) return SU2_E_INVAL;
+    DeviceGuard guard(lat->device);
+    su2_status st = ensure_staging(lat);
+    if (st != SU2_OK) return st;
+    SU2_CUDA(cudaMemcpyAsync(lat->staging, host, sizeof(float4) * 4 * (size_t)lat->vol, cudaMemcpyHostToDevice,
+                             lat->stream));
+    convert_kernel<false><<<grid_for(4 * lat->vol, 256, 152 * 16), 256, 0, lat->stream>>>(
+        lat->links, (float4 *)lat->staging, geom_of(lat));
+    SU2_CUDA(cudaGetLastError());
+    return SU2_OK;
+}
+
+su2_status su2_get_links_async(su2_lattice *lat, float *host)
+{
+    if (!lat || !host) return SU2_E_INVAL;
+    DeviceGuard guard(lat->device);
+    su2_status st = ensure_staging(lat);
+    if (st != SU2_OK) return st;
+    convert_kernel<true><<<grid_for(4 * lat->vol, 256, 152 * 16), 256, 0, lat->stream>>>(
+        lat->links, (float4 *)lat->staging, geom_of(lat));
+    SU2_CUDA(cudaGetLastError());
+    SU2_CUDA(cudaMemcpyAsync(host, lat->staging, sizeof(float4) * 4 * (size_t)lat->vol, cudaMemcpyDeviceToHost,
+                             lat->stream));
+    return SU2_OK;
+}
+
+su2_status su2_sync(su2_lattice *lat)
+{
+    if (!lat) return SU2_E_INVAL;
+    DeviceGuard guard(lat->device);
+    unsigned int flags[4];
+    SU2_CUDA(cudaMemcpyAsync(flags, lat->scratch.flags, sizeof flags, cudaMemcpyDeviceToHost, lat->stream));
+    SU2_CUDA(cudaStreamSynchronize(lat->stream));
+    if (flags[0] != 0) {
+        SU2_CUDA(cudaMemsetAsync(lat->scratch.flags, 0, sizeof(unsigned int), lat->stream));
+        SU2_CUDA(cudaStreamSynchronize(lat->stream));
+        set_last_error("heat-bath sampler hit its trial cap");
+        return SU2_E_SAMPLER;
+    }
+    return SU2_OK;
+}
+
 su2_status su2_reunitarize(su2_lattice *lat)
 {
     if (!lat) return SU2_E_INVAL;

@@ -89,6 +89,10 @@ _SIGS = {
     "su2_polyakov": [_P, ctypes.POINTER(_f64)],
     "su2_get_links": [_P, _P],
     "su2_set_links": [_P, _P],
+    "su2_get_links_async": [_P, _P],
+    "su2_set_links_async": [_P, _P],
+    "su2_generate_async": [_P, _i32, _i32, _i32, _P, _P],
+    "su2_sync": [_P],
     "su2_get_state": [_P, ctypes.POINTER(su2_state)],
     "su2_set_state": [_P, ctypes.POINTER(su2_state)],
     "su2_set_beta": [_P, _f64],
@@ -264,6 +268,40 @@ def su2_get_links(lat: int, ns: int, nt: int, out: np.ndarray | None = None) -> 
 def su2_set_links(lat: int, links: np.ndarray) -> None:
     links = np.ascontiguousarray(links, dtype=np.float32)
     _check(_lib.su2_set_links(lat, _host_ptr(links)), "su2_set_links")
+
+
+def su2_set_links_async(lat: int, links: np.ndarray) -> None:
+    """Enqueues the upload of `links` (C-contiguous float32 [site, mu, 4]);
+    the caller keeps the array alive and unchanged until su2_sync."""
+    if not (links.flags["C_CONTIGUOUS"] and links.dtype == np.float32):
+        raise ValueError("su2_set_links_async needs a C-contiguous float32 array")
+    _check(_lib.su2_set_links_async(lat, _host_ptr(links)), "su2_set_links_async")
+
+
+def su2_get_links_async(lat: int, out: np.ndarray) -> None:
+    """Enqueues the download of the links into `out` (C-contiguous float32
+    [site, mu, 4]), valid after su2_sync."""
+    if not (out.flags["C_CONTIGUOUS"] and out.dtype == np.float32):
+        raise ValueError("su2_get_links_async needs a C-contiguous float32 array")
+    _check(_lib.su2_get_links_async(lat, _host_ptr(out)), "su2_get_links_async")
+
+
+def su2_generate_async(lat: int, nsweeps: int, measure_every: int = 1, reunit_every: int = 0,
+                       plaq: np.ndarray | None = None, poly: np.ndarray | None = None) -> None:
+    """su2_generate without statistics and without waiting; plaq / poly
+    (float64, nsweeps // measure_every values, nullable) hold their values
+    after su2_sync."""
+    nmeas = nsweeps // measure_every if measure_every > 0 else 0
+    for a in (plaq, poly):
+        if a is not None and (a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"] or a.size < nmeas):
+            raise ValueError("su2_generate_async: plaq / poly need nsweeps // measure_every float64 values")
+    _check(_lib.su2_generate_async(lat, nsweeps, measure_every, reunit_every,
+                                   _host_ptr(plaq) if plaq is not None and nmeas else None,
+                                   _host_ptr(poly) if poly is not None and nmeas else None), "su2_generate_async")
+
+
+def su2_sync(lat: int) -> None:
+    _check(_lib.su2_sync(lat), "su2_sync")
 
 
 def su2_get_state(lat: int) -> dict:

@@ -28,7 +28,7 @@ def test_every_declared_symbol_is_exported(su2):
         assert hasattr(lib, n), n
     core = {"su2_create", "su2_destroy", "su2_heatbath_sweep", "su2_reunitarize", "su2_plaquette", "su2_polyakov"}
     assert core <= set(names)
-    assert su2.su2_abi_version() == 2
+    assert su2.su2_abi_version() == 3
     # su2_stats as declared: 8 + 8 + 8*8 + 8 + 4 + 4 + 8 + 8 + 8 + 8 bytes
     assert ctypes.sizeof(su2.su2_stats) == 128
 
