@@ -15,7 +15,7 @@ namespace su2 {
 
 constexpr int kOrThreads = 256;
 #ifndef SU2_OR_MIN_BLOCKS
-#define SU2_OR_MIN_BLOCKS 3
+#define SU2_OR_MIN_BLOCKS 4
 #endif
 constexpr int kOrMinBlocks = SU2_OR_MIN_BLOCKS;  // blocks per SM the register budget is set for
 
