@@ -236,8 +236,10 @@ su2_status su2_set_timing(su2_lattice *lat, int enable);
  *   hardware base-2 logarithm that screens Creutz trials; n inputs x[n] ->
  *   y[n] (and y2[n] = cos for which = 2).  which = 4: x holds n quadruples
  *   (r1, r2, 1/(beta k), exp(-2 beta k)); y[i] = the screen's verdict (0
- *   reject, 1 accept, 2 undecided), y2[i] = the exact test's (0 or 1).  y2
- *   may be NULL unless which is 2 or 4. */
+ *   reject, 1 accept, 2 undecided), y2[i] = the exact test's (0 or 1).
+ *   which = 5: x holds n octuples (beta k, a', a, f'(z'), f'(z), u1, unused,
+ *   unused) of the learned step's Metropolis test; y[i] = the screened
+ *   verdict, y2[i] = the exact one.  y2 may be NULL unless which is 2, 4 or 5. */
 su2_status su2_selftest_philox(const uint32_t *ck, uint32_t *out, size_t n);
 su2_status su2_selftest_math(int which, const float *x, float *y, float *y2, size_t n);
 

@@ -127,7 +127,8 @@ __global__ void __launch_bounds__(kLearnThreads, kLearnMinBlocks) learned_phase_
         float4 sp_next = v_next;
         // ---- part 1
         nl = load_nu_eo<MU, OtherDir<MU, 1>::value>(p.links, p.g, xn, en, en_p, p.parity);
-        const bool accept = valid && learned::learned_accept(r, old, uniform01(w.y));
+        const bool ok = learned::learned_accept(r, old, uniform01(w.y), valid);
+        const bool accept = valid && ok;
         v_next = add_nu_terms(v_next, nl);
         if (MU == 2) sp_next = v_next;
         // ---- part 2

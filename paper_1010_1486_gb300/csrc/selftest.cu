@@ -2,6 +2,7 @@
 // counter generator and the series log / exp / sin-cos used by the heat bath.
 // They let the tests compare the device arithmetic with independent
 // implementations word for word.
+#include "learned.cuh"
 #include "su2_device.cuh"
 #include "su2_internal.h"
 
@@ -37,6 +38,12 @@ __global__ void math_selftest_kernel(int which, const float *__restrict__ x, flo
             y[i] = (float)creutz_screen(__fmaf_rn(r1, ome, e), r2, make_screen(ibk));
             float c;
             y2[i] = creutz_trial(r1, r2, ibk, e, ome, ibk == 0.0f, c) ? 1.0f : 0.0f;
+        } else if (which == 5) {
+            // octuple (beta k, a', a, f'(z'), f'(z), u1, -, -): the screened and
+            // the exact Metropolis verdicts of the learned step
+            const float *q = x + 8 * i;
+            y[i] = (float)learned::metropolis_screen(q[0], q[1], q[2], q[3], q[4], q[5]);
+            y2[i] = learned::metropolis_exact(q[0], q[1], q[2], q[3], q[4], q[5]) ? 1.0f : 0.0f;
         } else {
             float s, c;
             sincos_2pi(x[i], s, c);
@@ -96,10 +103,11 @@ su2_status su2_selftest_philox(const uint32_t *ck, uint32_t *out, size_t n)
 
 su2_status su2_selftest_math(int which, const float *x, float *y, float *y2, size_t n)
 {
-    const bool two = which == 2 || which == 4;
-    if (!x || !y || which < 0 || which > 4 || (two && !y2)) return SU2_E_INVAL;
+    const bool two = which == 2 || which == 4 || which == 5;
+    if (!x || !y || which < 0 || which > 5 || (two && !y2)) return SU2_E_INVAL;
     if (n == 0) return SU2_OK;
-    return run_with_buffers(x, (which == 4 ? 16 : 4) * n, y, 4 * n, two ? y2 : nullptr, two ? 4 * n : 0,
+    const size_t in_bytes = (which == 4 ? 16 : which == 5 ? 32 : 4) * n;
+    return run_with_buffers(x, in_bytes, y, 4 * n, two ? y2 : nullptr, two ? 4 * n : 0,
                             [which, n](char *in, char *o, char *o2, cudaStream_t s) {
                                 math_selftest_kernel<<<grid_for((int64_t)n, 256), 256, 0, s>>>(
                                     which, (const float *)in, (float *)o, (float *)o2, n);
