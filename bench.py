@@ -429,6 +429,18 @@ def compare_forms(args, dist, lat, su2, torch, stream, tau_int):
     return out
 
 
+def timed_batch(stream, torch, fn, k):
+    """ms per sweep of fn(k) on the batch's stream (CUDA events), after 3 untimed sweeps."""
+    fn(3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn(k)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / k
+
+
 def run_batched(args, dist, su2, torch):
     """64 independent lattices (8^4, 12^3x4, 16^3x6, 16^4, 24^3x8; beta in
     [1.5, 3]; cold start): one persistent cooperative launch per sweep,
@@ -443,6 +455,8 @@ def run_batched(args, dist, su2, torch):
     b = su2.su2_batch_create(cfg["ns"], cfg["nt"], cfg["beta"], cfg["seed"], cfg["start"], stream=stream)
     try:
         su2.su2_batch_sweep(b, 20)
+        # the fixed default launch (queue depth 4, all co-resident blocks) first
+        fixed_ms = timed_batch(stream, torch, lambda k: su2.su2_batch_generate(b, n, k, 1), 50)
         depth, grid = su2.su2_batch_autotune(b, 5)
         su2.su2_batch_generate(b, n, 5, 1)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -464,6 +478,7 @@ def run_batched(args, dist, su2, torch):
                         "cold start, plaquette and Polyakov loop of every lattice every sweep",
             "sites": sites, "value": value, "unit": UNIT, "sweeps_per_s": args.batched_steps / (ms * 1e-3),
             "ms_per_sweep": ms / args.batched_steps, "queue_depth": depth, "grid_blocks": grid,
+            "fixed_config_ms_per_sweep": fixed_ms,
             "cuda_graph": info["graphs"], "gpu_launches": args.batched_steps,
             "roofline": {"bound": "hbm", "kernel": "batch_sweep_kernel", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak,
@@ -545,9 +560,16 @@ def oracle_sample(seconds: float, label: str):
         if time.perf_counter() - t0 >= seconds:
             break
     dt = time.perf_counter() - t0
+    # one core, the paper's serial-CPU comparison: one even/odd phase (V/2 updates)
+    t1 = time.perf_counter()
+    oracle.heatbath_phase(NS, NT, BETA, SEED, steps, 0, 0, links, nthreads=1)
+    dt1 = time.perf_counter() - t1
     return {"value": steps * LINKS / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{label}: {steps} step(s) of the {NS}^4 beta={BETA} hot-start lattice "
-                      f"(one sweep over {threads} threads + plaquette + Polyakov loop), {dt:.1f} s"}
+                      f"(one sweep over {threads} threads + plaquette + Polyakov loop), {dt:.1f} s",
+            "single_core": {"value": (LINKS // 8) / dt1, "unit": UNIT, "cores": 1,
+                            "sample": f"one even/odd phase ({LINKS // 8} link updates) of the same lattice on "
+                                      f"one thread, {dt1:.1f} s"}}
 
 
 def run_reference(args, world: int):
