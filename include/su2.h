@@ -214,6 +214,22 @@ su2_status su2_generate_async(su2_lattice *lat, int nsweeps, int measure_every, 
                               double *poly);
 su2_status su2_sync(su2_lattice *lat);
 
+/* Link health (failure detection): counts the links with a non-finite
+ * component (*nonfinite) and those with | |a| - 1 | > tol (*off_norm; both
+ * pointers nullable).  Synchronous.  Returns SU2_E_NUMERIC if any link is
+ * non-finite, SU2_E_INVAL for tol < 0 or NaN.  Heat-bath links stay within
+ * about 3e-7 of unit norm; su2_reunitarize restores it. */
+su2_status su2_check_links(su2_lattice *lat, double tol, uint64_t *nonfinite, uint64_t *off_norm);
+
+/* Diagnostic cap on the a0 sampler's trials per link (Creutz and
+ * Kennedy-Pendleton heat-bath sweeps of this lattice; even, 2..4096, default
+ * 4096, where the chance of reaching it is below 0.8^4096).  A link that
+ * reaches it keeps its old value, and the call that reads the statistics
+ * (su2_generate, su2_heatbath_sweep with stats, su2_sync) returns
+ * SU2_E_SAMPLER with stats->sampler_failures set.  Creutz draws of the
+ * Kennedy-Pendleton sweep below beta k = 2 keep the default cap. */
+su2_status su2_set_trial_cap(su2_lattice *lat, int max_trials);
+
 /* Resumable state (sweep counter, seed, beta).  set_state requires matching extents. */
 su2_status su2_get_state(const su2_lattice *lat, su2_state *out);
 su2_status su2_set_state(su2_lattice *lat, const su2_state *in);

@@ -244,6 +244,17 @@ def heatbath_sweep(ns: int, nt: int, beta: float, seed: int, sweep: int, links: 
     return trials
 
 
+def heatbath_phase_kp(ns: int, nt: int, beta: float, seed: int, sweep: int, mu: int, parity: int,
+                      links: np.ndarray, nthreads: int = 1) -> int:
+    """One Kennedy-Pendleton phase in place; returns its trial count."""
+    t = ctypes.c_int64(0)
+    err = _load().orc_heatbath_phase_kp(ns, nt, beta, seed, sweep, mu, parity, _ptr(links), ctypes.byref(t),
+                                        nthreads)
+    if err:
+        raise RuntimeError(f"{err} links hit the trial cap")
+    return t.value
+
+
 def heatbath_sweep_kp(ns: int, nt: int, beta: float, seed: int, sweep: int, links: np.ndarray,
                       nthreads: int = 1) -> np.ndarray:
     """One sweep with the Kennedy-Pendleton sampler (Creutz below beta k = 2)."""

@@ -30,6 +30,7 @@ struct HbParams {
     float beta;
     uint32_t sweep;
     const uint32_t *sweep_dev;  // if non-NULL the sweep counter is read here (graph replays)
+    int max_blocks;             // trial cap / 2: Philox blocks a link may use before it keeps its old value
     unsigned long long *trial_slots;
     unsigned int *flags;
     const unsigned int *gate;  // if non-NULL and *gate == 1 the phase is left to the learned kernel
@@ -150,16 +151,17 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
         const uint4 w = philox_rk(make_uint4((uint32_t)eo, sweep, sw_creutz, (uint32_t)blk), p.rk);
         bool first_ok;
         float val;
-        const bool ok = creutz_pair(w, ibk, e, have, first_ok, val) && have;
+        const bool over = blk >= p.max_blocks;  // only with a cap of two trials
+        const bool ok = creutz_pair(w, ibk, e, have, first_ok, val) && have && !over;
         bool again = false;
         if (ok) {
             trials += (unsigned int)(2 * blk + (first_ok ? 1 : 2));
         } else if (have) {
-            if (blk + 1 < kMaxTrials / 2) {
+            if (!over && blk + 1 < p.max_blocks) {
                 again = true;
             } else {
                 atomicAdd(&p.flags[0], 1u);  // trial cap: the link keeps its old value
-                trials += (unsigned int)kMaxTrials;
+                trials += (unsigned int)(2 * p.max_blocks);
             }
         }
         push_retry(again, ut, ibk, e, eo, blk + 1, sp);
@@ -270,6 +272,7 @@ su2_status launch_hb_phase(su2_lattice *lat, int mu, int parity, uint32_t sweep,
     p.beta = (float)lat->beta;
     p.sweep = sweep;
     p.sweep_dev = lat->capturing ? lat->d_ctr : nullptr;
+    p.max_blocks = lat->max_trials / 2;
     p.trial_slots = lat->scratch.trials;
     p.flags = lat->scratch.flags;
     p.plaq = fused_slot(lat, mu, parity, 0);
@@ -441,6 +444,7 @@ static uint64_t generation_signature(const su2_lattice *lat)
     mix(lat->seed);
     mix((uint64_t)lat->sampler);
     mix((uint64_t)lat->overrelax);
+    mix((uint64_t)lat->max_trials);
     mix((uint64_t)(uintptr_t)lat->scratch.history);
     mix((uint64_t)lat->scratch.history_cap);
     return h | 1ull;  // never 0 (0 marks an empty slot)
@@ -594,6 +598,13 @@ su2_status su2_heatbath_sweep(su2_lattice *lat, int nsweeps, su2_stats *stats)
         if ((st = one_sweep(lat)) != SU2_OK) return st;
     lat->hb_log.used = 0;
     lat->or_log.used = 0;
+    return SU2_OK;
+}
+
+su2_status su2_set_trial_cap(su2_lattice *lat, int max_trials)
+{
+    if (!lat || max_trials < 2 || max_trials > kMaxTrials || (max_trials & 1)) return SU2_E_INVAL;
+    lat->max_trials = max_trials;
     return SU2_OK;
 }
 

@@ -33,6 +33,7 @@ struct KpParams {
     float beta;
     uint32_t sweep;
     const uint32_t *sweep_dev;  // if non-NULL the sweep counter is read here (graph replays)
+    int max_trials;             // trials a link may use before it keeps its old value
     unsigned long long *trial_slots;
     unsigned int *flags;
     const unsigned int *gate;  // skip the phase while *gate == 1 (learned sweeps)
@@ -104,10 +105,10 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
             const int eo = s_eo[wib][q];
             float a0 = 0.0f;
             int t = 1;
-            for (; t < kMaxTrials; ++t)
+            for (; t < p.max_trials; ++t)
                 if (kp_trial(philox_rk(make_uint4((uint32_t)eo, sweep, sw_kp, (uint32_t)t), p.rk), two_bk, a0))
                     break;
-            if (t < kMaxTrials) {
+            if (t < p.max_trials) {
                 const float4 out =
                     direction_update(a0, ut, philox_rk(make_uint4((uint32_t)eo, sweep, sw_dir, 0u), p.rk));
                 p.links[link_index(p.g, MU, p.parity, eo)] = out;
@@ -115,7 +116,7 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
                 trials += (unsigned int)(t + 1);
             } else {
                 atomicAdd(&p.flags[0], 1u);  // trial cap: the link keeps its old value
-                trials += (unsigned int)kMaxTrials;
+                trials += (unsigned int)p.max_trials;
             }
         }
         __syncwarp();
@@ -243,6 +244,7 @@ su2_status launch_kp_phase(su2_lattice *lat, int mu, int parity, uint32_t sweep,
     p.beta = (float)lat->beta;
     p.sweep = sweep;
     p.sweep_dev = lat->capturing ? lat->d_ctr : nullptr;
+    p.max_trials = lat->max_trials;
     p.trial_slots = lat->scratch.trials;
     p.flags = lat->scratch.flags;
     p.gate = gate;

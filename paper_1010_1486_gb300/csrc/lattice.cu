@@ -226,6 +226,31 @@ su2_status collect_stats(su2_lattice *lat, su2_stats *stats, uint64_t sweeps)
     return SU2_OK;
 }
 
+// Counts links with a non-finite component, and links with | |a| - 1 | > tol
+// (|a|^2 summed as the fixed chain of the quaternion norm, in binary32).
+__global__ void check_links_kernel(const float4 *__restrict__ L, int64_t n, float tol,
+                                   unsigned long long *__restrict__ counts)
+{
+    unsigned long long bad = 0, off = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 a = __ldg(L + i);
+        if (!(isfinite(a.x) && isfinite(a.y) && isfinite(a.z) && isfinite(a.w))) {
+            ++bad;
+        } else {
+            const float r = __fsqrt_rn(qnorm2(a));
+            if (fabsf(__fsub_rn(r, 1.0f)) > tol) ++off;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        bad += __shfl_down_sync(0xffffffffu, bad, o);
+        off += __shfl_down_sync(0xffffffffu, off, o);
+    }
+    if ((threadIdx.x & 31) == 0 && (bad | off)) {
+        atomicAdd(counts, bad);
+        atomicAdd(counts + 1, off);
+    }
+}
+
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace su2
@@ -506,6 +531,33 @@ su2_status su2_sync(su2_lattice *lat)
         SU2_CUDA(cudaStreamSynchronize(lat->stream));
         set_last_error("heat-bath sampler hit its trial cap");
         return SU2_E_SAMPLER;
+    }
+    return SU2_OK;
+}
+
+su2_status su2_check_links(su2_lattice *lat, double tol, uint64_t *nonfinite, uint64_t *off_norm)
+{
+    if (!lat || !(tol >= 0.0)) return SU2_E_INVAL;
+    DeviceGuard guard(lat->device);
+    unsigned long long *d = (unsigned long long *)device_alloc(2 * sizeof(unsigned long long), lat->device,
+                                                               lat->stream);
+    if (!d) return SU2_E_NOMEM;
+    unsigned long long h[2] = {0ull, 0ull};
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof h, lat->stream);
+    if (e == cudaSuccess) {
+        check_links_kernel<<<grid_for(4 * lat->vol, 256, 152 * 8), 256, 0, lat->stream>>>(lat->links, 4 * lat->vol,
+                                                                                          (float)tol, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, lat->stream);
+    device_free(d, 2 * sizeof(unsigned long long), lat->device, lat->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lat->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "su2_check_links");
+    if (nonfinite) *nonfinite = h[0];
+    if (off_norm) *off_norm = h[1];
+    if (h[0]) {
+        set_last_error("non-finite link components");
+        return SU2_E_NUMERIC;
     }
     return SU2_OK;
 }

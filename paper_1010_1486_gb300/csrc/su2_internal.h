@@ -60,6 +60,7 @@ struct su2_lattice {
     uint64_t seed = 0;
     uint32_t sweep = 0;
     int sampler = 0;  // SU2_SAMPLER_CREUTZ or SU2_SAMPLER_KP
+    int max_trials = 4096;  // sampler trials per link before it keeps its old value (su2_set_trial_cap)
     int device = 0;
     cudaStream_t stream = nullptr;
 

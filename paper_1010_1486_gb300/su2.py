@@ -93,6 +93,8 @@ _SIGS = {
     "su2_set_links_async": [_P, _P],
     "su2_generate_async": [_P, _i32, _i32, _i32, _P, _P],
     "su2_sync": [_P],
+    "su2_check_links": [_P, _f64, ctypes.POINTER(_u64), ctypes.POINTER(_u64)],
+    "su2_set_trial_cap": [_P, _i32],
     "su2_get_state": [_P, ctypes.POINTER(su2_state)],
     "su2_set_state": [_P, ctypes.POINTER(su2_state)],
     "su2_set_beta": [_P, _f64],
@@ -302,6 +304,18 @@ def su2_generate_async(lat: int, nsweeps: int, measure_every: int = 1, reunit_ev
 
 def su2_sync(lat: int) -> None:
     _check(_lib.su2_sync(lat), "su2_sync")
+
+
+def su2_check_links(lat: int, tol: float = 1e-6):
+    """(non-finite links, links with | |a| - 1 | > tol); raises SU2Error
+    (SU2_E_NUMERIC) if any link is non-finite."""
+    nf, off = _u64(), _u64()
+    _check(_lib.su2_check_links(lat, float(tol), ctypes.byref(nf), ctypes.byref(off)), "su2_check_links")
+    return nf.value, off.value
+
+
+def su2_set_trial_cap(lat: int, max_trials: int) -> None:
+    _check(_lib.su2_set_trial_cap(lat, int(max_trials)), "su2_set_trial_cap")
 
 
 def su2_get_state(lat: int) -> dict:
