@@ -1,4 +1,4 @@
-"""Host driver of the learned proposal: initial weights, and the pipeline
+"""Host side of the learned proposal: initial weights, and the pipeline
 collect pairs on the lattice -> train on the GPU -> install the proposal.
 Every computation runs in libsu2's kernels; this module only sequences calls.
 """
