@@ -60,7 +60,7 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--e2e-in-flight", type=int, default=4, help="configurations in flight in the e2e pipeline")
-    ap.add_argument("--tau-sweeps", type=int, default=4000,
+    ap.add_argument("--tau-sweeps", type=int, default=8000,
                     help="sweeps per form for tau_int and the plaquette comparison (0 = skip)")
     ap.add_argument("--therm", type=int, default=1500, help="thermalisation sweeps before the form comparison")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sample length")
@@ -372,7 +372,7 @@ def compare_forms(args, dist, lat, su2, torch, stream, tau_int):
         r = out[form]["roofline"]
         r["frac"] = r["achieved"] / peak
     if args.tau_sweeps > 0:
-        nblk = 8
+        nblk = 16  # interleaved blocks per form: the spread of their means gives the plaquette check's error
         per = max(50, args.tau_sweeps // nblk)
         plain_blocks, learned_blocks, kp_blocks, or_blocks = [], [], [], []
         per_or = max(50, per // (N_OR + 1) * 2)
