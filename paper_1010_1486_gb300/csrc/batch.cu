@@ -261,11 +261,11 @@ __device__ void batch_phase(const BatchParams &bp, int parity, uint32_t sweep, C
             const int e = min(cur, last);
             const Coord x = eo_to_coord(g, e, parity);
             const int e_p = eo_fwd<MU>(g, x, e);
-            v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 0>::value>(links, g, x, e, e_p, parity));
+            v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 0>::value, false>(links, g, x, e, e_p, parity));
             if (MU == 1) sp_cur = v_cur;
-            v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 1>::value>(links, g, x, e, e_p, parity));
+            v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 1>::value, false>(links, g, x, e, e_p, parity));
             if (MU == 2) sp_cur = v_cur;
-            v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 2>::value>(links, g, x, e, e_p, parity));
+            v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 2>::value, false>(links, g, x, e, e_p, parity));
             if (MU == 3) sp_cur = v_cur;
         }
 #pragma unroll 1
@@ -276,13 +276,13 @@ __device__ void batch_phase(const BatchParams &bp, int parity, uint32_t sweep, C
             const Coord xn = eo_to_coord(g, en, parity);
             const int en_p = eo_fwd<MU>(g, xn, en);
             // ---- part 0
-            NuLinks nl = load_nu_eo<MU, OtherDir<MU, 0>::value>(links, g, xn, en, en_p, parity);
+            NuLinks nl = load_nu_eo<MU, OtherDir<MU, 0>::value, false>(links, g, xn, en, en_p, parity);
             const DrawSetup ds = prepare_draw(v_cur, beta);
             const uint4 w = philox_key(make_uint4((uint32_t)cur, sweep, sw_creutz, 0u), k0, k1);
             float4 v_next = add_nu_terms(make_float4(0.0f, 0.0f, 0.0f, 0.0f), nl);
             float4 sp_next = v_next;
             // ---- part 1
-            nl = load_nu_eo<MU, OtherDir<MU, 1>::value>(links, g, xn, en, en_p, parity);
+            nl = load_nu_eo<MU, OtherDir<MU, 1>::value, false>(links, g, xn, en, en_p, parity);
             {
                 bool first_ok;
                 float val;
@@ -295,7 +295,7 @@ __device__ void batch_phase(const BatchParams &bp, int parity, uint32_t sweep, C
             v_next = add_nu_terms(v_next, nl);
             if (MU == 2) sp_next = v_next;
             // ---- part 2
-            nl = load_nu_eo<MU, OtherDir<MU, 2>::value>(links, g, xn, en, en_p, parity);
+            nl = load_nu_eo<MU, OtherDir<MU, 2>::value, false>(links, g, xn, en, en_p, parity);
             flush_done();
             v_next = add_nu_terms(v_next, nl);
             if (MU == 3) sp_next = v_next;
@@ -351,11 +351,11 @@ __device__ void batch_measure_rounds(const BatchParams &bp)
             if (s < 2 * g.vh) {
                 const int parity = s >= g.vh;
                 const int eo = s - (parity ? g.vh : 0);
-                val = (double)site_plaquette(d->links, g, eo_to_coord(g, eo, parity), eo, parity);
+                val = (double)site_plaquette<false>(d->links, g, eo_to_coord(g, eo, parity), eo, parity);
             }
         } else {
             const int xs = (local - d->nplaq_rounds) * 32 + lane;
-            if (xs < g.vs) val = (double)site_polyakov(d->links, g, xs);
+            if (xs < g.vs) val = (double)site_polyakov<false>(d->links, g, xs);
         }
         val = warp_sum(val);
         if (lane == 0) bp.round_partials[mr] = val;

@@ -2,6 +2,7 @@
 // the reduction kernels.
 #pragma once
 
+#include "link_load.cuh"
 #include "su2_device.cuh"
 
 namespace su2 {
@@ -28,6 +29,7 @@ __device__ __forceinline__ double block_sum(double v)
 
 // Sum over the six planes mu < nu, in the order (0,1),(0,2),(0,3),(1,2),(1,3),
 // (2,3), of (1/2) Tr U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag.
+template <bool NC = true>
 __device__ __forceinline__ float site_plaquette(const float4 *__restrict__ L, const Geom &g, const Coord &x,
                                                 int eo, int parity)
 {
@@ -36,7 +38,7 @@ __device__ __forceinline__ float site_plaquette(const float4 *__restrict__ L, co
     int e_fwd[4];
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
-        u[mu] = __ldg(L + link_index(g, mu, parity, eo));
+        u[mu] = load_link<NC>(L + link_index(g, mu, parity, eo));
         e_fwd[mu] = lex_fwd(g, x.lex, x.c[mu], mu) >> 1;
     }
     float sum = 0.0f;
@@ -44,8 +46,8 @@ __device__ __forceinline__ float site_plaquette(const float4 *__restrict__ L, co
     for (int mu = 0; mu < 4; ++mu)
 #pragma unroll
         for (int nu = mu + 1; nu < 4; ++nu) {
-            const float4 b = __ldg(L + link_index(g, nu, op, e_fwd[mu]));
-            const float4 c = __ldg(L + link_index(g, mu, op, e_fwd[nu]));
+            const float4 b = load_link<NC>(L + link_index(g, nu, op, e_fwd[mu]));
+            const float4 c = load_link<NC>(L + link_index(g, mu, op, e_fwd[nu]));
             const float4 t = qmul(qmul(u[mu], b), qdag(c));
             sum = __fadd_rn(sum, qmul_re(t, qdag(u[nu])));
         }
@@ -78,6 +80,7 @@ __device__ __forceinline__ void finish_reduction(double block_total, double *__r
 
 // (1/2) Tr of U_3(x,0) U_3(x,1) ... U_3(x,Nt-1), multiplied left to right,
 // for spatial site xs (lexicographic in x, y, z).
+template <bool NC = true>
 __device__ __forceinline__ float site_polyakov(const float4 *__restrict__ L, const Geom &g, int xs)
 {
     const int rest = xs / g.ns;
@@ -85,7 +88,7 @@ __device__ __forceinline__ float site_polyakov(const float4 *__restrict__ L, con
     const int y = rest % g.ns;
     const int z = rest / g.ns;
     const int p0 = (x + y + z) & 1;
-    float4 p = __ldg(L + link_index(g, 3, p0, xs >> 1));
+    float4 p = load_link<NC>(L + link_index(g, 3, p0, xs >> 1));
     int t = 1;
     // eight loads in flight, then the eight products in t order
     for (; t + 8 <= g.nt; t += 8) {
@@ -93,14 +96,14 @@ __device__ __forceinline__ float site_polyakov(const float4 *__restrict__ L, con
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int64_t lex = (int64_t)(t + j) * g.vs + xs;
-            q[j] = __ldg(L + link_index(g, 3, (p0 + t + j) & 1, (int)(lex >> 1)));
+            q[j] = load_link<NC>(L + link_index(g, 3, (p0 + t + j) & 1, (int)(lex >> 1)));
         }
 #pragma unroll
         for (int j = 0; j < 8; ++j) p = qmul(p, q[j]);
     }
     for (; t < g.nt; ++t) {
         const int64_t lex = (int64_t)t * g.vs + xs;
-        p = qmul(p, __ldg(L + link_index(g, 3, (p0 + t) & 1, (int)(lex >> 1))));
+        p = qmul(p, load_link<NC>(L + link_index(g, 3, (p0 + t) & 1, (int)(lex >> 1))));
     }
     return p.x;
 }

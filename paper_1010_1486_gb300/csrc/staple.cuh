@@ -2,6 +2,7 @@
 // (one thread per link), shared by the batched and learned kernels.
 #pragma once
 
+#include "link_load.cuh"
 #include "su2_device.cuh"
 
 namespace su2 {
@@ -65,8 +66,9 @@ __device__ __forceinline__ int eo_bwd_offset(const Geom &g, const Coord &x)
     return x.c[NU] == 0 ? (g.wrap[NU] >> 1) : -(g.stride[NU] >> 1);
 }
 
-// load_nu with the indices above; eo = index of x, e_p = index of x + mu.
-template <int MU, int NU>
+// The six links of direction nu with the indices above; eo = index of x,
+// e_p = index of x + mu.  NC: read-only path (see load_link).
+template <int MU, int NU, bool NC = true>
 __device__ __forceinline__ NuLinks load_nu_eo(const float4 *__restrict__ L, const Geom &g, const Coord &x, int eo,
                                               int e_p, int parity)
 {
@@ -76,12 +78,12 @@ __device__ __forceinline__ NuLinks load_nu_eo(const float4 *__restrict__ L, cons
     const float4 *__restrict__ mu_other = L + (uint32_t)(2 * MU + op) * (uint32_t)g.vh;
     const int off_m = eo_bwd_offset<NU>(g, x);
     NuLinks n;
-    n.nu_xp = __ldg(nu_other + (uint32_t)e_p);
-    n.mu_xn = __ldg(mu_other + (uint32_t)eo_fwd<NU>(g, x, eo));
-    n.nu_x = __ldg(nu_same + (uint32_t)eo);
-    n.nu_xpm = __ldg(nu_same + (uint32_t)(e_p + off_m));
-    n.mu_xm = __ldg(mu_other + (uint32_t)(eo + off_m));
-    n.nu_xm = __ldg(nu_other + (uint32_t)(eo + off_m));
+    n.nu_xp = load_link<NC>(nu_other + (uint32_t)e_p);
+    n.mu_xn = load_link<NC>(mu_other + (uint32_t)eo_fwd<NU>(g, x, eo));
+    n.nu_x = load_link<NC>(nu_same + (uint32_t)eo);
+    n.nu_xpm = load_link<NC>(nu_same + (uint32_t)(e_p + off_m));
+    n.mu_xm = load_link<NC>(mu_other + (uint32_t)(eo + off_m));
+    n.nu_xm = load_link<NC>(nu_other + (uint32_t)(eo + off_m));
     return n;
 }
 
