@@ -31,7 +31,11 @@
  *     the parity of a site is (x+y+z+t) mod 2.
  *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key = seed and
  *     counter (even/odd site index, sweep, stream kind/parity/mu, block), so a
- *     run is a pure function of (start, seed, beta, sweep count).
+ *     run is a pure function of (start, seed, beta, sweep count).  A 32-bit
+ *     word w becomes the uniform ((w >> 8) + 1) 2^-24 in (0, 1], or, where the
+ *     uniform is the argument of a logarithm (Creutz's x, the
+ *     Kennedy-Pendleton exponentials), w 2^-32 + 2^-33 rounded once, in
+ *     [2^-33, 1], so that -ln x is not cut at 24 ln 2.
  */
 #ifndef SU2_H
 #define SU2_H
@@ -126,8 +130,9 @@ su2_status su2_heatbath_phase(su2_lattice *lat, int mu, int parity);
  * On a lattice created with a stream (not the legacy default stream) and
  * with timing off, each sweep is replayed from a CUDA graph captured on first
  * use (the sweep counter and the measurement slot are kept on the device;
- * the graph is captured again when the sampler, beta, seed, over-relaxation
- * or the measurement buffer change); the chain is the same bit for bit. */
+ * the graph is captured again when the sampler, beta, seed, over-relaxation,
+ * trial cap or the measurement buffer change); the chain is the same bit for
+ * bit. */
 su2_status su2_generate(su2_lattice *lat, int nsweeps, int measure_every, int reunit_every, double *plaq,
                         double *poly, su2_stats *stats);
 
