@@ -59,6 +59,24 @@ def test_trial_cap_keeps_the_old_link_and_reports(sampler, ns, cap):
         su2.su2_destroy(h)
 
 
+def test_trial_cap_change_recaptures_the_generation_graph():
+    """On a lattice with a stream su2_generate replays a captured graph; the
+    cap is part of its signature, so lowering it must take effect at once."""
+    import torch
+
+    h = su2.su2_create(8, 8, 6.0, 7, su2.SU2_COLD, stream=torch.cuda.Stream())
+    try:
+        su2.su2_generate(h, 2, 1, 0)  # captured and replayed at the default cap
+        su2.su2_set_trial_cap(h, 2)
+        with pytest.raises(su2.SU2Error) as err:
+            su2.su2_generate(h, 1, 1, 0)
+        assert err.value.status == SU2_E_SAMPLER
+        su2.su2_set_trial_cap(h, 4096)
+        su2.su2_generate(h, 2, 1, 0)
+    finally:
+        su2.su2_destroy(h)
+
+
 def test_trial_cap_arguments():
     h = su2.su2_create(4, 4, 2.0, 1, su2.SU2_COLD)
     try:
