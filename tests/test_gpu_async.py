@@ -103,6 +103,32 @@ def test_three_configurations_in_flight_equal_three_sequential_chains():
             su2.su2_destroy(h)
 
 
+@pytest.mark.parametrize("use_stream", [True, False])
+def test_async_with_pageable_buffers_and_the_default_stream(use_stream):
+    """Pageable host memory (staged by the driver) and a lattice on the legacy
+    default stream give the same chain as the synchronous calls."""
+    ns, nt, beta, seed = 6, 4, 2.4, 9
+    x0 = start_links(ns, nt, 3)
+    a = su2.su2_create(ns, nt, beta, seed, su2.SU2_COLD)
+    b = su2.su2_create(ns, nt, beta, seed, su2.SU2_COLD, stream=torch.cuda.Stream() if use_stream else None)
+    try:
+        su2.su2_set_links(a, x0)
+        p_sync, _, _ = su2.su2_generate(a, 3, 1, 0)
+        y_sync = su2.su2_get_links(a, ns, nt)
+        xin = x0.copy()                       # ordinary numpy memory
+        yout = np.empty_like(x0)
+        plaq = np.zeros(3)
+        su2.su2_set_links_async(b, xin)
+        su2.su2_generate_async(b, 3, 1, 0, plaq, None)
+        su2.su2_get_links_async(b, yout)
+        su2.su2_sync(b)
+        assert np.array_equal(yout.view(np.uint32), y_sync.view(np.uint32))
+        assert np.array_equal(plaq, p_sync)
+    finally:
+        su2.su2_destroy(a)
+        su2.su2_destroy(b)
+
+
 def test_async_calls_check_their_arguments():
     h = su2.su2_create(4, 4, 2.0, 1, su2.SU2_COLD)
     try:
