@@ -386,13 +386,26 @@ def compare_forms(args, dist, lat, su2, torch, stream, tau_int):
             su2.su2_set_overrelax(lat, 0)
             su2.su2_set_sampler(lat, su2.SU2_SAMPLER_CREUTZ)
         plain_blocks.append(su2.su2_generate(lat, per, 1, 0)[0].copy())
+        # The 48^4 lattice still drifts slowly (the plaquette rises by about
+        # 2e-7 per round of blocks), so each block is compared with the plain
+        # blocks around it interpolated at its own centre, counted in sweeps
+        # (a compound sweep is 1 + N_OR sweeps): the learned block sits at
+        # f_l, the over-relaxation block at f_o of the way from one plain
+        # block's centre to the next.
+        span = 3 * per + (N_OR + 1) * per_or
+        f_l = per / span
+        f_o = (2.5 * per + 0.5 * (N_OR + 1) * per_or) / span
+
+        def plain_at(k, f):
+            a, b = plain_blocks[k].mean(), plain_blocks[k + 1].mean()
+            return a + f * (b - a)
+
         tau_o, dtau_o = tau_int(or_blocks, own_means=True)[:2]
         out["kp_overrelax"]["tau_int"] = float(tau_o)
         out["kp_overrelax"]["tau_int_err"] = float(dtau_o)
         out["kp_overrelax"]["tau_int_unit"] = "compound sweeps"
         out["kp_overrelax"]["value_tau_adjusted"] = compound_per_s * 4 * VOL / (2 * tau_o)
-        d_o = np.array([or_blocks[k].mean() - 0.5 * (plain_blocks[k].mean() + plain_blocks[k + 1].mean())
-                        for k in range(nblk)])
+        d_o = np.array([or_blocks[k].mean() - plain_at(k, f_o) for k in range(nblk)])
         se_o = d_o.std(ddof=1) / np.sqrt(nblk)
         out["kp_overrelax"]["plaquette_minus_plain"] = float(d_o.mean())
         out["kp_overrelax"]["plaquette_sigma"] = float(d_o.mean() / se_o) if se_o > 0 else None
@@ -404,8 +417,7 @@ def compare_forms(args, dist, lat, su2, torch, stream, tau_int):
         out["plain_kennedy_pendleton"]["tau_int"] = float(tau_k)
         out["plain_kennedy_pendleton"]["tau_int_err"] = float(dtau_k)
         out["plain_kennedy_pendleton"]["value_tau_adjusted"] = value_kp / (2 * tau_k)
-        d = np.array([learned_blocks[k].mean() - 0.5 * (plain_blocks[k].mean() + plain_blocks[k + 1].mean())
-                      for k in range(nblk)])
+        d = np.array([learned_blocks[k].mean() - plain_at(k, f_l) for k in range(nblk)])
         se = d.std(ddof=1) / np.sqrt(nblk)
         out["plain"]["tau_int"] = float(tau_p)
         out["plain"]["tau_int_err"] = float(dtau_p)
@@ -413,7 +425,7 @@ def compare_forms(args, dist, lat, su2, torch, stream, tau_int):
         out["learned"]["tau_int_err"] = float(dtau_l)
         out["plain"]["value_tau_adjusted"] = value_plain / (2 * tau_p)
         out["learned"]["value_tau_adjusted"] = value_learned / (2 * tau_l)
-        out["plaquette_check"] = {"blocks": nblk, "sweeps_per_block": per,
+        out["plaquette_check"] = {"blocks": nblk, "sweeps_per_block": per, "reference_position": f_l,
                                   "plain_mean": float(np.mean([b.mean() for b in plain_blocks])),
                                   "learned_mean": float(np.mean([b.mean() for b in learned_blocks])),
                                   "learned_minus_plain": float(d.mean()), "stderr": float(se),
