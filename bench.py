@@ -288,8 +288,11 @@ def compare_forms(args, dist, lat, su2, torch, stream, tau_int):
     48^4 lattice.  After `therm` more sweeps: (beta k, a0) pairs from the plain
     sampler, training on the GPU, then both forms timed back to back, then
     interleaved blocks plain / learned / plain ... for tau_int and the
-    plaquette: every learned block is compared with the mean of the plain
-    blocks around it, so a slow drift of the lattice cancels."""
+    plaquette: every learned block is compared with the plain blocks around
+    it, interpolated at its own position (analysis.interleaved_offset), so a
+    slow drift of the lattice cancels."""
+    from paper_1010_1486_gb300.analysis import interleaved_offset
+
     import numpy as np
 
     from paper_1010_1486_gb300 import learn
@@ -396,19 +399,15 @@ def compare_forms(args, dist, lat, su2, torch, stream, tau_int):
         f_l = per / span
         f_o = (2.5 * per + 0.5 * (N_OR + 1) * per_or) / span
 
-        def plain_at(k, f):
-            a, b = plain_blocks[k].mean(), plain_blocks[k + 1].mean()
-            return a + f * (b - a)
-
         tau_o, dtau_o = tau_int(or_blocks, own_means=True)[:2]
         out["kp_overrelax"]["tau_int"] = float(tau_o)
         out["kp_overrelax"]["tau_int_err"] = float(dtau_o)
         out["kp_overrelax"]["tau_int_unit"] = "compound sweeps"
         out["kp_overrelax"]["value_tau_adjusted"] = compound_per_s * 4 * VOL / (2 * tau_o)
-        d_o = np.array([or_blocks[k].mean() - plain_at(k, f_o) for k in range(nblk)])
-        se_o = d_o.std(ddof=1) / np.sqrt(nblk)
-        out["kp_overrelax"]["plaquette_minus_plain"] = float(d_o.mean())
-        out["kp_overrelax"]["plaquette_sigma"] = float(d_o.mean() / se_o) if se_o > 0 else None
+        plain_means = [b.mean() for b in plain_blocks]
+        m_o, se_o = interleaved_offset([b.mean() for b in or_blocks], plain_means, f_o)
+        out["kp_overrelax"]["plaquette_minus_plain"] = m_o
+        out["kp_overrelax"]["plaquette_sigma"] = m_o / se_o if se_o > 0 else None
         # blocks of one form are replicas of its chain: pooled Gamma method,
         # each block about its own mean (the 48^4 lattice still drifts slowly)
         tau_p, dtau_p = tau_int(plain_blocks, own_means=True)[:2]
@@ -417,8 +416,7 @@ def compare_forms(args, dist, lat, su2, torch, stream, tau_int):
         out["plain_kennedy_pendleton"]["tau_int"] = float(tau_k)
         out["plain_kennedy_pendleton"]["tau_int_err"] = float(dtau_k)
         out["plain_kennedy_pendleton"]["value_tau_adjusted"] = value_kp / (2 * tau_k)
-        d = np.array([learned_blocks[k].mean() - plain_at(k, f_l) for k in range(nblk)])
-        se = d.std(ddof=1) / np.sqrt(nblk)
+        m_l, se = interleaved_offset([b.mean() for b in learned_blocks], plain_means, f_l)
         out["plain"]["tau_int"] = float(tau_p)
         out["plain"]["tau_int_err"] = float(dtau_p)
         out["learned"]["tau_int"] = float(tau_l)
@@ -428,8 +426,8 @@ def compare_forms(args, dist, lat, su2, torch, stream, tau_int):
         out["plaquette_check"] = {"blocks": nblk, "sweeps_per_block": per, "reference_position": f_l,
                                   "plain_mean": float(np.mean([b.mean() for b in plain_blocks])),
                                   "learned_mean": float(np.mean([b.mean() for b in learned_blocks])),
-                                  "learned_minus_plain": float(d.mean()), "stderr": float(se),
-                                  "sigma": float(d.mean() / se) if se > 0 else None}
+                                  "learned_minus_plain": m_l, "stderr": se,
+                                  "sigma": m_l / se if se > 0 else None}
         out["value_tau_adjusted"] = {"plain": out["plain"]["value_tau_adjusted"],
                                      "plain_kennedy_pendleton": out["plain_kennedy_pendleton"]["value_tau_adjusted"],
                                      "learned": out["learned"]["value_tau_adjusted"],

@@ -88,6 +88,23 @@ def tau_int(series, s_factor: float = 1.5, own_means: bool = False):
     return tau, dtau, window, err_mean
 
 
+def interleaved_offset(test_means, ref_means, position: float):
+    """Offset of one form against a reference form from interleaved blocks:
+    block k of the test form runs between reference blocks k and k + 1, its
+    centre `position` (0..1) of the way from the centre of reference block k
+    to that of block k + 1.  Each test block is compared with the reference
+    interpolated linearly at its centre, so a slow linear drift of the chain
+    cancels (the midpoint of the two reference blocks would leave a bias of
+    (position - 1/2) times the drift per round).  Returns (mean offset, its
+    standard error from the spread of the per-block offsets)."""
+    t = np.asarray(test_means, dtype=np.float64)
+    r = np.asarray(ref_means, dtype=np.float64)
+    if r.size != t.size + 1 or t.size < 2:
+        raise ValueError("need n >= 2 test blocks and n + 1 reference blocks")
+    d = t - (r[:-1] + position * (r[1:] - r[:-1]))
+    return float(d.mean()), float(d.std(ddof=1) / math.sqrt(d.size))
+
+
 def effective_potential(w) -> np.ndarray:
     """Static-potential estimates from Wilson loops W[R-1, T-1]:
     V_eff(R, T) = log(W(R, T) / W(R, T+1)), shape (rmax, tmax - 1).  For large
