@@ -260,7 +260,12 @@ su2_status su2_set_timing(su2_lattice *lat, int enable);
  *   reject, 1 accept, 2 undecided), y2[i] = the exact test's (0 or 1).
  *   which = 5: x holds n octuples (beta k, a', a, f'(z'), f'(z), u1, unused,
  *   unused) of the learned step's Metropolis test; y[i] = the screened
- *   verdict, y2[i] = the exact one.  y2 may be NULL unless which is 2, 4 or 5. */
+ *   verdict, y2[i] = the exact one.  which = 6: x holds n pairs (beta k,
+ *   w) with w a 32-bit Philox word stored in the float's bits; y[i] = the
+ *   Creutz trial variable x = e + r1 (1 - e), r1 the log uniform of w,
+ *   y2[i] = that trial's candidate a0 (Sec. 2), with e = exp(-2 beta k) as
+ *   the heat-bath kernels set it up.  y2 may be NULL unless which is 2, 4, 5
+ *   or 6. */
 su2_status su2_selftest_philox(const uint32_t *ck, uint32_t *out, size_t n);
 su2_status su2_selftest_math(int which, const float *x, float *y, float *y2, size_t n);
 

@@ -83,6 +83,7 @@ def _load():
             "orc_reunitarize": (None, [i32, i32, P]),
             "orc_max_threads": (i32, []),
             "orc_creutz_a0_v": (None, [f32, u64, u32, u32, i64, P, P]),
+            "orc_creutz_x_a0_v": (None, [P, P, i64, P, P]),
             "orc_heatbath_link_v": (None, [f32, P, u64, u32, u32, i32, i32, i64, P, P]),
             "orc_heatbath_sweep_kp": (i64, [i32, i32, f64, u64, u32, P, P, i32]),
             "orc_heatbath_phase_kp": (i64, [i32, i32, f64, u64, u32, i32, i32, P, ctypes.POINTER(i64), i32]),
@@ -221,6 +222,19 @@ def creutz_a0_many(bk: float, seed: int, n: int, eo0: int = 0, sweep: int = 0):
     t = np.zeros(n, dtype=np.int32)
     _load().orc_creutz_a0_v(bk, seed, eo0, sweep, n, _ptr(a0), _ptr(t))
     return a0, t
+
+
+def creutz_x_a0(bk, w):
+    """Single Creutz trials: for beta k = bk[i] and first Philox word w[i],
+    x = e + r1 (1 - e) and the candidate a0 (clamped), as the heat-bath link
+    forms them."""
+    bk = np.ascontiguousarray(bk, dtype=np.float32)
+    w = np.ascontiguousarray(w, dtype=np.uint32)
+    assert bk.shape == w.shape
+    x = np.empty_like(bk)
+    a0 = np.empty_like(bk)
+    _load().orc_creutz_x_a0_v(_ptr(bk), _ptr(w), bk.size, _ptr(x), _ptr(a0))
+    return x, a0
 
 
 def heatbath_link_many(beta: float, v, seed: int, eo: int, parity: int, mu: int, n: int, sweep0: int = 0):

@@ -375,6 +375,45 @@ void orc_staple(int ns, int nt, const float *links, int64_t s, int mu, float v[4
 /* ------------------------------------------------------------------------ */
 #define ORC_MAX_TRIALS 4096
 
+/* What a link's Creutz trials need from beta k (Sec. 2): e = exp(-2 beta k)
+ * (0 on the Haar branch and above beta k = 43), 1 - e and 1/(beta k). */
+struct creutz_setup {
+    int haar;
+    float e, one_minus_e, inv_bk;
+};
+
+static struct creutz_setup creutz_prepare(float bk)
+{
+    struct creutz_setup c;
+    c.haar = bk < 1e-6f;
+    c.e = 0.0f;
+    if (!c.haar && bk <= 43.0f) c.e = orc_expf(-2.0f * bk);
+    c.one_minus_e = 1.0f - c.e;
+    /* a0 = 1 + ln(x)/(beta k) is evaluated as 1 + ln(x) * (1/(beta k)) with
+     * the reciprocal rounded once per link (Sec. 2 fixes the formula, not its
+     * rounding; one division per link instead of one per trial) */
+    c.inv_bk = c.haar ? 0.0f : 1.0f / bk;
+    return c;
+}
+
+/* The candidate a0 of one trial from its first uniform r1, clamped to
+ * [-1, 1]; *x_out gets x = e + r1 (1 - e) (r1 itself on the Haar branch). */
+static float creutz_candidate(const struct creutz_setup *c, float r1, float *x_out)
+{
+    float cand;
+    if (c->haar) {
+        *x_out = r1;
+        cand = 2.0f * r1 - 1.0f;
+    } else {
+        float x = fmaf(r1, c->one_minus_e, c->e);
+        *x_out = x;
+        cand = 1.0f + orc_logf(x) * c->inv_bk;
+    }
+    if (cand < -1.0f) cand = -1.0f;
+    if (cand > 1.0f) cand = 1.0f;
+    return cand;
+}
+
 int orc_heatbath_link(float beta, const float v[4], uint64_t seed, uint32_t eo, uint32_t sweep,
                       int parity, int mu, float out[4])
 {
@@ -389,15 +428,7 @@ int orc_heatbath_link(float beta, const float v[4], uint64_t seed, uint32_t eo, 
     } else {
         ut[0] = 1.0f; ut[1] = 0.0f; ut[2] = 0.0f; ut[3] = 0.0f;
     }
-    float bk = beta * k;
-    int haar = bk < 1e-6f;
-    float e = 0.0f;
-    if (!haar && bk <= 43.0f) e = orc_expf(-2.0f * bk);
-    float one_minus_e = 1.0f - e;
-    /* a0 = 1 + ln(x)/(beta k) is evaluated as 1 + ln(x) * (1/(beta k)) with
-     * the reciprocal rounded once per link (Sec. 2 fixes the formula, not its
-     * rounding; one division per link instead of one per trial) */
-    float inv_bk = haar ? 0.0f : 1.0f / bk;
+    const struct creutz_setup setup = creutz_prepare(beta * k);
 
     float a0 = 0.0f;
     int trials = 0;
@@ -407,15 +438,8 @@ int orc_heatbath_link(float beta, const float v[4], uint64_t seed, uint32_t eo, 
         if ((t & 1) == 0) draw_words(seed, eo, sweep, ORC_KIND_CREUTZ, parity, mu, (uint32_t)(t >> 1), w);
         float r1 = orc_u01_log(w[2 * (t & 1)]); /* the argument of the log */
         float r2 = orc_u01(w[2 * (t & 1) + 1]);
-        float cand;
-        if (haar) {
-            cand = 2.0f * r1 - 1.0f;
-        } else {
-            float x = fmaf(r1, one_minus_e, e);
-            cand = 1.0f + orc_logf(x) * inv_bk;
-        }
-        if (cand < -1.0f) cand = -1.0f;
-        if (cand > 1.0f) cand = 1.0f;
+        float x;
+        float cand = creutz_candidate(&setup, r1, &x);
         trials = t + 1;
         if (r2 * r2 <= fmaf(-cand, cand, 1.0f)) {
             a0 = cand;
@@ -449,6 +473,21 @@ float orc_creutz_a0(float bk, uint64_t seed, uint32_t eo, uint32_t sweep, int pa
     int n = orc_heatbath_link(1.0f, v, seed, eo, sweep, parity, mu, out);
     *trials = n;
     return out[0];
+}
+
+/* x and the candidate a0 of single Creutz trials: trial i has beta k = bk[i]
+ * (from a staple along the identity with |V| = bk[i], beta = 1, as in
+ * orc_creutz_a0) and its first word w[i]; x = e + r1 (1 - e), r1 the log
+ * uniform of w[i].  Lets a test compare the device's trial variable with the
+ * definition for chosen words (the smallest included). */
+void orc_creutz_x_a0_v(const float *bk, const uint32_t *w, int64_t n, float *x, float *a0)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        const float v[4] = {bk[i], 0.0f, 0.0f, 0.0f};
+        const float k = sqrtf(dot4(v[0], v[0], v[1], v[1], v[2], v[2], v[3], v[3]));
+        const struct creutz_setup setup = creutz_prepare(1.0f * k);
+        a0[i] = creutz_candidate(&setup, orc_u01_log(w[i]), &x[i]);
+    }
 }
 
 /* One heat-bath phase: every link U_mu(x) with parity(x) = p (Sec. 4).  The

@@ -44,6 +44,14 @@ __global__ void math_selftest_kernel(int which, const float *__restrict__ x, flo
             const float *q = x + 8 * i;
             y[i] = (float)learned::metropolis_screen(q[0], q[1], q[2], q[3], q[4], q[5]);
             y2[i] = learned::metropolis_exact(q[0], q[1], q[2], q[3], q[4], q[5]) ? 1.0f : 0.0f;
+        } else if (which == 6) {
+            // pair (beta k, first Philox word as bits): x = e + r1 (1 - e) and
+            // the candidate a0 of that Creutz trial, with e from the draw setup
+            // of a staple along the identity with |V| = beta k, beta = 1
+            const DrawSetup d = prepare_draw(make_float4(x[2 * i], 0.0f, 0.0f, 0.0f), 1.0f);
+            const float xv = __fmaf_rn(uniform_log(__float_as_uint(x[2 * i + 1])), __fsub_rn(1.0f, d.e), d.e);
+            y[i] = xv;
+            y2[i] = creutz_a0(xv, d.ibk);
         } else {
             float s, c;
             sincos_2pi(x[i], s, c);
@@ -103,10 +111,10 @@ su2_status su2_selftest_philox(const uint32_t *ck, uint32_t *out, size_t n)
 
 su2_status su2_selftest_math(int which, const float *x, float *y, float *y2, size_t n)
 {
-    const bool two = which == 2 || which == 4 || which == 5;
-    if (!x || !y || which < 0 || which > 5 || (two && !y2)) return SU2_E_INVAL;
+    const bool two = which == 2 || which == 4 || which == 5 || which == 6;
+    if (!x || !y || which < 0 || which > 6 || (two && !y2)) return SU2_E_INVAL;
     if (n == 0) return SU2_OK;
-    const size_t in_bytes = (which == 4 ? 16 : which == 5 ? 32 : 4) * n;
+    const size_t in_bytes = (which == 4 ? 16 : which == 5 ? 32 : which == 6 ? 8 : 4) * n;
     return run_with_buffers(x, in_bytes, y, 4 * n, two ? y2 : nullptr, two ? 4 * n : 0,
                             [which, n](char *in, char *o, char *o2, cudaStream_t s) {
                                 math_selftest_kernel<<<grid_for((int64_t)n, 256), 256, 0, s>>>(

@@ -223,15 +223,19 @@ __device__ __forceinline__ float qnorm2(float4 a) { return chain4(a.x, a.x, a.y,
 // ------------------------------------------------------------ heat bath
 constexpr int kMaxTrials = 4096;
 constexpr float kHaarBelow = 1e-6f;  // beta k below this: a0 from the Haar marginal
-// beta k above this: exp(-2 beta k) taken as 0.  It changes no draw: for
-// beta k > 17, e = exp(-2 beta k) < 2^-48, so 1 - e rounds to 1 and
-// x = r1 (1 - e) + e rounds to r1 for every uniform r1 >= 2^-24 (half an ulp
-// of r1 is at least 2^-48); the exponential is simply not computed there.
-constexpr float kExpCutoff = 17.0f;
+// beta k above this: exp(-2 beta k) is not computed and taken as 0.  It
+// changes no draw: for beta k > 21, e = exp(-2 beta k) < exp(-42) < 2^-60, so
+// 1 - e rounds to 1 and x = r1 (1 - e) + e rounds to r1 for every log uniform
+// r1 >= 2^-33 (uniform_log's smallest value), whose half ulp is at least
+// 2^-57 > e.  The definition keeps e up to beta k = 43, where it leaves the
+// binary32 normal range; between 21 and 43 it makes no difference to x.
+// (A cutoff of 17 was wrong: there e ~ 2^-49 moves x = r1 for r1 below about
+// 2^-26, i.e. for the smallest words.)
+constexpr float kExpCutoff = 21.0f;
 
 // Normalised staple (Sec. 2): k = |v| = sqrt(det V), U~^dag = v^dag / k
-// (identity if k = 0), bk = beta k, e = exp(-2 beta k) (0 when beta k > 43 or
-// on the Haar branch).
+// (identity if k = 0), bk = beta k, e = exp(-2 beta k) (0 when beta k >
+// kExpCutoff, where it changes no draw, or on the Haar branch).
 struct DrawSetup {
     float4 ut;
     float bk;

@@ -376,14 +376,15 @@ def su2_selftest_philox(ck: np.ndarray) -> np.ndarray:
 
 def su2_selftest_math(which: int, x: np.ndarray):
     """which = 4 takes x of shape (n, 4): rows (r1, r2, 1/(beta k), exp(-2 beta k));
-    which = 5 x of shape (n, 8): rows (beta k, a', a, f'(z'), f'(z), u1, 0, 0)."""
+    which = 5 x of shape (n, 8): rows (beta k, a', a, f'(z'), f'(z), u1, 0, 0);
+    which = 6 x of shape (n, 2): rows (beta k, Philox word bits as float32)."""
     x = np.ascontiguousarray(x, dtype=np.float32)
-    n = x.shape[0] if which in (4, 5) else x.size
+    n = x.shape[0] if which in (4, 5, 6) else x.size
     y = np.empty(n, dtype=np.float32)
-    y2 = np.empty(n, dtype=np.float32) if which in (2, 4, 5) else None
+    y2 = np.empty(n, dtype=np.float32) if which in (2, 4, 5, 6) else None
     _check(_lib.su2_selftest_math(which, _host_ptr(x), _host_ptr(y), _host_ptr(y2) if y2 is not None else None,
                                   n), "su2_selftest_math")
-    if which not in (4, 5):
+    if which not in (4, 5, 6):
         y = y.reshape(x.shape)
         y2 = y2.reshape(x.shape) if y2 is not None else None
     return (y, y2) if y2 is not None else y

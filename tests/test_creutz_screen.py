@@ -45,7 +45,7 @@ def random_trials(rng, n, near_boundary):
     near_boundary puts r2 within a relative 2e-4 of sqrt(1 - a0^2)."""
     bk = np.exp(rng.uniform(np.log(0.05), np.log(60.0), n))
     ibk = (1.0 / bk).astype(np.float32)
-    e = np.where(bk <= 17.0, np.exp(-2.0 * bk), 0.0).astype(np.float32)
+    e = np.where(bk <= 21.0, np.exp(-2.0 * bk), 0.0).astype(np.float32)
     # r1 as the kernels draw it for a logarithm: w 2^-32 + 2^-33
     w = rng.integers(0, 1 << 32, n, dtype=np.uint64)
     r1 = (w.astype(np.float32).astype(np.float64) * 2.0 ** -32 + 2.0 ** -33).astype(np.float32)

@@ -80,6 +80,26 @@ def test_elementary_functions_bitwise():
     assert np.array_equal(c.view(np.uint32), co.view(np.uint32))
 
 
+def test_creutz_trial_variable_matches_definition_over_beta_k():
+    """x = e + r1 (1 - e) and the candidate a0 of a Creutz trial, device
+    against oracle, bitwise, over beta k in [16, 44] (through the kernels'
+    exp(-2 beta k) cutoff at 21 and the definition's at 43) for every word
+    below 2^16 (the smallest log uniforms, from 2^-33) and random words."""
+    rng = np.random.default_rng(7)
+    words = np.concatenate([np.arange(0, 1 << 16), rng.integers(0, 2 ** 32, 8192),
+                            np.arange(2 ** 32 - 256, 2 ** 32)]).astype(np.uint32)
+    bks = np.concatenate([np.linspace(16.0, 44.0, 113), [17.0, 17.5, 20.5, 21.0, 43.0],
+                          [np.nextafter(np.float32(21.0), np.float32(50.0)),
+                           np.nextafter(np.float32(43.0), np.float32(50.0))]]).astype(np.float32)
+    bk = np.repeat(bks, words.size).astype(np.float32)
+    w = np.tile(words, bks.size)
+    x_ref, a0_ref = oracle.creutz_x_a0(bk, w)
+    q = np.stack([bk, w.view(np.float32)], axis=1)
+    x, a0 = su2.su2_selftest_math(6, q)
+    assert np.array_equal(x.view(np.uint32), x_ref.view(np.uint32))
+    assert np.array_equal(a0.view(np.uint32), a0_ref.view(np.uint32))
+
+
 # ------------------------------------------------------------- start kernels
 @pytest.mark.parametrize("ns,nt", [(2, 2), (4, 6), (6, 4), (8, 8), (12, 4)])
 def test_starts_match_oracle(lattice, ns, nt):
@@ -257,18 +277,20 @@ def test_torch_allocator_and_stream():
 # ------------------------------------------------- full size (48^4, beta = 6)
 def test_full_size_48_hot_start_one_sweep(lattice):
     """48^4, beta = 6.0, hot start from seed 3: the launch configuration the
-    benchmark times.  Whole lattice compared after the start and after one
-    sweep (the oracle runs threaded over sites)."""
+    benchmark times.  Whole lattice compared bit for bit after the start and
+    after each of two sweeps (the first from the hot start puts many links
+    at 17 < beta k < 21, the second more above; the oracle runs threaded
+    over sites)."""
     ns = nt = 48
     beta, seed = 6.0, 3
     lat = lattice(ns, nt, beta, seed)
     ref = oracle.hot_start(ns, nt, seed)
     assert np.array_equal(lat.links(), ref)
-    st = su2.su2_heatbath_sweep(lat.h, 1, stats=True)
-    tr = oracle.heatbath_sweep(ns, nt, beta, seed, 0, ref, nthreads=nthreads())
-    got = lat.links()
-    assert float(np.abs(got - ref).max()) <= LINK_TOL
-    assert st["trials"] == [int(t) for t in tr]
+    for s in range(2):
+        st = su2.su2_heatbath_sweep(lat.h, 1, stats=True)
+        tr = oracle.heatbath_sweep(ns, nt, beta, seed, s, ref, nthreads=nthreads())
+        assert np.array_equal(lat.links(), ref), s
+        assert st["trials"] == [int(t) for t in tr], s
     assert obs_close(su2.su2_plaquette(lat.h), oracle.plaquette(ns, nt, ref))
     assert obs_close(su2.su2_polyakov(lat.h), oracle.polyakov(ns, nt, ref))
 

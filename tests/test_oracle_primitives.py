@@ -183,14 +183,51 @@ def test_quaternion_dagger_inverts_unit_elements():
         assert np.allclose(m @ m.conj().T, np.eye(2), atol=1e-6)
 
 
-def test_creutz_variable_ignores_exp_below_cutoff():
-    """The device skips exp(-2 beta k) for beta k > 17: there e < 2^-48, so
-    1 - e rounds to 1 and r1 (1 - e) + e rounds to r1 in binary32 for every
-    uniform r1 = j 2^-24 (the draws are those of the oracle, which keeps e)."""
-    e = float(oracle.expf(np.array([-34.0], np.float32))[0])
-    assert 0.0 < e < 2.0 ** -48
-    assert np.float32(np.float32(1.0) - np.float32(e)) == np.float32(1.0)
-    j = np.concatenate([np.arange(1, 4097), np.arange(2 ** 24 - 4096, 2 ** 24 + 1),
-                        np.random.default_rng(0).integers(1, 2 ** 24, 200_000)])
-    r1 = (j.astype(np.float64) * 2.0 ** -24)
-    assert np.array_equal((r1 + e).astype(np.float32), r1.astype(np.float32))
+def log_uniforms(w):
+    """r1 as the definition draws it for a logarithm: the word rounded to
+    binary32, times 2^-32, plus 2^-33, rounded once (exact in binary64
+    before the last rounding)."""
+    w = np.asarray(w, dtype=np.uint64)
+    return (w.astype(np.float32).astype(np.float64) * 2.0 ** -32 + 2.0 ** -33).astype(np.float32)
+
+
+def cutoff_words():
+    """The smallest words (r1 down to 2^-33, where x = e + r1 (1 - e) is most
+    sensitive to e), the largest, and random ones."""
+    rng = np.random.default_rng(0)
+    return np.concatenate([np.arange(0, 4097), np.arange(2 ** 32 - 4096, 2 ** 32),
+                           rng.integers(0, 2 ** 32, 50_000)]).astype(np.uint32)
+
+
+def test_log_uniform_is_the_whole_word_rounded_once():
+    w = cutoff_words()
+    r1, _ = oracle.creutz_x_a0(np.full(w.size, 50.0, np.float32), w)  # e = 0 above 43
+    assert np.array_equal(r1, log_uniforms(w))
+    assert r1.min() == np.float32(2.0 ** -33) and r1.max() == np.float32(1.0)
+
+
+def test_creutz_variable_ignores_exp_above_21():
+    """The heat-bath kernels do not compute e = exp(-2 beta k) above
+    beta k = 21 and take x = r1; the definition keeps e up to 43.  This is
+    the same draw only if x = r1 (1 - e) + e rounds to r1 for every log
+    uniform r1 >= 2^-33 there: e < exp(-42) < 2^-60 lies below half an ulp
+    of 2^-33 (2^-57).  Checked on the definition's own x for the smallest,
+    the largest and random words over beta k in (21, 43], and against a
+    cutoff of 17, which moves x for the smallest words."""
+    assert float(oracle.expf(np.array([-42.0], np.float32))[0]) < 2.0 ** -60
+    w = cutoff_words()
+    r1 = log_uniforms(w)
+    bks = np.concatenate([[np.nextafter(np.float32(21.0), np.float32(50.0))],
+                          np.linspace(21.0, 43.0, 221)[1:], [np.float32(43.0)]]).astype(np.float32)
+    for bk in bks:
+        x, _ = oracle.creutz_x_a0(np.full(w.size, bk, np.float32), w)
+        assert np.array_equal(x, r1), bk
+    # at beta k = 17.5 the smallest words do move: x = r1 is not the definition there
+    x, _ = oracle.creutz_x_a0(np.full(w.size, 17.5, np.float32), w)
+    moved = w[x != r1]
+    assert moved.size > 0 and moved.max() < 2 ** 12, moved[:8]
+    assert x[1] != r1[1]  # w = 1: r1 = 3.49246e-10, x = 3.492466e-10
+    # the smallest beta k from which no word moves lies between 19.5 and 21
+    lo = np.float32(19.5)
+    x, _ = oracle.creutz_x_a0(np.full(w.size, lo, np.float32), w)
+    assert not np.array_equal(x, r1)
