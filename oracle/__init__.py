@@ -105,6 +105,9 @@ def _load():
             "orc_learned_phase": (i64, [i32, i32, f64, u64, u32, i32, i32, P, P, i32, f32, f32, f32, f32]),
             "orc_learned_sweep": (i64, [i32, i32, f64, u64, u32, P, P, i32, f32, f32, f32, f32, P]),
             "orc_learned_chain": (i64, [P, i32, f32, f32, f32, f32, f32, P, P, u64, i64, P]),
+            "orc_learned_link_net": (i32, [P, f32, P, P, u64, u32, u32, i32, i32, P]),
+            "orc_learned_sweep_net": (i64, [i32, i32, f64, u64, u32, P, P, P]),
+            "orc_learned_chain_net": (i64, [P, f32, P, P, u64, i64, P]),
             "orc_collect_pairs": (i64, [i32, i32, f64, u64, u32, i32, i32, i32, P, P]),
             "orc_nll_grad": (f64, [P, P, i64, P]),
             "orc_nll_outputs": (f64, [P, f64, P]),
@@ -419,6 +422,25 @@ def learned_chain(table, s_lo, s_hi, mean, scale, beta, v, old0, seed, n):
     a0 = np.zeros(n, dtype=np.float32)
     acc = _load().orc_learned_chain(_ptr(table), table.shape[0], s_lo, s_hi, mean, scale, beta, _ptr(v), _ptr(old0),
                                     seed, n, _ptr(a0))
+    return a0, acc
+
+
+def learned_sweep_net(ns, nt, beta, seed, sweep, links, w) -> np.ndarray:
+    """One learned sweep in place with the network evaluated at every link's
+    beta k (the proposal as defined, no table); accepted links per phase."""
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    assert w.size == N_WEIGHTS
+    acc = np.zeros(8, dtype=np.int64)
+    _load().orc_learned_sweep_net(ns, nt, beta, seed, sweep, _ptr(links), _ptr(w), _ptr(acc))
+    return acc
+
+
+def learned_chain_net(w, beta, v, old0, seed, n):
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    v = np.ascontiguousarray(v, dtype=np.float32)
+    old0 = np.ascontiguousarray(old0, dtype=np.float32)
+    a0 = np.zeros(n, dtype=np.float32)
+    acc = _load().orc_learned_chain_net(_ptr(w), beta, _ptr(v), _ptr(old0), seed, n, _ptr(a0))
     return a0, acc
 
 

@@ -213,13 +213,17 @@ void orc_table_params(const float *table, int G, float s_lo, float s_hi, float s
  * (= target / proposal density up to constants), as u1 <= exp(Delta),
  * Delta = beta k (a0' - a_cur) + log(sqrt((1 - a0'^2)/(1 - a_cur^2)) f'(z')/f'(z_cur)).
  * All four uniforms come from one Philox block of the learned stream.
- * Returns 1 if accepted (out = new link), 0 if rejected (out = old). */
-int orc_learned_link(const float *table, int G, float s_lo, float s_hi, float mean, float scale, float beta,
-                     const float v[4], const float old[4], uint64_t seed, uint32_t eo, uint32_t sweep, int parity,
-                     int mu, float out[4])
+ *
+ * The proposal's spline parameters are, by definition, the network's at
+ * s = (beta k - mean) * scale (orc_learned_link_net).  orc_learned_link takes
+ * them from the proposal table instead: the network at G grid points in s,
+ * interpolated linearly, which is what the GPU kernel evaluates.  Both chains
+ * are exact (acceptance and proposal use the same density); the tests bound
+ * how far the table's density and acceptance are from the network's. */
+static float staple_frame(const float v[4], float beta, float ut[4])
 {
-    float k = sqrtf(fmaf(v[0], v[0], fmaf(v[1], v[1], fmaf(v[2], v[2], v[3] * v[3]))));
-    float ut[4] = {1.0f, 0.0f, 0.0f, 0.0f};
+    const float k = sqrtf(fmaf(v[0], v[0], fmaf(v[1], v[1], fmaf(v[2], v[2], v[3] * v[3]))));
+    ut[0] = 1.0f; ut[1] = 0.0f; ut[2] = 0.0f; ut[3] = 0.0f;
     if (k > 0.0f) {
         const float inv_k = 1.0f / k;
         ut[0] = v[0] * inv_k;
@@ -227,10 +231,14 @@ int orc_learned_link(const float *table, int G, float s_lo, float s_hi, float me
         ut[2] = -v[2] * inv_k;
         ut[3] = -v[3] * inv_k;
     }
-    const float bk = beta * k;
-    float p[LP];
-    orc_table_params(table, G, s_lo, s_hi, (bk - mean) * scale, p);
+    return beta * k;
+}
 
+/* The step itself, given the link's spline parameters p; returns 1 if
+ * accepted (out = new link), 0 if rejected (out = old). */
+static int learned_step(const float p[LP], float bk, const float ut[4], const float old[4], uint64_t seed,
+                        uint32_t eo, uint32_t sweep, int parity, int mu, float out[4])
+{
     uint32_t ctr[4] = {eo, sweep, ((uint32_t)KIND_LEARNED << 3) | ((uint32_t)parity << 2) | (uint32_t)mu, 0u};
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     uint32_t wd[4];
@@ -274,6 +282,31 @@ int orc_learned_link(const float *table, int G, float s_lo, float s_hi, float me
     return 1;
 }
 
+/* The step with the table's interpolated spline parameters (the kernel's). */
+int orc_learned_link(const float *table, int G, float s_lo, float s_hi, float mean, float scale, float beta,
+                     const float v[4], const float old[4], uint64_t seed, uint32_t eo, uint32_t sweep, int parity,
+                     int mu, float out[4])
+{
+    float ut[4];
+    const float bk = staple_frame(v, beta, ut);
+    float p[LP];
+    orc_table_params(table, G, s_lo, s_hi, (bk - mean) * scale, p);
+    return learned_step(p, bk, ut, old, seed, eo, sweep, parity, mu, out);
+}
+
+/* The step with the network evaluated at this link's beta k: the proposal
+ * as defined (w holds the weights, then the input mean and scale). */
+int orc_learned_link_net(const float *w, float beta, const float v[4], const float old[4], uint64_t seed,
+                         uint32_t eo, uint32_t sweep, int parity, int mu, float out[4])
+{
+    float ut[4];
+    const float bk = staple_frame(v, beta, ut);
+    float o[LO], p[LP];
+    orc_mlp_forward(w, (bk - w[OFF_MEAN]) * w[OFF_SCALE], o);
+    orc_spline_params(o, p);
+    return learned_step(p, bk, ut, old, seed, eo, sweep, parity, mu, out);
+}
+
 /* lattice helpers (same geometry as su2_oracle.c) */
 static int lattice_parity(int64_t s, int ns)
 {
@@ -314,6 +347,31 @@ int64_t orc_learned_sweep(int ns, int nt, double beta, uint64_t seed, uint32_t s
             accepted[2 * mu + p] =
                 orc_learned_phase(ns, nt, beta, seed, sweep, mu, p, links, table, G, s_lo, s_hi, mean, scale);
             total += accepted[2 * mu + p];
+        }
+    return total;
+}
+
+/* One sweep of the learned step with the network evaluated per link (the
+ * definition); returns the number of accepted links, per phase in accepted[]. */
+int64_t orc_learned_sweep_net(int ns, int nt, double beta, uint64_t seed, uint32_t sweep, float *links,
+                              const float *w, int64_t accepted[8])
+{
+    const int64_t vol = (int64_t)ns * ns * ns * nt;
+    int64_t total = 0;
+    for (int mu = 0; mu < 4; ++mu)
+        for (int p = 0; p < 2; ++p) {
+            int64_t acc = 0;
+            for (int64_t s = 0; s < vol; ++s) {
+                if (lattice_parity(s, ns) != p) continue;
+                float v[4], old[4], out[4];
+                orc_staple(ns, nt, links, s, mu, v);
+                float *l = links + (s * 4 + mu) * 4;
+                memcpy(old, l, sizeof old);
+                acc += orc_learned_link_net(w, (float)beta, v, old, seed, (uint32_t)(s >> 1), sweep, p, mu, out);
+                memcpy(l, out, sizeof out);
+            }
+            accepted[2 * mu + p] = acc;
+            total += acc;
         }
     return total;
 }
@@ -571,6 +629,22 @@ int64_t orc_learned_chain(const float *table, int G, float s_lo, float s_hi, flo
     int64_t acc = 0;
     for (int64_t i = 0; i < n; ++i) {
         acc += orc_learned_link(table, G, s_lo, s_hi, mean, scale, beta, v, cur, seed, 7u, (uint32_t)i, 0, 0, nxt);
+        memcpy(cur, nxt, sizeof cur);
+        a0_out[i] = fmaf(cur[0], ut[0], fmaf(cur[1], ut[1], fmaf(cur[2], ut[2], cur[3] * ut[3])));
+    }
+    return acc;
+}
+
+/* orc_learned_chain with the network evaluated per step (the definition). */
+int64_t orc_learned_chain_net(const float *w, float beta, const float v[4], const float old0[4], uint64_t seed,
+                              int64_t n, float *a0_out)
+{
+    float cur[4], nxt[4], ut[4];
+    memcpy(cur, old0, sizeof cur);
+    staple_frame(v, beta, ut);
+    int64_t acc = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        acc += orc_learned_link_net(w, beta, v, cur, seed, 7u, (uint32_t)i, 0, 0, nxt);
         memcpy(cur, nxt, sizeof cur);
         a0_out[i] = fmaf(cur[0], ut[0], fmaf(cur[1], ut[1], fmaf(cur[2], ut[2], cur[3] * ut[3])));
     }

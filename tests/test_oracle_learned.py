@@ -12,6 +12,8 @@
   network -- the property that keeps the learned chain exact.
 - Collected (beta k, a0) pairs follow the exact conditional law.
 """
+import os
+
 import numpy as np
 import pytest
 from scipy import integrate
@@ -148,3 +150,105 @@ def test_collected_pairs_follow_the_exact_law():
     before = links.copy()
     oracle.collect_pairs(ns, nt, 2.4, 3, 5, 2, 1, 3, links)
     assert np.array_equal(before, links)
+
+
+# ------------------------------------------------ the table against the network
+# The proposal is defined by the network evaluated at each link's beta k
+# (orc_learned_link_net).  The kernel, and orc_learned_link, evaluate the
+# network once per grid point of a 256-row table and interpolate every spline
+# parameter linearly in s.  The network is piecewise linear in s (ReLU units,
+# scalar input) and the spline parameters are smooth functions of its outputs,
+# so the interpolation error is O(h^2) between kinks and O(h) in the grid cells
+# that hold a kink (h = grid step).  The bounds below are measured on a
+# trained network (tests/golden/learned_weights.txt, written from the oracle
+# alone) with margin; they make the table a pinned approximation of the
+# definition.  Both chains are exact for their own proposal.
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "learned_weights.txt")
+
+
+def golden_weights():
+    with open(GOLDEN) as f:
+        w = np.array([float(x) for x in f if not x.startswith("#")], dtype=np.float32)
+    assert w.size == oracle.N_WEIGHTS
+    return w
+
+
+def golden_table(G=256, bk_lo=1.0, bk_hi=40.0):
+    w = golden_weights()
+    mean, scale = w[oracle.N_TRAIN], w[oracle.N_TRAIN + 1]
+    s_lo = float(np.float32((bk_lo - mean) * scale))
+    s_hi = float(np.float32((bk_hi - mean) * scale))
+    return w, oracle.proposal_table(w, s_lo, s_hi, G), s_lo, s_hi
+
+
+def test_table_parameters_and_density_are_close_to_the_network():
+    w, table, s_lo, s_hi = golden_table()
+    rng = np.random.default_rng(21)
+    h = (s_hi - s_lo) / 255
+    ss = np.concatenate([rng.uniform(s_lo, s_hi, 120), s_lo + (np.arange(0, 255, 3) + 0.5) * h]).astype(np.float32)
+    a = np.linspace(-1.0, 1.0, 200001)[1:-1].astype(np.float32)
+    da = 2.0 / 200000
+    z = np.linspace(-1.0, 1.0, 20001)[1:-1].astype(np.float32)
+    worst = dict(knot=0.0, der=0.0, tv=0.0, dlogq=0.0)
+    for s in ss:
+        pt = oracle.table_params(table, s_lo, s_hi, float(s))
+        pn = oracle.spline_params(oracle.mlp_forward(w, float(s)))
+        worst["knot"] = max(worst["knot"], float(np.abs(pt[:18] - pn[:18]).max()))
+        worst["der"] = max(worst["der"], float((np.abs(pt[18:] - pn[18:]) / pn[18:]).max()))
+        # total variation between the two proposal densities q = 1 / (2 f'(f^-1(a)))
+        _, ft = oracle.spline_inverse(pt, a)
+        _, fn = oracle.spline_inverse(pn, a)
+        qt, qn = 0.5 / ft.astype(np.float64), 0.5 / fn.astype(np.float64)
+        assert abs(qn.sum() * da - 1.0) < 1e-4
+        worst["tv"] = max(worst["tv"], 0.5 * float(np.abs(qt - qn).sum()) * da)
+        # mean |log q_table - log q_net| over the network's own proposals
+        an, fpn = oracle.spline_forward(pn, z)
+        _, fpt = oracle.spline_inverse(pt, an)
+        worst["dlogq"] = max(worst["dlogq"], float(np.abs(np.log(fpt / fpn.astype(np.float64))).mean()))
+    assert worst["knot"] < 3e-3, worst
+    assert worst["der"] < 2e-2, worst
+    assert worst["tv"] < 4e-3, worst
+    assert worst["dlogq"] < 8e-3, worst
+
+@pytest.mark.parametrize("bk", [2.0, 6.0, 12.0, 30.0])
+def test_table_acceptance_matches_the_network(bk):
+    """Independence-Metropolis chains with the same uniforms, one with the
+    table's proposal and one with the network's: acceptances agree within
+    2e-3 (the densities differ by at most 4e-3 in total variation)."""
+    w, table, s_lo, s_hi = golden_table()
+    v = np.array([bk, 0.0, 0.0, 0.0], dtype=np.float32)  # beta = 1: beta k = bk, U~ = 1
+    old = np.array([1.0, 0.0, 0.0, 0.0], dtype=np.float32)
+    n = 100_000
+    mean, scale = float(w[oracle.N_TRAIN]), float(w[oracle.N_TRAIN + 1])
+    _, acc_t = oracle.learned_chain(table, s_lo, s_hi, mean, scale, 1.0, v, old, 5, n)
+    _, acc_n = oracle.learned_chain_net(w, 1.0, v, old, 5, n)
+    assert acc_n / n > 0.85, acc_n / n  # a trained proposal
+    assert abs(acc_t - acc_n) / n < 2e-3, (acc_t / n, acc_n / n)
+
+
+@pytest.mark.parametrize("bk", [3.0, 25.0])
+def test_network_chain_has_the_exact_heatbath_law(bk):
+    """The proposal as defined (network per step) keeps the heat-bath law."""
+    w = golden_weights()
+    v = np.array([bk, 0.0, 0.0, 0.0], dtype=np.float32)
+    old = np.array([1.0, 0.0, 0.0, 0.0], dtype=np.float32)
+    a0, acc = oracle.learned_chain_net(w, 1.0, v, old, 41, 300_000)
+    assert acc > 0
+    assert chi2_pvalue_a0(np.clip(a0[1000::10].astype(np.float64), -1, 1), bk) > 1e-4
+
+
+def test_network_sweep_reproduces_the_table_sweep_statistics():
+    """A lattice sweep with the network per link and one with the table, from
+    the same configuration: acceptances per phase within 0.5% of the links."""
+    w, table, s_lo, s_hi = golden_table()
+    ns, nt, beta, seed = 6, 6, 2.3, 9
+    links = oracle.hot_start(ns, nt, seed)
+    for s in range(4):
+        oracle.heatbath_sweep(ns, nt, beta, seed, s, links)
+    lt, ln = links.copy(), links.copy()
+    mean, scale = float(w[oracle.N_TRAIN]), float(w[oracle.N_TRAIN + 1])
+    acc_t = oracle.learned_sweep(ns, nt, beta, seed, 4, lt, table, s_lo, s_hi, mean, scale)
+    acc_n = oracle.learned_sweep_net(ns, nt, beta, seed, 4, ln, w)
+    half = ns ** 3 * nt // 2
+    assert np.all(np.abs(acc_t - acc_n) <= 0.005 * half), (acc_t, acc_n)
+    assert acc_n.sum() > 0.85 * 8 * half
