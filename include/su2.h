@@ -292,7 +292,15 @@ typedef struct {
 /* Installs the proposal: the network is evaluated (binary32, on the device)
  * at grid_points (2..400) equally spaced inputs s in [s_lo, s_hi]; a link's
  * spline parameters are interpolated linearly between the two grid points
- * around its clamped input.  Synchronous. */
+ * around its clamped input.  Synchronous.
+ * The proposal is defined by the network at each link's own s = (beta k -
+ * mean) * scale; the kernel reads it from this table instead (one network
+ * evaluation per grid point rather than about 1,900 multiply-adds per link),
+ * which is why the call takes the grid: [s_lo, s_hi] should cover the s of
+ * the lattice's links (inputs outside are clamped to the end rows), and 256
+ * points keep the table's density within a few 1e-3 in total variation of
+ * the network's.  The chain is exact for any table: proposal and acceptance
+ * use the same interpolated density. */
 su2_status su2_set_proposal(su2_lattice *lat, const float *weights, int n, double s_lo, double s_hi, int grid_points);
 
 /* The grid_points x 27 spline parameters (knots x0..x8, y0..y8, derivatives
@@ -306,8 +314,15 @@ su2_status su2_get_proposal_table(su2_lattice *lat, float *host);
 su2_status su2_learned_generate(su2_lattice *lat, int nsweeps, int measure_every, double min_acceptance,
                                 double *plaq, double *poly, su2_learned_stats *stats);
 
+/* nsweeps learned sweeps without measurements and with the fallback at
+ * acceptance 0.7: su2_learned_generate(lat, nsweeps, 0, 0.7, NULL, NULL,
+ * stats).  stats may be NULL.  Synchronous. */
+su2_status su2_learned_sweep(su2_lattice *lat, int nsweeps, su2_learned_stats *stats);
+
 /* Training pairs (beta k, a0), float2 each, for the links U_mu(x) of the given
- * parity whose even/odd index is a multiple of stride: a0 is a fresh Creutz
+ * parity whose even/odd index is a multiple of stride (mu, parity and stride
+ * choose the sample of links; one call per phase covers a sweep's links
+ * with stride 1): a0 is a fresh Creutz
  * draw (own counter stream) given the current staple, so the pairs have the
  * exact heat-bath law and the lattice is not changed.  dev_pairs: device
  * buffer of cap pairs; *n receives ceil((V/2) / stride).  Asynchronous. */
@@ -413,7 +428,10 @@ su2_status su2_selftest_barrier_timeout(int blocks, uint64_t timeout_ns, unsigne
  * (cudaGetSymbolAddress), so make it before capturing a stream into a CUDA
  * graph.  All calls share the array and it keeps the last call's contents:
  * calls whose kernels may overlap on the GPU (unordered streams) race and
- * give wrong results -- order them. */
+ * give wrong results -- order them.  The array's device address is looked up
+ * once per device and kept for the life of the process; cudaDeviceReset
+ * unloads the module and may move the array, so after a device reset this
+ * entry point must not be called again in the same process. */
 su2_status su2_plaquette_noalloc(const void *links, int ns, int nt, double *out, void *cuda_stream);
 
 /* Self-test of the tensor-core path used by training: D (128 x 32, FP32,

@@ -416,6 +416,11 @@ su2_status su2_learned_generate(su2_lattice *lat, int nsweeps, int measure_every
     return st;
 }
 
+su2_status su2_learned_sweep(su2_lattice *lat, int nsweeps, su2_learned_stats *stats)
+{
+    return su2_learned_generate(lat, nsweeps, 0, 0.7, nullptr, nullptr, stats);
+}
+
 su2_status su2_collect_pairs(su2_lattice *lat, int mu, int parity, int stride, float *dev_pairs, size_t cap,
                              size_t *n)
 {

@@ -124,6 +124,7 @@ _SIGS = {
     "su2_set_proposal": [_P, _P, _i32, _f64, _f64, _i32],
     "su2_get_proposal_table": [_P, _P],
     "su2_learned_generate": [_P, _i32, _i32, _f64, _P, _P, ctypes.POINTER(su2_learned_stats)],
+    "su2_learned_sweep": [_P, _i32, ctypes.POINTER(su2_learned_stats)],
     "su2_collect_pairs": [_P, _i32, _i32, _i32, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)],
     "su2_trainer_create": [_P, _u64, _P, ctypes.POINTER(_P)],
     "su2_trainer_destroy": [_P],
@@ -426,6 +427,13 @@ def su2_learned_generate(lat: int, nsweeps: int, measure_every: int = 1, min_acc
     _check(_lib.su2_learned_generate(lat, nsweeps, measure_every, float(min_acceptance), _host_ptr(plaq),
                                      _host_ptr(poly), ctypes.byref(st)), "su2_learned_generate")
     return plaq[:nmeas], poly[:nmeas], st.as_dict()
+
+
+def su2_learned_sweep(lat: int, nsweeps: int):
+    """nsweeps learned sweeps, fallback below acceptance 0.7, no measurements."""
+    st = su2_learned_stats()
+    _check(_lib.su2_learned_sweep(lat, nsweeps, ctypes.byref(st)), "su2_learned_sweep")
+    return st.as_dict()
 
 
 def su2_collect_pairs(lat: int, mu: int, parity: int, stride: int, dev_ptr: int, cap: int) -> int:

@@ -116,3 +116,42 @@ def test_collected_pairs_are_bitwise_the_oracles():
         assert np.array_equal(su2.su2_get_links(h, ns, nt), links)  # the chain did not move
     finally:
         su2.su2_destroy(h)
+
+
+def test_learned_sweep_with_the_cpu_trained_network_matches_the_oracle():
+    """su2_learned_sweep (fallback at 0.7, no measurements) with the network
+    that the oracle trained on exact draws (tests/golden/learned_weights.txt):
+    the kernel chain is bitwise the oracle's table chain, with equal
+    acceptance counts, and its acceptance is that of the network's own chain
+    within the table's pinned error."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "learned_weights.txt")
+    with open(path) as f:
+        w = np.array([float(x) for x in f if not x.startswith("#")], dtype=np.float32)
+    mean, scale = float(w[1945]), float(w[1946])
+    lo, hi = float(np.float32((1.0 - mean) * scale)), float(np.float32((40.0 - mean) * scale))
+    ns, nt, beta, seed = 8, 8, 2.4, 17
+    h = su2.su2_create(ns, nt, beta, seed, su2.SU2_HOT)
+    try:
+        su2.su2_heatbath_sweep(h, 3)
+        su2.su2_set_proposal(h, w, lo, hi, 256)
+        st = su2.su2_learned_sweep(h, 2)
+        got = su2.su2_get_links(h, ns, nt)
+    finally:
+        su2.su2_destroy(h)
+    assert st["plain_sweeps"] == 0 and st["learned_sweeps"] == 2
+    links = oracle.hot_start(ns, nt, seed)
+    for s in range(3):
+        oracle.heatbath_sweep(ns, nt, beta, seed, s, links)
+    start = links.copy()
+    table = oracle.proposal_table(w, lo, hi, 256)
+    acc = np.zeros(8, dtype=np.int64)
+    for s in range(3, 5):
+        acc += oracle.learned_sweep(ns, nt, beta, seed, s, links, table, lo, hi, mean, scale)
+    assert np.array_equal(got, links)
+    assert [int(a) for a in st["accepted"]] == [int(a) for a in acc]
+    net = np.zeros(8, dtype=np.int64)
+    for s in range(3, 5):
+        net += oracle.learned_sweep_net(ns, nt, beta, seed, s, start, w)
+    half = ns ** 3 * nt // 2
+    assert abs(int(acc.sum()) - int(net.sum())) <= 0.005 * 16 * half, (acc, net)
+    assert acc.sum() > 0.85 * 16 * half
