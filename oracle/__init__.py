@@ -88,6 +88,7 @@ def _load():
             "orc_heatbath_sweep_kp": (i64, [i32, i32, f64, u64, u32, P, P, i32]),
             "orc_heatbath_phase_kp": (i64, [i32, i32, f64, u64, u32, i32, i32, P, ctypes.POINTER(i64), i32]),
             "orc_kp_a0_v": (None, [f32, u64, u32, i64, P, P]),
+            "orc_slab_phase": (i64, [i32, i32, i32, i32, f64, u64, u32, i32, i32, i32, P, ctypes.POINTER(i64), i32]),
             "orc_overrelax_link": (None, [P, P]),
             "orc_wilson_loop_at": (f32, [i32, i32, P, i64, i32, i32, i32]),
             "orc_wilson_loops": (None, [i32, i32, P, i32, i32, P, i32]),
@@ -259,6 +260,19 @@ def heatbath_sweep(ns: int, nt: int, beta: float, seed: int, sweep: int, links: 
     if err:
         raise RuntimeError(f"{err} links hit the trial cap")
     return trials
+
+
+def slab_phase(ns: int, nt: int, t0: int, nt_local: int, beta: float, seed: int, sweep: int, mu: int,
+               parity: int, slab: np.ndarray, kp: bool = False, nthreads: int = 1) -> int:
+    """One phase on a time slab in place (slab: Ns^3 x (nt_local + 2) sites,
+    ghosts at local slices 0 and nt_local + 1); returns its trial count."""
+    assert slab.shape == (ns ** 3 * (nt_local + 2), 4, 4) and slab.dtype == np.float32
+    t = ctypes.c_int64(0)
+    err = _load().orc_slab_phase(ns, nt, t0, nt_local, beta, seed, sweep, mu, parity, int(kp), _ptr(slab),
+                                 ctypes.byref(t), nthreads)
+    if err:
+        raise RuntimeError(f"{err} links hit the trial cap")
+    return t.value
 
 
 def heatbath_phase_kp(ns: int, nt: int, beta: float, seed: int, sweep: int, mu: int, parity: int,

@@ -787,6 +787,51 @@ int64_t orc_heatbath_sweep_kp(int ns, int nt, double beta, uint64_t seed, uint32
     return errors;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Time-slab decomposition (Sec. 4, multi-GPU part, Fig. 1): a rank holds     */
+/* the Nt_local time slices t0 .. t0 + Nt_local - 1 of the Ns^3 x Nt lattice  */
+/* plus one ghost slice on each side: an array of Ns^3 x (Nt_local + 2) sites */
+/* in the natural layout, local slice tl = global slice (t0 - 1 + tl) mod Nt. */
+/* A phase (mu, p) updates the interior links U_mu(x) with global parity p;   */
+/* the staples read the ghosts for t +- 1 (no site of the interior wraps in  */
+/* the local array), and the random numbers use the site's global even/odd   */
+/* index and parity, so a slab phase is the lattice phase restricted to the   */
+/* slab.  kp selects the Kennedy-Pendleton sampler.  Returns the cap hits.    */
+/* ------------------------------------------------------------------------ */
+int64_t orc_slab_phase(int ns, int nt, int t0, int nt_local, double beta, uint64_t seed, uint32_t sweep, int mu,
+                       int p, int kp, float *slab, int64_t *trials_out, int nthreads)
+{
+    const int ntl = nt_local + 2;
+    const int64_t vs = (int64_t)ns * ns * ns;
+    const float beta_f = (float)beta;
+    int64_t trials = 0, errors = 0;
+#ifdef _OPENMP
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(static) reduction(+ : trials, errors) num_threads(nthreads)
+#endif
+    for (int64_t s = vs; s < (int64_t)(nt_local + 1) * vs; ++s) {
+        int c[4];
+        site_coords(s, ns, c);
+        int g[4] = {c[0], c[1], c[2], (t0 - 1 + c[3] + nt) % nt};
+        const int64_t sg = site_index(g, ns);
+        if (site_parity(sg, ns) != p) continue;
+        float v[4];
+        orc_staple(ns, ntl, slab, s, mu, v);
+        float *l = slab + (s * 4 + mu) * 4;
+        int n = kp ? orc_heatbath_link_kp(beta_f, v, seed, (uint32_t)(sg >> 1), sweep, p, mu, l)
+                   : orc_heatbath_link(beta_f, v, seed, (uint32_t)(sg >> 1), sweep, p, mu, l);
+        if (n < 0) {
+            errors += 1;
+            trials += ORC_MAX_TRIALS;
+        } else {
+            trials += n;
+        }
+    }
+    (void)nthreads;
+    *trials_out = trials;
+    return errors;
+}
+
 /* n draws of a0 at fixed beta k with the Kennedy-Pendleton sampler (draw i
  * uses even/odd index eo0 + i). */
 void orc_kp_a0_v(float bk, uint64_t seed, uint32_t eo0, int64_t n, float *a0, int32_t *trials)
