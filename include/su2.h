@@ -410,6 +410,60 @@ su2_status su2_batch_info(su2_batch *b, int *n, uint32_t *sweep, int *queue_dept
  * timeout_ns (<= 5 s); *timed_out receives the number of blocks that did. */
 su2_status su2_selftest_barrier_timeout(int blocks, uint64_t timeout_ns, unsigned int *timed_out);
 
+/* ------------------------------------------------------------------------
+ * Time slabs: one lattice decomposed over ranks (Sec. 4, multi-GPU part, and
+ * Fig. 1).  A slab holds the time slices t0 .. t0 + nt_local - 1 of the
+ * Ns^3 x Nt lattice plus one ghost slice on each side (Ns^3 x (nt_local + 2)
+ * sites; local slice tl is global slice (t0 - 1 + tl) mod Nt).  A phase
+ * updates the slab's interior with the random numbers of the global sites, so
+ * slabs that exchange their boundaries after every phase reproduce the single
+ * lattice's chain bit for bit.  The paper exchanged the border cells through
+ * host memory between the GPUs' threads; here the caller moves them (pack /
+ * unpack through any buffer and transport) or, for slabs of one process,
+ * su2_slab_exchange copies them directly.
+ * ------------------------------------------------------------------------- */
+typedef struct su2_slab su2_slab;
+
+/* Ns, Nt, nt_local and t0 even, nt_local >= 2, t0 + nt_local <= Nt; the start
+ * is that of the whole lattice (hot: the global sites' Haar links, ghosts
+ * included).  Stream as su2_create.  SU2_E_INVAL on bad extents. */
+su2_status su2_slab_create(int ns, int nt, int t0, int nt_local, double beta, uint64_t seed, su2_start start,
+                           void *cuda_stream, su2_slab **out);
+su2_status su2_slab_destroy(su2_slab *s);
+/* SU2_SAMPLER_CREUTZ or SU2_SAMPLER_KP. */
+su2_status su2_slab_set_sampler(su2_slab *s, int sampler);
+/* Phase (mu, parity) of the slab's interior, parity of the global site; the
+ * sweep counter advances after (3, 1).  Asynchronous.  Before the next phase
+ * the boundaries of this one must be exchanged. */
+su2_status su2_slab_phase(su2_slab *s, int mu, int parity);
+/* Bytes of one boundary message: the Ns^3 / 2 links U_mu of one parity in one
+ * time slice, float4 each (8 Ns^3). */
+size_t su2_slab_boundary_bytes(const su2_slab *s);
+/* After phase (mu, parity): pack side 0 (first interior slice) or 1 (last)
+ * into dst; unpack src into side 0 (lower ghost) or 1 (upper ghost).  dst /
+ * src: host (pinned or pageable) or device memory of su2_slab_boundary_bytes.
+ * Asynchronous on the slab's stream (su2_slab_sync before reusing a host
+ * buffer).  The first interior slice goes to the lower neighbour's upper
+ * ghost, the last to the upper neighbour's lower ghost. */
+su2_status su2_slab_pack(su2_slab *s, int mu, int parity, int side, void *dst);
+su2_status su2_slab_unpack(su2_slab *s, int mu, int parity, int side, const void *src);
+/* Both boundary copies of phase (mu, parity) between neighbouring slabs of
+ * one process (lower's last slice -> upper's lower ghost, upper's first ->
+ * lower's upper ghost), ordered after both slabs' work and before their next
+ * phases (events when their streams differ).  lower == upper: a slab that
+ * holds the whole lattice, its own neighbour. */
+su2_status su2_slab_exchange(su2_slab *lower, su2_slab *upper, int mu, int parity);
+su2_status su2_slab_sync(su2_slab *s);
+/* Links of the whole local array, ghosts included, lexicographic in local
+ * sites ([site][mu][a0..a3], 4 Ns^3 (nt_local + 2) float4).  Synchronous. */
+su2_status su2_slab_get_links(su2_slab *s, float *host);
+su2_status su2_slab_set_links(su2_slab *s, const float *host);
+/* Trial counts per phase (2 mu + parity, parity of the global site) since the
+ * last call (then cleared), and links that hit the trial cap (SU2_E_SAMPLER if
+ * any).  Synchronous. */
+su2_status su2_slab_stats(su2_slab *s, uint64_t trials[8], uint64_t *sampler_failures);
+su2_status su2_slab_info(const su2_slab *s, int *t0, int *nt_local, uint32_t *sweep);
+
 /* Mean plaquette of links that already sit in device memory, computed without
  * allocating anything (no cudaMalloc, cudaFree or allocating library call).
  * The paper has no counterpart: this is for callers that cannot allocate

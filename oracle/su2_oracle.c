@@ -224,6 +224,18 @@ void orc_quat_mul(const float a[4], const float b[4], float c[4])
     c[0] = r0; c[1] = r1; c[2] = r2; c[3] = r3;
 }
 
+/* c <- a b + c, each component the chain of orc_quat_mul with its innermost
+ * product fused with the component of c: fmaf(p0,q0, fmaf(p1,q1, fmaf(p2,q2,
+ * fmaf(p3,q3, c)))).  The staple accumulates its terms this way. */
+static void quat_mul_add(const float a[4], const float b[4], float c[4])
+{
+    float r0 = fmaf(a[0], b[0], fmaf(-a[1], b[1], fmaf(-a[2], b[2], fmaf(-a[3], b[3], c[0]))));
+    float r1 = fmaf(a[0], b[1], fmaf(a[1], b[0], fmaf(-a[2], b[3], fmaf(a[3], b[2], c[1]))));
+    float r2 = fmaf(a[0], b[2], fmaf(a[2], b[0], fmaf(-a[3], b[1], fmaf(a[1], b[3], c[2]))));
+    float r3 = fmaf(a[0], b[3], fmaf(a[3], b[0], fmaf(-a[1], b[2], fmaf(a[2], b[1], c[3]))));
+    c[0] = r0; c[1] = r1; c[2] = r2; c[3] = r3;
+}
+
 static void quat_dag(const float a[4], float d[4])
 {
     d[0] = a[0]; d[1] = -a[1]; d[2] = -a[2]; d[3] = -a[3];
@@ -331,7 +343,9 @@ int orc_hot_start(int ns, int nt, uint64_t seed, float *links)
 /*   U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag                                    */
 /* + U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu),                             */
 /* so that (1/2) Tr(U_mu(x) V) is the sum of the six plaquettes holding it.   */
-/* nu ascending, forward term then backward term, plain float adds from 0.    */
+/* nu ascending, forward term then backward term, from 0; each term's second  */
+/* product is fused with the running sum (quat_mul_add), one rounding per     */
+/* component and term.                                                        */
 /* ------------------------------------------------------------------------ */
 void orc_staple(int ns, int nt, const float *links, int64_t s, int mu, float v[4])
 {
@@ -342,19 +356,17 @@ void orc_staple(int ns, int nt, const float *links, int64_t s, int mu, float v[4
         int64_t xn = site_shift(s, nu, +1, ns, nt);
         int64_t xm = site_shift(s, nu, -1, ns, nt);
         int64_t xpm = site_shift(xp, nu, -1, ns, nt);
-        float d1[4], d2[4], t[4], fwd[4], bwd[4];
+        float d1[4], d2[4], t[4];
         /* forward: U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag */
         quat_dag(link_at(links, xn, mu), d1);
         orc_quat_mul(link_at(links, xp, nu), d1, t);
         quat_dag(link_at(links, s, nu), d2);
-        orc_quat_mul(t, d2, fwd);
+        quat_mul_add(t, d2, v);
         /* backward: U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu) */
         quat_dag(link_at(links, xpm, nu), d1);
         quat_dag(link_at(links, xm, mu), d2);
         orc_quat_mul(d1, d2, t);
-        orc_quat_mul(t, link_at(links, xm, nu), bwd);
-        for (int c = 0; c < 4; ++c) v[c] = v[c] + fwd[c];
-        for (int c = 0; c < 4; ++c) v[c] = v[c] + bwd[c];
+        quat_mul_add(t, link_at(links, xm, nu), v);
     }
 }
 

@@ -35,6 +35,7 @@ struct HbParams {
     unsigned int *flags;
     const unsigned int *gate;  // if non-NULL and *gate == 1 the phase is left to the learned kernel
     double *plaq;              // measuring phases: block partials of the plaquettes of planes (nu < mu, mu)
+    SlabRange slab;            // SLAB kernels: the interior eo range and the global keys of its random numbers
 };
 
 constexpr int kCrThreads = 256;
@@ -70,9 +71,15 @@ constexpr int kCrMinBlocks = SU2_HB_MIN_BLOCKS;  // blocks per SM the register b
 // of the plaquettes of planes (nu, MU) at x and x - nu, so over the odd sites
 // every such plaquette of the final configuration is counted once; the block
 // partial goes to p.plaq[block].
-template <int MU, bool MEAS>
+template <int MU, bool MEAS, bool SLAB>
 __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(const HbParams p)
 {
+    // a time slab updates its interior eo range; its random numbers are those
+    // of the global site (even/odd index + rng_eo, global parity)
+    const int eo_begin = SLAB ? p.slab.eo_begin : 0;
+    const int eo_end = SLAB ? p.slab.eo_end : p.g.vh;
+    const uint32_t rng_eo = SLAB ? p.slab.rng_eo : 0u;
+    const uint32_t rng_parity = SLAB ? (uint32_t)p.slab.rng_parity : (uint32_t)p.parity;
     if (p.gate != nullptr && *(volatile const unsigned int *)p.gate == 1u) return;
     __shared__ CrQueues s_q[kCrWarps];
     const uint32_t sweep = p.sweep_dev ? *p.sweep_dev : p.sweep;
@@ -80,9 +87,9 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
     CrQueues &Q = s_q[threadIdx.x >> 5];
     const unsigned int lanes_below = (1u << lane) - 1u;
     const int stride = gridDim.x * kCrThreads;
-    const int last = p.g.vh - 1;
-    const uint32_t sw_creutz = stream_word(kCreutz, (uint32_t)p.parity, MU);
-    const uint32_t sw_dir = stream_word(kDirection, (uint32_t)p.parity, MU);
+    const int last = eo_end - 1;
+    const uint32_t sw_creutz = stream_word(kCreutz, rng_parity, MU);
+    const uint32_t sw_dir = stream_word(kDirection, rng_parity, MU);
     unsigned int trials = 0;
     double plaq = 0.0;
     int retry_n = 0, done_n = 0;  // warp-uniform queue lengths
@@ -118,7 +125,7 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
         if (lane < n) {
             const int q = first + lane;
             const int eo = Q.d_eo[q];
-            const uint4 wd = philox_rk(make_uint4((uint32_t)eo, sweep, sw_dir, 0u), p.rk);
+            const uint4 wd = philox_rk(make_uint4((uint32_t)eo + rng_eo, sweep, sw_dir, 0u), p.rk);
             const float4 out = direction_update(deferred_a0(Q.d_val[q], Q.d_ibk[q]), Q.d_ut[q], wd);
             p.links[link_index(p.g, MU, p.parity, eo)] = out;
             if (MEAS) plaq += (double)qmul_re(out, Q.d_sp[q]);
@@ -148,7 +155,7 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
             if (MEAS) sp = Q.r_sp[q];
         }
         __syncwarp();
-        const uint4 w = philox_rk(make_uint4((uint32_t)eo, sweep, sw_creutz, (uint32_t)blk), p.rk);
+        const uint4 w = philox_rk(make_uint4((uint32_t)eo + rng_eo, sweep, sw_creutz, (uint32_t)blk), p.rk);
         bool first_ok;
         float val;
         const bool over = blk >= p.max_blocks;  // only with a cap of two trials
@@ -169,11 +176,11 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
         flush_done();
     };
 
-    int base = blockIdx.x * kCrThreads + (threadIdx.x & ~31);
+    int base = eo_begin + blockIdx.x * kCrThreads + (threadIdx.x & ~31);
     int cur = base + lane;
     float4 v_cur = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     float4 sp_cur = v_cur;  // MEAS: staple terms of nu < MU (the first MU groups)
-    if (base < p.g.vh) {
+    if (base < eo_end) {
         const int e = min(cur, last);
         const Coord x = eo_to_coord(p.g, e, p.parity);
         const int e_p = eo_fwd<MU>(p.g, x, e);
@@ -184,7 +191,7 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
         v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 2>::value>(p.links, p.g, x, e, e_p, p.parity));
         if (MU == 3) sp_cur = v_cur;
     }
-    while (base < p.g.vh) {  // warp-uniform
+    while (base < eo_end) {  // warp-uniform
         const bool valid = cur <= last;
         const int nxt = cur + stride;
         const int en = min(nxt, last);
@@ -193,7 +200,7 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
         // ---- part 0
         NuLinks nl = load_nu_eo<MU, OtherDir<MU, 0>::value>(p.links, p.g, xn, en, en_p, p.parity);
         const DrawSetup d = prepare_draw(v_cur, p.beta);
-        const uint4 w = philox_rk(make_uint4((uint32_t)cur, sweep, sw_creutz, 0u), p.rk);
+        const uint4 w = philox_rk(make_uint4((uint32_t)cur + rng_eo, sweep, sw_creutz, 0u), p.rk);
         float4 v_next = add_nu_terms(make_float4(0.0f, 0.0f, 0.0f, 0.0f), nl);
         float4 sp_next = v_next;
         // ---- part 1
@@ -240,7 +247,7 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
     }
 }
 
-template <int MU, bool MEAS>
+template <int MU, bool MEAS, bool SLAB = false>
 static cudaError_t launch_hb(const HbParams &p, int device, cudaStream_t stream)
 {
     static int blocks_per_sm[64] = {};
@@ -248,15 +255,16 @@ static cudaError_t launch_hb(const HbParams &p, int device, cudaStream_t stream)
     if (device < 0 || device >= 64) device = 0;
     if (!blocks_per_sm[device]) {
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[device],
-                                                                      hb_phase_kernel<MU, MEAS>, kCrThreads, 0);
+                                                                      hb_phase_kernel<MU, MEAS, SLAB>, kCrThreads, 0);
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&num_sms[device], cudaDevAttrMultiProcessorCount, device);
         if (e != cudaSuccess) return e;
         if (blocks_per_sm[device] < 1) blocks_per_sm[device] = 1;
     }
-    const int want = (p.g.vh + kCrThreads - 1) / kCrThreads;
+    const int n = SLAB ? p.slab.eo_end - p.slab.eo_begin : p.g.vh;
+    const int want = (n + kCrThreads - 1) / kCrThreads;
     const int grid = std::max(1, std::min(std::min(want, blocks_per_sm[device] * num_sms[device]), kFusedSlots));
-    hb_phase_kernel<MU, MEAS><<<grid, kCrThreads, 0, stream>>>(p);
+    hb_phase_kernel<MU, MEAS, SLAB><<<grid, kCrThreads, 0, stream>>>(p);
     return cudaGetLastError();
 }
 
@@ -290,6 +298,34 @@ su2_status launch_hb_phase(su2_lattice *lat, int mu, int parity, uint32_t sweep,
         case 2: e = launch_hb<2, false>(p, lat->device, lat->stream); break;
         default: e = launch_hb<3, false>(p, lat->device, lat->stream); break;
         }
+    }
+    SU2_CUDA(e);
+    return SU2_OK;
+}
+
+su2_status launch_hb_phase_slab(su2_lattice *lat, int mu, int parity_local, uint32_t sweep, const SlabRange &r)
+{
+    if (lat->sampler == SU2_SAMPLER_KP) return launch_kp_phase_slab(lat, mu, parity_local, sweep, r);
+    HbParams p;
+    p.gate = nullptr;
+    p.links = lat->links;
+    p.g = geom_of(lat);
+    p.rk = make_round_keys(lat->seed);
+    p.parity = parity_local;
+    p.beta = (float)lat->beta;
+    p.sweep = sweep;
+    p.sweep_dev = nullptr;
+    p.max_blocks = lat->max_trials / 2;
+    p.trial_slots = lat->scratch.trials;
+    p.flags = lat->scratch.flags;
+    p.plaq = nullptr;
+    p.slab = r;
+    cudaError_t e;
+    switch (mu) {
+    case 0: e = launch_hb<0, false, true>(p, lat->device, lat->stream); break;
+    case 1: e = launch_hb<1, false, true>(p, lat->device, lat->stream); break;
+    case 2: e = launch_hb<2, false, true>(p, lat->device, lat->stream); break;
+    default: e = launch_hb<3, false, true>(p, lat->device, lat->stream); break;
     }
     SU2_CUDA(e);
     return SU2_OK;

@@ -38,6 +38,7 @@ struct KpParams {
     unsigned int *flags;
     const unsigned int *gate;  // skip the phase while *gate == 1 (learned sweeps)
     double *plaq;              // measuring phases: block partials of the plaquettes of planes (nu < mu, mu)
+    SlabRange slab;            // SLAB kernels: the interior eo range and the global keys of its random numbers
 };
 
 // One trial (block t of the KP stream): a0 = 1 - 2 u, and whether it is
@@ -75,9 +76,14 @@ constexpr int kRetryCap = 64;  // per warp: at most 31 left over + 32 pushed by 
 // results, so the main path has no divergent branch.  MEAS: the plaquette
 // contributions (1/2) Tr U'S, S the staple terms of nu < MU, as in the
 // Creutz kernel.
-template <int MU, bool MEAS>
+template <int MU, bool MEAS, bool SLAB>
 __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(const KpParams p)
 {
+    // a time slab: interior eo range, random numbers of the global site
+    const int eo_begin = SLAB ? p.slab.eo_begin : 0;
+    const int eo_end = SLAB ? p.slab.eo_end : p.g.vh;
+    const uint32_t rng_eo = SLAB ? p.slab.rng_eo : 0u;
+    const uint32_t rng_parity = SLAB ? (uint32_t)p.slab.rng_parity : (uint32_t)p.parity;
     if (p.gate != nullptr && *(volatile const unsigned int *)p.gate == 1u) return;
     __shared__ float4 s_ut[kKpWarps][kRetryCap];
     __shared__ float4 s_sp[MEAS ? kKpWarps : 1][kRetryCap];
@@ -88,9 +94,9 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
     const int wib = threadIdx.x >> 5;
     const unsigned int lanes_below = (1u << lane) - 1u;
     const int stride = gridDim.x * kKpThreads;
-    const int last = p.g.vh - 1;
-    const uint32_t sw_kp = stream_word(kKennedyPendleton, (uint32_t)p.parity, MU);
-    const uint32_t sw_dir = stream_word(kDirection, (uint32_t)p.parity, MU);
+    const int last = eo_end - 1;
+    const uint32_t sw_kp = stream_word(kKennedyPendleton, rng_parity, MU);
+    const uint32_t sw_dir = stream_word(kDirection, rng_parity, MU);
     unsigned int trials = 0;
     double plaq = 0.0;
     int queued = 0;  // warp-uniform length of the retry queue
@@ -106,11 +112,11 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
             float a0 = 0.0f;
             int t = 1;
             for (; t < p.max_trials; ++t)
-                if (kp_trial(philox_rk(make_uint4((uint32_t)eo, sweep, sw_kp, (uint32_t)t), p.rk), two_bk, a0))
+                if (kp_trial(philox_rk(make_uint4((uint32_t)eo + rng_eo, sweep, sw_kp, (uint32_t)t), p.rk), two_bk, a0))
                     break;
             if (t < p.max_trials) {
                 const float4 out =
-                    direction_update(a0, ut, philox_rk(make_uint4((uint32_t)eo, sweep, sw_dir, 0u), p.rk));
+                    direction_update(a0, ut, philox_rk(make_uint4((uint32_t)eo + rng_eo, sweep, sw_dir, 0u), p.rk));
                 p.links[link_index(p.g, MU, p.parity, eo)] = out;
                 if (MEAS) plaq += (double)qmul_re(out, s_sp[MEAS ? wib : 0][q]);
                 trials += (unsigned int)(t + 1);
@@ -122,11 +128,11 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
         __syncwarp();
     };
 
-    int base = blockIdx.x * kKpThreads + (wib << 5);
+    int base = eo_begin + blockIdx.x * kKpThreads + (wib << 5);
     int cur = base + lane;
     float4 v_cur = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     float4 sp_cur = v_cur;  // MEAS: staple terms of nu < MU (the first MU groups)
-    if (base < p.g.vh) {
+    if (base < eo_end) {
         const int e = min(cur, last);
         const Coord x = eo_to_coord(p.g, e, p.parity);
         const int e_p = eo_fwd<MU>(p.g, x, e);
@@ -137,7 +143,7 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
         v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 2>::value>(p.links, p.g, x, e, e_p, p.parity));
         if (MU == 3) sp_cur = v_cur;
     }
-    while (base < p.g.vh) {  // warp-uniform
+    while (base < eo_end) {  // warp-uniform
         const bool valid = cur <= last;
         const int nxt = cur + stride;
         const int en = min(nxt, last);
@@ -148,11 +154,11 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
         const float k = __fsqrt_rn(qnorm2(v_cur));
         const float bk = __fmul_rn(p.beta, k);
         const bool use_kp = bk >= kKpMinBk;
-        const float inv_k = __fdiv_rn(1.0f, k);
+        const float inv_k = __frcp_rn(k);
         const float4 ut = make_float4(__fmul_rn(v_cur.x, inv_k), __fmul_rn(-v_cur.y, inv_k),
                                       __fmul_rn(-v_cur.z, inv_k), __fmul_rn(-v_cur.w, inv_k));
-        uint4 w = make_uint4((uint32_t)cur, sweep, sw_kp, 0u);
-        uint4 wd = make_uint4((uint32_t)cur, sweep, sw_dir, 0u);
+        uint4 w = make_uint4((uint32_t)cur + rng_eo, sweep, sw_kp, 0u);
+        uint4 wd = make_uint4((uint32_t)cur + rng_eo, sweep, sw_dir, 0u);
         philox2_rk(w, wd, p.rk);
         float4 v_next = add_nu_terms(make_float4(0.0f, 0.0f, 0.0f, 0.0f), nl);
         float4 sp_next = v_next;
@@ -164,7 +170,7 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
         const bool park = valid && use_kp && !first_ok;
         if (valid && !use_kp) {  // beta k < 2: Creutz's method
             float4 out;
-            const int n = heatbath_draw(v_cur, p.beta, p.rk, (uint32_t)cur, sweep, (uint32_t)p.parity, MU, out);
+            const int n = heatbath_draw(v_cur, p.beta, p.rk, (uint32_t)cur + rng_eo, sweep, rng_parity, MU, out);
             if (n > 0) {
                 p.links[link_index(p.g, MU, p.parity, cur)] = out;
                 if (MEAS) plaq += (double)qmul_re(out, sp_cur);
@@ -215,22 +221,23 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
     }
 }
 
-template <int MU, bool MEAS>
+template <int MU, bool MEAS, bool SLAB = false>
 static cudaError_t launch_kp(const KpParams &p, int device, cudaStream_t stream)
 {
     static int per_sm[64] = {};
     static int sms[64] = {};
     if (device < 0 || device >= 64) device = 0;
     if (!per_sm[device]) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[device], kp_phase_kernel<MU, MEAS>,
-                                                                      kKpThreads, 0);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[device],
+                                                                      kp_phase_kernel<MU, MEAS, SLAB>, kKpThreads, 0);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms[device], cudaDevAttrMultiProcessorCount, device);
         if (e != cudaSuccess) return e;
         per_sm[device] = std::max(1, per_sm[device]);
     }
-    const int want = (p.g.vh + kKpThreads - 1) / kKpThreads;
+    const int n = SLAB ? p.slab.eo_end - p.slab.eo_begin : p.g.vh;
+    const int want = (n + kKpThreads - 1) / kKpThreads;
     const int grid = std::max(1, std::min(std::min(want, per_sm[device] * sms[device]), kFusedSlots));
-    kp_phase_kernel<MU, MEAS><<<grid, kKpThreads, 0, stream>>>(p);
+    kp_phase_kernel<MU, MEAS, SLAB><<<grid, kKpThreads, 0, stream>>>(p);
     return cudaGetLastError();
 }
 
@@ -263,6 +270,33 @@ su2_status launch_kp_phase(su2_lattice *lat, int mu, int parity, uint32_t sweep,
         case 2: e = launch_kp<2, false>(p, lat->device, lat->stream); break;
         default: e = launch_kp<3, false>(p, lat->device, lat->stream); break;
         }
+    }
+    SU2_CUDA(e);
+    return SU2_OK;
+}
+
+su2_status launch_kp_phase_slab(su2_lattice *lat, int mu, int parity_local, uint32_t sweep, const SlabRange &r)
+{
+    KpParams p;
+    p.links = lat->links;
+    p.g = geom_of(lat);
+    p.rk = make_round_keys(lat->seed);
+    p.parity = parity_local;
+    p.beta = (float)lat->beta;
+    p.sweep = sweep;
+    p.sweep_dev = nullptr;
+    p.max_trials = lat->max_trials;
+    p.trial_slots = lat->scratch.trials;
+    p.flags = lat->scratch.flags;
+    p.gate = nullptr;
+    p.plaq = nullptr;
+    p.slab = r;
+    cudaError_t e;
+    switch (mu) {
+    case 0: e = launch_kp<0, false, true>(p, lat->device, lat->stream); break;
+    case 1: e = launch_kp<1, false, true>(p, lat->device, lat->stream); break;
+    case 2: e = launch_kp<2, false, true>(p, lat->device, lat->stream); break;
+    default: e = launch_kp<3, false, true>(p, lat->device, lat->stream); break;
     }
     SU2_CUDA(e);
     return SU2_OK;

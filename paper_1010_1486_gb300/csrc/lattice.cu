@@ -72,10 +72,7 @@ __global__ void cold_start_kernel(float4 *__restrict__ links, int64_t n)
         links[i] = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
 }
 
-// Haar-random links (Marsaglia 1972): two points uniform in the unit disk,
-// (x1,x2) with s1 and (x3,x4) with s2, give (x1, x2, x3 f, x4 f),
-// f = sqrt((1-s1)/s2), uniform on S^3.  Candidate pair m uses words 2(m&1),
-// 2(m&1)+1 of hot-start block m>>1 of the link's counter.
+// Haar-random links (hot_link in su2_device.cuh), link (mu, parity, eo).
 __global__ void hot_start_kernel(float4 *__restrict__ links, Geom g, const RoundKeys rk,
                                  unsigned int *__restrict__ flags)
 {
@@ -84,32 +81,8 @@ __global__ void hot_start_kernel(float4 *__restrict__ links, Geom g, const Round
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int group = (int)(idx / g.vh);
         const int eo = (int)(idx - (int64_t)group * g.vh);
-        const int mu = group >> 1, parity = group & 1;
-        float px[2] = {0.0f, 0.0f}, py[2] = {0.0f, 0.0f}, ps[2] = {1.0f, 1.0f};
-        int found = 0;
-        uint4 w = make_uint4(0u, 0u, 0u, 0u);
-        for (int m = 0; m < 64 && found < 2; ++m) {
-            if ((m & 1) == 0)
-                w = philox_rk(make_uint4((uint32_t)eo, 0u, stream_word(kHotStart, (uint32_t)parity, (uint32_t)mu),
-                                         (uint32_t)(m >> 1)),
-                              rk);
-            const float x = __fsub_rn(__fmul_rn(2.0f, uniform01((m & 1) ? w.z : w.x)), 1.0f);
-            const float y = __fsub_rn(__fmul_rn(2.0f, uniform01((m & 1) ? w.w : w.y)), 1.0f);
-            const float s = __fmaf_rn(x, x, __fmul_rn(y, y));
-            if (s < 1.0f && s > 0.0f) {
-                px[found] = x;
-                py[found] = y;
-                ps[found] = s;
-                ++found;
-            }
-        }
-        float4 out = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
-        if (found == 2) {
-            const float f = __fsqrt_rn(__fdiv_rn(__fsub_rn(1.0f, ps[0]), ps[1]));
-            out = make_float4(px[0], py[0], __fmul_rn(px[1], f), __fmul_rn(py[1], f));
-        } else {
-            atomicAdd(&flags[1], 1u);
-        }
+        float4 out;
+        if (!hot_link((uint32_t)eo, (uint32_t)(group & 1), (uint32_t)(group >> 1), rk, out)) atomicAdd(&flags[1], 1u);
         links[idx] = out;
     }
 }

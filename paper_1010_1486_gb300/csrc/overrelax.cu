@@ -31,7 +31,7 @@ __device__ __forceinline__ float4 staple_direction(float4 v)
 {
     const float k = __fsqrt_rn(qnorm2(v));
     if (!(k > 0.0f)) return make_float4(1.0f, 0.0f, 0.0f, 0.0f);
-    const float inv_k = __fdiv_rn(1.0f, k);
+    const float inv_k = __frcp_rn(k);
     return make_float4(__fmul_rn(v.x, inv_k), __fmul_rn(-v.y, inv_k), __fmul_rn(-v.z, inv_k),
                        __fmul_rn(-v.w, inv_k));
 }

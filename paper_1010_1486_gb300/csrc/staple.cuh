@@ -7,7 +7,8 @@
 
 namespace su2 {
 
-// Staple of U_mu(x) (Sec. 2), nu ascending, forward then backward term.
+// Staple of U_mu(x) (Sec. 2), nu ascending, forward then backward term, each
+// term's second product fused with the running sum (qmul_add).
 template <int MU>
 __device__ __forceinline__ float4 staple_at(const float4 *__restrict__ L, const Geom &g, const Coord &x, int parity)
 {
@@ -26,8 +27,8 @@ __device__ __forceinline__ float4 staple_at(const float4 *__restrict__ L, const 
         const float4 d = __ldg(L + link_index(g, nu, parity, e_xpm));
         const float4 e = __ldg(L + link_index(g, MU, op, e_xm));
         const float4 f = __ldg(L + link_index(g, nu, op, e_xm));
-        v = qadd(v, qmul(qmul(a, qdag(b)), qdag(c)));
-        v = qadd(v, qmul(qmul(qdag(d), qdag(e)), f));
+        v = qmul_add(qmul(a, qdag(b)), qdag(c), v);
+        v = qmul_add(qmul(qdag(d), qdag(e)), f, v);
     }
     return v;
 }
@@ -41,9 +42,8 @@ struct NuLinks {
 
 __device__ __forceinline__ float4 add_nu_terms(float4 v, const NuLinks &n)
 {
-    const float4 fwd = qmul(qmul(n.nu_xp, qdag(n.mu_xn)), qdag(n.nu_x));
-    const float4 bwd = qmul(qmul(qdag(n.nu_xpm), qdag(n.mu_xm)), n.nu_xm);
-    return qadd(qadd(v, fwd), bwd);
+    v = qmul_add(qmul(n.nu_xp, qdag(n.mu_xn)), qdag(n.nu_x), v);
+    return qmul_add(qmul(qdag(n.nu_xpm), qdag(n.mu_xm)), n.nu_xm, v);
 }
 
 // Even/odd neighbour indices straight from the coordinates.  The strides of

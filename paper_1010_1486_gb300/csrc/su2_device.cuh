@@ -205,6 +205,16 @@ __device__ __forceinline__ float4 qmul(float4 a, float4 b)
                        chain4(a.x, b.w, a.w, b.x, -a.y, b.z, a.z, b.y));
 }
 
+// a b + c: the chains of qmul with the innermost product fused with c's
+// component (one rounding per component), as the staple accumulates its terms.
+__device__ __forceinline__ float4 qmul_add(float4 a, float4 b, float4 c)
+{
+    return make_float4(__fmaf_rn(a.x, b.x, __fmaf_rn(-a.y, b.y, __fmaf_rn(-a.z, b.z, __fmaf_rn(-a.w, b.w, c.x)))),
+                       __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, __fmaf_rn(-a.z, b.w, __fmaf_rn(a.w, b.z, c.y)))),
+                       __fmaf_rn(a.x, b.z, __fmaf_rn(a.z, b.x, __fmaf_rn(-a.w, b.y, __fmaf_rn(a.y, b.w, c.z)))),
+                       __fmaf_rn(a.x, b.w, __fmaf_rn(a.w, b.x, __fmaf_rn(-a.y, b.z, __fmaf_rn(a.z, b.y, c.w)))));
+}
+
 // Real part only: (1/2) Tr(a b).
 __device__ __forceinline__ float qmul_re(float4 a, float4 b)
 {
@@ -249,14 +259,14 @@ __device__ __forceinline__ DrawSetup prepare_draw(float4 v, float beta)
     const float k = __fsqrt_rn(qnorm2(v));
     d.ut = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
     if (k > 0.0f) {
-        const float inv_k = __fdiv_rn(1.0f, k);
+        const float inv_k = __frcp_rn(k);
         d.ut = make_float4(__fmul_rn(v.x, inv_k), __fmul_rn(-v.y, inv_k), __fmul_rn(-v.z, inv_k),
                            __fmul_rn(-v.w, inv_k));
     }
     d.bk = __fmul_rn(beta, k);
     d.e = 0.0f;
     if (!(d.bk < kHaarBelow) && d.bk <= kExpCutoff) d.e = exp_series(__fmul_rn(-2.0f, d.bk));
-    d.ibk = d.bk < kHaarBelow ? 0.0f : __fdiv_rn(1.0f, d.bk);
+    d.ibk = d.bk < kHaarBelow ? 0.0f : __frcp_rn(d.bk);
     return d;
 }
 
@@ -414,6 +424,36 @@ __device__ __forceinline__ int heatbath_draw(float4 v, float beta, const RoundKe
     if (trials == 0) return 0;
     out = direction_update(a0, s.ut, philox_rk(make_uint4(eo, sweep, stream_word(kDirection, parity, mu), 0u), rk));
     return trials;
+}
+
+// Haar-random link (Marsaglia 1972), the hot start (Sec. 4.1): two points
+// uniform in the unit disk, (x1,x2) with s1 and (x3,x4) with s2, give
+// (x1, x2, x3 f, x4 f), f = sqrt((1-s1)/s2), uniform on S^3.  Candidate pair m
+// uses words 2(m&1), 2(m&1)+1 of hot-start block m>>1 of the link's counter
+// (even/odd index eo, sweep 0, parity, mu).  Returns false (out = identity)
+// if 64 pairs gave no two points.
+__device__ __forceinline__ bool hot_link(uint32_t eo, uint32_t parity, uint32_t mu, const RoundKeys &rk, float4 &out)
+{
+    float px[2] = {0.0f, 0.0f}, py[2] = {0.0f, 0.0f}, ps[2] = {1.0f, 1.0f};
+    int found = 0;
+    uint4 w = make_uint4(0u, 0u, 0u, 0u);
+    for (int m = 0; m < 64 && found < 2; ++m) {
+        if ((m & 1) == 0) w = philox_rk(make_uint4(eo, 0u, stream_word(kHotStart, parity, mu), (uint32_t)(m >> 1)), rk);
+        const float x = __fsub_rn(__fmul_rn(2.0f, uniform01((m & 1) ? w.z : w.x)), 1.0f);
+        const float y = __fsub_rn(__fmul_rn(2.0f, uniform01((m & 1) ? w.w : w.y)), 1.0f);
+        const float s = __fmaf_rn(x, x, __fmul_rn(y, y));
+        if (s < 1.0f && s > 0.0f) {
+            px[found] = x;
+            py[found] = y;
+            ps[found] = s;
+            ++found;
+        }
+    }
+    out = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+    if (found < 2) return false;
+    const float f = __fsqrt_rn(__fdiv_rn(__fsub_rn(1.0f, ps[0]), ps[1]));
+    out = make_float4(px[0], py[0], __fmul_rn(px[1], f), __fmul_rn(py[1], f));
+    return true;
 }
 
 // Division by an invariant positive integer d < 2^31 with a multiply-high and

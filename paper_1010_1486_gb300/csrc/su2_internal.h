@@ -95,6 +95,16 @@ struct su2_lattice {
 
 namespace su2 {
 
+// The part of a phase that a time slab runs (Sec. 4, multi-GPU part): the
+// even/odd indices [eo_begin, eo_end) of its interior slices, and the keys of
+// their random numbers in the whole lattice -- even/odd index + rng_eo and the
+// global parity rng_parity.  A whole lattice is [0, vh), 0, its own parity.
+struct SlabRange {
+    int eo_begin = 0, eo_end = 0;
+    uint32_t rng_eo = 0;
+    int rng_parity = 0;
+};
+
 // Error bookkeeping (per thread).
 void set_last_error(const std::string &msg);
 su2_status cuda_fail(cudaError_t e, const char *what);
@@ -176,6 +186,10 @@ su2_status launch_hot_start(su2_lattice *lat);
 su2_status launch_hb_phase(su2_lattice *lat, int mu, int parity, uint32_t sweep,
                            const unsigned int *gate = nullptr);
 su2_status launch_kp_phase(su2_lattice *lat, int mu, int parity, uint32_t sweep, const unsigned int *gate);
+// A phase on the interior of a time slab: parity_local selects the slab's
+// even/odd arrays, r the eo range and the random-number keys (sampler as set).
+su2_status launch_hb_phase_slab(su2_lattice *lat, int mu, int parity_local, uint32_t sweep, const SlabRange &r);
+su2_status launch_kp_phase_slab(su2_lattice *lat, int mu, int parity_local, uint32_t sweep, const SlabRange &r);
 su2_status launch_reunitarize(su2_lattice *lat);
 // Observables: write the value into *dst (device memory) without synchronising.
 su2_status launch_plaquette(su2_lattice *lat, double *dst);

@@ -125,6 +125,18 @@ _SIGS = {
     "su2_get_proposal_table": [_P, _P],
     "su2_learned_generate": [_P, _i32, _i32, _f64, _P, _P, ctypes.POINTER(su2_learned_stats)],
     "su2_learned_sweep": [_P, _i32, ctypes.POINTER(su2_learned_stats)],
+    "su2_slab_create": [_i32, _i32, _i32, _i32, _f64, _u64, _i32, _P, ctypes.POINTER(_P)],
+    "su2_slab_destroy": [_P],
+    "su2_slab_set_sampler": [_P, _i32],
+    "su2_slab_phase": [_P, _i32, _i32],
+    "su2_slab_pack": [_P, _i32, _i32, _i32, _P],
+    "su2_slab_unpack": [_P, _i32, _i32, _i32, _P],
+    "su2_slab_exchange": [_P, _P, _i32, _i32],
+    "su2_slab_sync": [_P],
+    "su2_slab_get_links": [_P, _P],
+    "su2_slab_set_links": [_P, _P],
+    "su2_slab_stats": [_P, _P, ctypes.POINTER(_u64)],
+    "su2_slab_info": [_P, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_u32)],
     "su2_collect_pairs": [_P, _i32, _i32, _i32, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)],
     "su2_trainer_create": [_P, _u64, _P, ctypes.POINTER(_P)],
     "su2_trainer_destroy": [_P],
@@ -143,6 +155,8 @@ _lib.su2_last_error.argtypes = []
 _lib.su2_last_error.restype = ctypes.c_char_p
 _lib.su2_abi_version.argtypes = []
 _lib.su2_abi_version.restype = ctypes.c_int
+_lib.su2_slab_boundary_bytes.argtypes = [_P]
+_lib.su2_slab_boundary_bytes.restype = ctypes.c_size_t
 
 
 def declared_symbols() -> list[str]:
@@ -434,6 +448,71 @@ def su2_learned_sweep(lat: int, nsweeps: int):
     st = su2_learned_stats()
     _check(_lib.su2_learned_sweep(lat, nsweeps, ctypes.byref(st)), "su2_learned_sweep")
     return st.as_dict()
+
+
+# ------------------------------------------------------------ time slabs
+def su2_slab_create(ns: int, nt: int, t0: int, nt_local: int, beta: float, seed: int, start: int = 1,
+                    stream=None) -> int:
+    h = _P()
+    _check(_lib.su2_slab_create(ns, nt, t0, nt_local, float(beta), int(seed), int(start), _stream_handle(stream),
+                                ctypes.byref(h)), "su2_slab_create")
+    return h.value
+
+
+def su2_slab_destroy(h: int) -> None:
+    _check(_lib.su2_slab_destroy(h), "su2_slab_destroy")
+
+
+def su2_slab_set_sampler(h: int, sampler: int) -> None:
+    _check(_lib.su2_slab_set_sampler(h, int(sampler)), "su2_slab_set_sampler")
+
+
+def su2_slab_phase(h: int, mu: int, parity: int) -> None:
+    _check(_lib.su2_slab_phase(h, mu, parity), "su2_slab_phase")
+
+
+def su2_slab_boundary_bytes(h: int) -> int:
+    return int(_lib.su2_slab_boundary_bytes(h))
+
+
+def su2_slab_pack(h: int, mu: int, parity: int, side: int, dst_ptr: int) -> None:
+    _check(_lib.su2_slab_pack(h, mu, parity, side, dst_ptr), "su2_slab_pack")
+
+
+def su2_slab_unpack(h: int, mu: int, parity: int, side: int, src_ptr: int) -> None:
+    _check(_lib.su2_slab_unpack(h, mu, parity, side, src_ptr), "su2_slab_unpack")
+
+
+def su2_slab_exchange(lower: int, upper: int, mu: int, parity: int) -> None:
+    _check(_lib.su2_slab_exchange(lower, upper, mu, parity), "su2_slab_exchange")
+
+
+def su2_slab_sync(h: int) -> None:
+    _check(_lib.su2_slab_sync(h), "su2_slab_sync")
+
+
+def su2_slab_get_links(h: int, ns: int, nt_local: int) -> np.ndarray:
+    out = np.empty((ns ** 3 * (nt_local + 2), 4, 4), dtype=np.float32)
+    _check(_lib.su2_slab_get_links(h, _host_ptr(out)), "su2_slab_get_links")
+    return out
+
+
+def su2_slab_set_links(h: int, links: np.ndarray) -> None:
+    links = np.ascontiguousarray(links, dtype=np.float32)
+    _check(_lib.su2_slab_set_links(h, _host_ptr(links)), "su2_slab_set_links")
+
+
+def su2_slab_stats(h: int):
+    trials = np.zeros(8, dtype=np.uint64)
+    fails = _u64()
+    _check(_lib.su2_slab_stats(h, _host_ptr(trials), ctypes.byref(fails)), "su2_slab_stats")
+    return [int(t) for t in trials], int(fails.value)
+
+
+def su2_slab_info(h: int):
+    t0, ntl, sw = _i32(), _i32(), _u32()
+    _check(_lib.su2_slab_info(h, ctypes.byref(t0), ctypes.byref(ntl), ctypes.byref(sw)), "su2_slab_info")
+    return t0.value, ntl.value, sw.value
 
 
 def su2_collect_pairs(lat: int, mu: int, parity: int, stride: int, dev_ptr: int, cap: int) -> int:
