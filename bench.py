@@ -48,8 +48,18 @@ BYTES_PER_LEARNED_UPDATE = 144  # + the old link of the updated direction and pa
 BYTES_PER_OR_UPDATE = 144  # over-relaxation: the staple links, the old link, the new link
 N_OR = 3  # over-relaxation sweeps after each heat-bath sweep in the compound form
 TRAIN_BATCH = 16384  # training mini-batch of the learned proposal
-HB_SOURCES = ["paper_1010_1486_gb300/csrc/heatbath.cu", "paper_1010_1486_gb300/csrc/su2_device.cuh"]
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "hb_phase_48x48x48x48_beta6.md")
+# the phase kernel of each plain sampler: its source files (for the source
+# digest that ties a committed ncu summary to the current kernel) and summary
+SAMPLERS = {
+    "kp": {"kernel": "kp_phase_kernel", "name": "Kennedy-Pendleton",
+           "sources": ["paper_1010_1486_gb300/csrc/kp.cu", "paper_1010_1486_gb300/csrc/su2_device.cuh",
+                       "paper_1010_1486_gb300/csrc/staple.cuh"],
+           "profile": os.path.join(ROOT, "profiles", "kp_phase_48x48x48x48_beta6.md")},
+    "creutz": {"kernel": "hb_phase_kernel", "name": "Creutz",
+               "sources": ["paper_1010_1486_gb300/csrc/heatbath.cu", "paper_1010_1486_gb300/csrc/su2_device.cuh",
+                           "paper_1010_1486_gb300/csrc/staple.cuh", "paper_1010_1486_gb300/csrc/creutz_queue.cuh"],
+               "profile": os.path.join(ROOT, "profiles", "hb_phase_48x48x48x48_beta6.md")},
+}
 
 
 def parse_args(argv=None):
@@ -68,6 +78,9 @@ def parse_args(argv=None):
     ap.add_argument("--learned-pairs", type=int, default=1_000_000, help="training pairs (0 = skip the learned form)")
     ap.add_argument("--train-steps", type=int, default=3000, help="Adam steps of each of the two training stages")
     ap.add_argument("--batched-steps", type=int, default=200, help="sweeps of the 64-lattice batch (0 = skip)")
+    ap.add_argument("--sampler", choices=sorted(SAMPLERS), default="kp",
+                    help="a0 sampler of the headline plain heat bath (both are exact; kp = Kennedy-Pendleton)")
+    ap.add_argument("--small", type=int, default=1, help="time the small, L2-resident workloads too (0 = skip)")
     return ap.parse_args(argv)
 
 
@@ -173,15 +186,16 @@ def source_digest(paths) -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic_per_launch():
-    """DRAM bytes per phase launch from the committed ncu summary, if it was
-    taken on the current source of the heat-bath kernel; else None."""
-    if not os.path.exists(PROFILE_SUMMARY):
+def ncu_traffic_per_launch(sampler: str):
+    """DRAM bytes per phase launch from the committed ncu summary of that
+    sampler's kernel, if it was taken on the current source; else None."""
+    spec = SAMPLERS[sampler]
+    if not os.path.exists(spec["profile"]):
         return None
-    text = open(PROFILE_SUMMARY).read()
+    text = open(spec["profile"]).read()
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
     s = re.search(r"source_sha:\s*([0-9a-f]+)", text)
-    if not m or not s or s.group(1) != source_digest(HB_SOURCES):
+    if not m or not s or s.group(1) != source_digest(spec["sources"]):
         return None
     return float(m.group(1))
 
@@ -198,8 +212,10 @@ def run_ours(args, dist):
     su2.use_torch_allocator()
     stream = torch.cuda.Stream()
     seed = SEED + dist.rank
+    sampler = su2.SU2_SAMPLER_KP if args.sampler == "kp" else su2.SU2_SAMPLER_CREUTZ
     lat = su2.su2_create(NS, NT, BETA, seed, su2.SU2_HOT, stream=stream)
     try:
+        su2.su2_set_sampler(lat, sampler)
         su2.su2_generate(lat, args.warmup, 1, 0)
         su2.su2_set_timing(lat, True)
         gpu_index = dist.local_rank
@@ -245,6 +261,7 @@ def run_ours(args, dist):
     batched = None
     if args.batched_steps > 0:
         batched = run_batched(args, dist, su2, torch)
+    small = run_small(args, dist, su2, torch) if args.small else None
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
@@ -252,11 +269,12 @@ def run_ours(args, dist):
         "vs_baseline": value / PAPER_RATE, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{NS}^4 lattice, beta={BETA}, hot start (Philox seed {SEED}+rank), one step = "
                                "heat-bath sweep (8 even/odd phases) + plaquette + Polyakov loop",
-                   "lattice": [NS, NS, NS, NT], "beta": BETA, "start": "hot", "form": "plain heat bath (Creutz)",
+                   "lattice": [NS, NS, NS, NT], "beta": BETA, "start": "hot",
+                   "form": f"plain heat bath ({SAMPLERS[args.sampler]['name']} a0 sampler)",
                    "parallelism": "independent replicas" if dist.world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (340 MB of links vs 129 MB L2), no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": ncu_traffic_per_launch(), "kernel": "hb_phase_kernel",
+                     "traffic": ncu_traffic_per_launch(args.sampler), "kernel": SAMPLERS[args.sampler]["kernel"],
                      "peak_source": f"{peak_kind} hbm_gbs", "bytes_per_launch": BYTES_PER_UPDATE * (VOL // 2),
                      "avg_launch_us": phase_s * 1e6},
         "e2e": e2e,
@@ -266,6 +284,7 @@ def run_ours(args, dist):
         "plaquette_last": float(plaq[-1]), "polyakov_last": float(poly[-1]),
         "forms": forms,
         "batched": batched,
+        "small_workloads": small,
     }
     if forms and "value_tau_adjusted" in forms:
         result["value_tau_adjusted"] = forms["value_tau_adjusted"]
@@ -284,20 +303,33 @@ def timed(stream, torch, dist, fn):
 
 
 def compare_forms(args, dist, lat, su2, torch, stream, tau_int):
-    """Plain heat bath against the learned proposal on the same thermalised
-    48^4 lattice.  After `therm` more sweeps: (beta k, a0) pairs from the plain
-    sampler, training on the GPU, then both forms timed back to back, then
-    interleaved blocks plain / learned / plain ... for tau_int and the
-    plaquette: every learned block is compared with the plain blocks around
-    it, interpolated at its own position (analysis.interleaved_offset), so a
-    slow drift of the lattice cancels."""
-    from paper_1010_1486_gb300.analysis import interleaved_offset
+    """The plain heat bath with each exact a0 sampler (Kennedy-Pendleton,
+    Creutz), the learned proposal and Kennedy-Pendleton + over-relaxation on
+    the same thermalised 48^4 lattice.
+
+    1. Thermalisation: `therm` compound sweeps (one Kennedy-Pendleton sweep +
+       N_OR over-relaxation sweeps; over-relaxation moves the slow, long-
+       wavelength modes that a heat bath alone relaxes diffusively).
+    2. (beta k, a0) pairs from the plain sampler, training on the GPU.
+    3. Each form timed over `steps` sweeps (rates and kernel rooflines).
+    4. Interleaved blocks per round: Kennedy-Pendleton (the reference),
+       learned, Creutz, Kennedy-Pendleton + over-relaxation; a final
+       reference block.  Each sweep records the plaquette and the Polyakov
+       loop.  tau_int per form for the plaquette and for |L| (a slow
+       observable), the blocks of a form pooled as replicas about their common
+       mean; the drift of the reference blocks against their scatter; each
+       form's plaquette against the reference interpolated at its blocks'
+       centres (analysis.interleaved_offset)."""
+    from paper_1010_1486_gb300 import learn
+    from paper_1010_1486_gb300.analysis import block_drift, interleaved_offset
 
     import numpy as np
 
-    from paper_1010_1486_gb300 import learn
-
+    KP, CR = su2.SU2_SAMPLER_KP, su2.SU2_SAMPLER_CREUTZ
+    su2.su2_set_sampler(lat, KP)
+    su2.su2_set_overrelax(lat, N_OR)
     su2.su2_generate(lat, args.therm, 0, 0)
+    su2.su2_set_overrelax(lat, 0)
     t0 = time.perf_counter()
     pairs = learn.collect(lat, NS, NT, args.learned_pairs, sweeps_between=1)
     t1 = time.perf_counter()
@@ -309,133 +341,110 @@ def compare_forms(args, dist, lat, su2, torch, stream, tau_int):
     su2.su2_set_proposal(lat, w, s_lo, s_hi, 256)
     peak, _ = measured_peaks()
 
-    # plain, timed on the thermalised lattice
+    def roof(kernel, phase_s, nbytes):
+        a = nbytes * (VOL // 2) / phase_s / 1e9
+        return {"bound": "hbm", "kernel": kernel, "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak,
+                "avg_launch_us": phase_s * 1e6, "bytes_per_launch": nbytes * (VOL // 2)}
+
     su2.su2_set_timing(lat, True)
-    ms_p, (_, _, st_p) = timed(stream, torch, dist, lambda: su2.su2_generate(lat, args.steps, 1, 0))
-    plain_phase_s = st_p["kernel_ms"] / st_p["kernel_launches"] * 1e-3
-    value_plain = dist.reduce(float(st_p["link_updates"]), "sum") / (ms_p * 1e-3)
-    # plain with the Kennedy-Pendleton sampler, timed
-    su2.su2_set_sampler(lat, su2.SU2_SAMPLER_KP)
-    su2.su2_generate(lat, 2, 1, 0)
-    ms_k, (_, _, st_k) = timed(stream, torch, dist, lambda: su2.su2_generate(lat, args.steps, 1, 0))
-    su2.su2_set_sampler(lat, su2.SU2_SAMPLER_CREUTZ)
-    kp_phase_s = st_k["kernel_ms"] / st_k["kernel_launches"] * 1e-3
-    value_kp = dist.reduce(float(st_k["link_updates"]), "sum") / (ms_k * 1e-3)
-    # learned, timed
+    out = {"lattice": f"thermalised 48^4, beta = 6.0 (after {args.therm} compound sweeps of Kennedy-Pendleton + "
+                      f"{N_OR} over-relaxation)"}
+    for key, sampler, kernel in (("kennedy_pendleton", KP, "kp_phase_kernel"), ("creutz", CR, "hb_phase_kernel")):
+        su2.su2_set_sampler(lat, sampler)
+        su2.su2_generate(lat, 2, 1, 0)
+        ms, (_, _, st) = timed(stream, torch, dist, lambda: su2.su2_generate(lat, args.steps, 1, 0))
+        phase_s = st["kernel_ms"] / st["kernel_launches"] * 1e-3
+        out[key] = {"value": dist.reduce(float(st["link_updates"]), "sum") / (ms * 1e-3), "unit": UNIT,
+                    "ms_per_step": ms / args.steps, "trials_per_update": sum(st["trials"]) / st["link_updates"],
+                    "roofline": roof(kernel, phase_s, BYTES_PER_UPDATE)}
+    su2.su2_set_sampler(lat, KP)  # the learned sweeps' fallback sampler
     su2.su2_learned_generate(lat, 2, 1, 0.7)
     ms_l, (_, _, st_l) = timed(stream, torch, dist, lambda: su2.su2_learned_generate(lat, args.steps, 1, 0.7))
     learned_phase_s = st_l["kernel_ms"] / max(1, st_l["kernel_launches"]) * 1e-3
-    value_learned = dist.reduce(float(st_l["link_updates"]), "sum") / (ms_l * 1e-3)
-    # compound sweeps: one Kennedy-Pendleton heat-bath sweep + N_OR over-relaxation sweeps, timed
-    su2.su2_set_sampler(lat, su2.SU2_SAMPLER_KP)
+    proposals = st_l["learned_sweeps"] * 4 * VOL
+    out["learned"] = {
+        "value": dist.reduce(float(st_l["link_updates"]), "sum") / (ms_l * 1e-3), "unit": UNIT,
+        "ms_per_step": ms_l / args.steps, "acceptance": sum(st_l["accepted"]) / max(1, proposals),
+        "learned_sweeps": st_l["learned_sweeps"], "fallback_sweeps": st_l["plain_sweeps"],
+        "fallback_sampler": "Kennedy-Pendleton",
+        "roofline": roof("learned_phase_kernel", learned_phase_s, BYTES_PER_LEARNED_UPDATE),
+        "gpu_launches": st_l["kernel_launches"] * 2 + args.steps * 3,
+        "training": {"pairs": args.learned_pairs, "steps": 2 * args.train_steps, "batch": TRAIN_BATCH,
+                     "schedule": f"{args.train_steps} Adam steps at 3e-3, {args.train_steps} at 3e-4",
+                     "collect_s": t1 - t0, "train_s": t2 - t1,
+                     "loss_first": float(losses[:10].mean()), "loss_last": float(losses[-50:].mean())}}
     su2.su2_set_overrelax(lat, N_OR)
     su2.su2_generate(lat, 2, 1, 0)
     n_cmp = max(1, args.steps // (N_OR + 1))
     ms_o, (_, _, st_o) = timed(stream, torch, dist, lambda: su2.su2_generate(lat, n_cmp, 1, 0))
     su2.su2_set_overrelax(lat, 0)
-    su2.su2_set_sampler(lat, su2.SU2_SAMPLER_CREUTZ)
     su2.su2_set_timing(lat, False)
     or_phase_s = st_o["overrelax_ms"] / (8 * st_o["overrelax_sweeps"]) * 1e-3
     compound_per_s = dist.reduce(float(n_cmp), "sum") / (ms_o * 1e-3)
-    proposals = st_l["learned_sweeps"] * 4 * VOL
-
-    out = {"lattice": "thermalised 48^4, beta = 6.0 (after warm-up, timed steps and %d more sweeps)" % args.therm,
-           "plain": {"value": value_plain, "unit": UNIT, "ms_per_step": ms_p / args.steps,
-                     "trials_per_update": sum(st_p["trials"]) / st_p["link_updates"],
-                     "roofline": {"bound": "hbm", "kernel": "hb_phase_kernel",
-                                  "achieved": BYTES_PER_UPDATE * (VOL // 2) / plain_phase_s / 1e9, "peak": peak,
-                                  "unit": "GB/s", "avg_launch_us": plain_phase_s * 1e6}},
-           "plain_kennedy_pendleton": {
-               "value": value_kp, "unit": UNIT, "ms_per_step": ms_k / args.steps,
-               "trials_per_update": sum(st_k["trials"]) / st_k["link_updates"],
-               "roofline": {"bound": "hbm", "kernel": "kp_phase_kernel",
-                            "achieved": BYTES_PER_UPDATE * (VOL // 2) / kp_phase_s / 1e9, "peak": peak,
-                            "unit": "GB/s", "avg_launch_us": kp_phase_s * 1e6}},
-           "learned": {"value": value_learned, "unit": UNIT, "ms_per_step": ms_l / args.steps,
-                       "acceptance": sum(st_l["accepted"]) / max(1, proposals),
-                       "learned_sweeps": st_l["learned_sweeps"], "fallback_sweeps": st_l["plain_sweeps"],
-                       "roofline": {"bound": "hbm", "kernel": "learned_phase_kernel",
-                                    "achieved": BYTES_PER_LEARNED_UPDATE * (VOL // 2) / learned_phase_s / 1e9,
-                                    "peak": peak, "unit": "GB/s", "avg_launch_us": learned_phase_s * 1e6,
-                                    "bytes_per_launch": BYTES_PER_LEARNED_UPDATE * (VOL // 2)},
-                       "gpu_launches": st_l["kernel_launches"] * 2 + args.steps * 3,
-                       "training": {"pairs": args.learned_pairs, "steps": 2 * args.train_steps, "batch": TRAIN_BATCH,
-                                    "schedule": f"{args.train_steps} Adam steps at 3e-3, {args.train_steps} at 3e-4",
-                                    "collect_s": t1 - t0, "train_s": t2 - t1,
-                                    "loss_first": float(losses[:10].mean()), "loss_last": float(losses[-50:].mean())}}}
     out["kp_overrelax"] = {
         "compound_sweep": f"1 Kennedy-Pendleton heat-bath sweep + {N_OR} over-relaxation sweeps",
         "compound_sweeps_per_s": compound_per_s, "ms_per_compound_sweep": ms_o / n_cmp,
         "value": compound_per_s * 4 * VOL * (N_OR + 1), "unit": UNIT + " (heat bath + over-relaxation)",
-        "roofline": {"bound": "hbm", "kernel": "or_phase_kernel",
-                     "achieved": BYTES_PER_OR_UPDATE * (VOL // 2) / or_phase_s / 1e9, "peak": peak,
-                     "unit": "GB/s", "avg_launch_us": or_phase_s * 1e6,
-                     "bytes_per_launch": BYTES_PER_OR_UPDATE * (VOL // 2)}}
-    for form in ("plain", "plain_kennedy_pendleton", "learned", "kp_overrelax"):
-        r = out[form]["roofline"]
-        r["frac"] = r["achieved"] / peak
-    if args.tau_sweeps > 0:
-        nblk = 16  # interleaved blocks per form: the spread of their means gives the plaquette check's error
-        per = max(50, args.tau_sweeps // nblk)
-        plain_blocks, learned_blocks, kp_blocks, or_blocks = [], [], [], []
-        per_or = max(50, per // (N_OR + 1) * 2)
-        for k in range(nblk):
-            plain_blocks.append(su2.su2_generate(lat, per, 1, 0)[0].copy())
-            learned_blocks.append(su2.su2_learned_generate(lat, per, 1, 0.7)[0].copy())
-            su2.su2_set_sampler(lat, su2.SU2_SAMPLER_KP)
-            kp_blocks.append(su2.su2_generate(lat, per, 1, 0)[0].copy())
-            su2.su2_set_overrelax(lat, N_OR)
-            or_blocks.append(su2.su2_generate(lat, per_or, 1, 0)[0].copy())
-            su2.su2_set_overrelax(lat, 0)
-            su2.su2_set_sampler(lat, su2.SU2_SAMPLER_CREUTZ)
-        plain_blocks.append(su2.su2_generate(lat, per, 1, 0)[0].copy())
-        # The 48^4 lattice still drifts slowly (the plaquette rises by about
-        # 2e-7 per round of blocks), so each block is compared with the plain
-        # blocks around it interpolated at its own centre, counted in sweeps
-        # (a compound sweep is 1 + N_OR sweeps): the learned block sits at
-        # f_l, the over-relaxation block at f_o of the way from one plain
-        # block's centre to the next.
-        span = 3 * per + (N_OR + 1) * per_or
-        f_l = per / span
-        f_o = (2.5 * per + 0.5 * (N_OR + 1) * per_or) / span
+        "roofline": roof("or_phase_kernel", or_phase_s, BYTES_PER_OR_UPDATE)}
+    if args.tau_sweeps <= 0:
+        return out
 
-        tau_o, dtau_o = tau_int(or_blocks, own_means=True)[:2]
-        out["kp_overrelax"]["tau_int"] = float(tau_o)
-        out["kp_overrelax"]["tau_int_err"] = float(dtau_o)
-        out["kp_overrelax"]["tau_int_unit"] = "compound sweeps"
-        out["kp_overrelax"]["value_tau_adjusted"] = compound_per_s * 4 * VOL / (2 * tau_o)
-        plain_means = [b.mean() for b in plain_blocks]
-        m_o, se_o = interleaved_offset([b.mean() for b in or_blocks], plain_means, f_o)
-        out["kp_overrelax"]["plaquette_minus_plain"] = m_o
-        out["kp_overrelax"]["plaquette_sigma"] = m_o / se_o if se_o > 0 else None
-        # blocks of one form are replicas of its chain: pooled Gamma method,
-        # each block about its own mean (the 48^4 lattice still drifts slowly)
-        tau_p, dtau_p = tau_int(plain_blocks, own_means=True)[:2]
-        tau_l, dtau_l = tau_int(learned_blocks, own_means=True)[:2]
-        tau_k, dtau_k = tau_int(kp_blocks, own_means=True)[:2]
-        out["plain_kennedy_pendleton"]["tau_int"] = float(tau_k)
-        out["plain_kennedy_pendleton"]["tau_int_err"] = float(dtau_k)
-        out["plain_kennedy_pendleton"]["value_tau_adjusted"] = value_kp / (2 * tau_k)
-        m_l, se = interleaved_offset([b.mean() for b in learned_blocks], plain_means, f_l)
-        out["plain"]["tau_int"] = float(tau_p)
-        out["plain"]["tau_int_err"] = float(dtau_p)
-        out["learned"]["tau_int"] = float(tau_l)
-        out["learned"]["tau_int_err"] = float(dtau_l)
-        out["plain"]["value_tau_adjusted"] = value_plain / (2 * tau_p)
-        out["learned"]["value_tau_adjusted"] = value_learned / (2 * tau_l)
-        out["plaquette_check"] = {"blocks": nblk, "sweeps_per_block": per, "reference_position": f_l,
-                                  "plain_mean": float(np.mean([b.mean() for b in plain_blocks])),
-                                  "learned_mean": float(np.mean([b.mean() for b in learned_blocks])),
-                                  "learned_minus_plain": m_l, "stderr": se,
-                                  "sigma": m_l / se if se > 0 else None}
-        out["value_tau_adjusted"] = {"plain": out["plain"]["value_tau_adjusted"],
-                                     "plain_kennedy_pendleton": out["plain_kennedy_pendleton"]["value_tau_adjusted"],
-                                     "learned": out["learned"]["value_tau_adjusted"],
-                                     "kp_overrelax": out["kp_overrelax"]["value_tau_adjusted"],
-                                     "convention": "4V x sweeps/s / (2 tau_int(plaquette)), tau_int = 1/2 + "
-                                                   "sum rho in sweeps (compound sweeps for kp_overrelax), Gamma "
-                                                   "method with the interleaved blocks of a form pooled as replicas, "
-                                                   "each about its own mean"}
+    nblk = 16
+    per = max(50, args.tau_sweeps // nblk)
+    per_or = max(25, per // (N_OR + 1) * 2)
+    blocks = {k: {"P": [], "L": []} for k in ("kennedy_pendleton", "learned", "creutz", "kp_overrelax")}
+
+    def record(key, res):
+        blocks[key]["P"].append(np.array(res[0], dtype=np.float64))
+        blocks[key]["L"].append(np.abs(np.array(res[1], dtype=np.float64)))
+
+    for k in range(nblk + 1):
+        su2.su2_set_sampler(lat, KP)
+        record("kennedy_pendleton", su2.su2_generate(lat, per, 1, 0))
+        if k == nblk:
+            break
+        record("learned", su2.su2_learned_generate(lat, per, 1, 0.7))
+        su2.su2_set_sampler(lat, CR)
+        record("creutz", su2.su2_generate(lat, per, 1, 0))
+        su2.su2_set_sampler(lat, KP)
+        su2.su2_set_overrelax(lat, N_OR)
+        record("kp_overrelax", su2.su2_generate(lat, per_or, 1, 0))
+        su2.su2_set_overrelax(lat, 0)
+    su2.su2_set_sampler(lat, CR)
+    # block centres, as fractions of a round from one reference block's centre
+    # to the next (a compound sweep counts as 1 + N_OR sweeps)
+    span = 3 * per + (N_OR + 1) * per_or
+    position = {"learned": per / span, "creutz": 2 * per / span,
+                "kp_overrelax": (2.5 * per + 0.5 * (N_OR + 1) * per_or) / span}
+    ref_means = [b.mean() for b in blocks["kennedy_pendleton"]["P"]]
+    slope, slope_err, block_err = block_drift(ref_means)
+    out["equilibrium"] = {
+        "reference": "Kennedy-Pendleton blocks", "blocks": nblk + 1, "sweeps_per_block": per,
+        "plaquette_drift_per_round": slope, "drift_err": slope_err, "block_error": block_err,
+        "drift_over_block_error": abs(slope) / block_err if block_err > 0 else None,
+        "sweeps_per_round": span}
+    for key, b in blocks.items():
+        rate = out[key]["value"] if key != "kp_overrelax" else compound_per_s * 4 * VOL
+        tp, dtp = tau_int(b["P"])[:2]
+        tl, dtl = tau_int(b["L"])[:2]
+        tp_own = tau_int(b["P"], own_means=True)[0]
+        unit = "compound sweeps" if key == "kp_overrelax" else "sweeps"
+        out[key].update({"tau_int": float(tp), "tau_int_err": float(dtp), "tau_int_abs_polyakov": float(tl),
+                         "tau_int_abs_polyakov_err": float(dtl), "tau_int_own_block_means": float(tp_own),
+                         "tau_int_unit": unit, "value_tau_adjusted": rate / (2 * tp),
+                         "value_tau_adjusted_abs_polyakov": rate / (2 * tl),
+                         "plaquette_mean": float(np.mean([x.mean() for x in b["P"]])),
+                         "abs_polyakov_mean": float(np.mean([x.mean() for x in b["L"]]))})
+        if key in position:
+            m, se = interleaved_offset([x.mean() for x in b["P"]], ref_means, position[key])
+            out[key]["plaquette_minus_kennedy_pendleton"] = m
+            out[key]["plaquette_sigma"] = m / se if se > 0 else None
+    out["value_tau_adjusted"] = {k: out[k]["value_tau_adjusted"] for k in blocks}
+    out["value_tau_adjusted"]["convention"] = (
+        "4V x sweeps/s / (2 tau_int(plaquette)), tau_int = 1/2 + sum rho in sweeps (compound sweeps for "
+        "kp_overrelax), Gamma method with the interleaved blocks of a form pooled as replicas about their "
+        "common mean")
+    out["value_tau_adjusted_abs_polyakov"] = {k: out[k]["value_tau_adjusted_abs_polyakov"] for k in blocks}
     return out
 
 
@@ -465,9 +474,12 @@ def run_batched(args, dist, su2, torch):
     b = su2.su2_batch_create(cfg["ns"], cfg["nt"], cfg["beta"], cfg["seed"], cfg["start"], stream=stream)
     try:
         su2.su2_batch_sweep(b, 20)
-        # the fixed default launch (queue depth 4, all co-resident blocks) first
+        # the fixed baseline first: 256-thread blocks, queue depth 4, all co-resident blocks
+        su2.su2_batch_set_launch(b, 4, 256, 0)
+        fixed = su2.su2_batch_launch_info(b)
         fixed_ms = timed_batch(stream, torch, lambda k: su2.su2_batch_generate(b, n, k, 1), 50)
         depth, grid = su2.su2_batch_autotune(b, 5)
+        tuned = su2.su2_batch_launch_info(b)
         su2.su2_batch_generate(b, n, 5, 1)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         dist.barrier()
@@ -487,13 +499,78 @@ def run_batched(args, dist, su2, torch):
     return {"workload": "64 lattices: 8^4, 12^3x4, 16^3x6, 16^4, 24^3x8 (13/13/13/13/12), beta uniform in [1.5, 3], "
                         "cold start, plaquette and Polyakov loop of every lattice every sweep",
             "sites": sites, "value": value, "unit": UNIT, "sweeps_per_s": args.batched_steps / (ms * 1e-3),
-            "ms_per_sweep": ms / args.batched_steps, "queue_depth": depth, "grid_blocks": grid,
-            "fixed_config_ms_per_sweep": fixed_ms,
+            "ms_per_sweep": ms / args.batched_steps,
+            "autotuned": {"queue_depth": tuned[0], "threads_per_block": tuned[1], "grid_blocks": tuned[2],
+                          "search": "queue depth 2/4/8 x 64/128/256 threads x full or half grid, 5 sweeps each"},
+            "fixed_config": {"queue_depth": fixed[0], "threads_per_block": fixed[1], "grid_blocks": fixed[2],
+                             "ms_per_sweep": fixed_ms},
+            "autotuned_speedup_vs_fixed": fixed_ms / (ms / args.batched_steps),
             "cuda_graph": info["graphs"], "gpu_launches": args.batched_steps,
             "roofline": {"bound": "hbm", "kernel": "batch_sweep_kernel", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak,
                          "note": "whole sweep incl. barriers and measurements; 169 MB of links, partly L2-resident"},
             "plaquette_last": [float(x) for x in plaq[-1][:5]]}
+
+
+def run_small(args, dist, su2, torch):
+    """The small workloads, L2-resident, so latency- rather than HBM-bound:
+    sweeps/s and microseconds per phase (graph-replayed sweeps on a stream,
+    CUDA events around the whole run, measurements included).
+      8^4, beta = 2.3, hot start (seed 1): 1000 sweeps, plaquette and
+        Polyakov loop every sweep, the headline sampler;
+      24^4, beta = 2.5, cold start (seed 2): 200 thermalisation sweeps, then
+        1000 measured sweeps with reunitarization every 10;
+      32^3 x 4, beta = 2.20 .. 2.60 in steps of 0.05, cold starts (seeds
+        100 + i): one batch of nine lattices, 500 thermalisation + 2000
+        measured sweeps, plaquette and |L| per beta (Sec. 4.2)."""
+    import numpy as np
+
+    from paper_1010_1486_gb300 import workloads
+
+    sampler = su2.SU2_SAMPLER_KP if args.sampler == "kp" else su2.SU2_SAMPLER_CREUTZ
+    out = {}
+
+    def lattice_run(cfg, therm, n, reunit):
+        st_ = torch.cuda.Stream()
+        h = su2.su2_create(cfg["ns"], cfg["nt"], cfg["beta"], cfg["seed"] + dist.rank, cfg["start"], stream=st_)
+        try:
+            su2.su2_set_sampler(h, sampler)
+            su2.su2_generate(h, max(therm, 3), 1, reunit)
+            ms, (plaq, poly, _) = timed(st_, torch, dist, lambda: su2.su2_generate(h, n, 1, reunit))
+        finally:
+            su2.su2_destroy(h)
+        return ms, plaq, poly
+
+    c1 = workloads.PARITY_8
+    ms, plaq, poly = lattice_run(c1, 10, 1000, 0)
+    out["8^4"] = {"workload": "8^4, beta 2.3, hot start, 1000 sweeps, plaquette + Polyakov loop every sweep",
+                  "sweeps_per_s": 1000 / (ms * 1e-3), "us_per_phase": ms * 1e3 / (8 * 1000),
+                  "link_updates_per_s": 1000 * 4 * 8 ** 4 / (ms * 1e-3), "plaquette_mean": float(plaq.mean())}
+    c2 = workloads.SCALE_24
+    ms, plaq, poly = lattice_run(c2, c2["therm"], c2["meas"], c2["reunit_every"])
+    out["24^4"] = {"workload": "24^4, beta 2.5, cold start, 200 + 1000 sweeps, reunitarized every 10, plaquette "
+                               "(binary64 sum) every sweep",
+                   "sweeps_per_s": c2["meas"] / (ms * 1e-3), "us_per_phase": ms * 1e3 / (8 * c2["meas"]),
+                   "link_updates_per_s": c2["meas"] * 4 * 24 ** 4 / (ms * 1e-3),
+                   "plaquette_mean": float(plaq.mean())}
+    c4 = workloads.FINITE_T
+    nb = len(c4["betas"])
+    bst = torch.cuda.Stream()
+    b = su2.su2_batch_create([c4["ns"]] * nb, [c4["nt"]] * nb, list(c4["betas"]),
+                             [c4["seed0"] + i for i in range(nb)], c4["start"], stream=bst)
+    try:
+        su2.su2_batch_generate(b, nb, 500, 0)
+        ms, (plaq, poly, _) = timed(bst, torch, dist, lambda: su2.su2_batch_generate(b, nb, 2000, 1))
+    finally:
+        su2.su2_batch_destroy(b)
+    out["32^3x4_beta_scan"] = {
+        "workload": "nine 32^3 x 4 lattices, beta 2.20 .. 2.60, cold, one batch (Creutz sampler): 500 + 2000 "
+                    "sweeps, plaquette and Polyakov loop of every lattice every sweep",
+        "sweeps_per_s": 2000 / (ms * 1e-3), "us_per_sweep_of_the_scan": ms * 1e3 / 2000,
+        "link_updates_per_s": 2000 * nb * 4 * 32 ** 3 * 4 / (ms * 1e-3),
+        "beta": list(c4["betas"]), "plaquette_mean": [float(x) for x in plaq.mean(axis=0)],
+        "abs_polyakov_mean": [float(x) for x in np.abs(poly).mean(axis=0)]}
+    return out
 
 
 def run_e2e(args, dist, lat, su2, torch):

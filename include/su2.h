@@ -397,11 +397,17 @@ su2_status su2_batch_polyakov(su2_batch *b, double *out_n);
 su2_status su2_batch_get_links(su2_batch *b, int i, float *host);
 
 /* Launch configuration: queue depth (2, 4 or 8: the work is split into chunks
- * of 32 x depth sites, and each warp takes a contiguous range of chunks) and
- * grid (blocks of 128 threads; <= 0 or too large = all co-resident blocks).
- * su2_batch_autotune times every depth with the full and the half grid over
- * `sweeps` sweeps, restores the links and sweep counter, and keeps the fastest. */
+ * of 32 x depth sites, and each warp takes a contiguous range of chunks),
+ * block size (64, 128 or 256 threads; the register budget is that of 768
+ * threads per SM for every size) and grid (<= 0 or too large = all
+ * co-resident blocks).  The default is depth 4, 128 threads, all co-resident
+ * blocks.  su2_batch_set_config keeps the block size.  su2_batch_autotune
+ * times all 18 combinations of depth, block size and full or half grid over
+ * `sweeps` sweeps each, restores the links and sweep counter, and keeps the
+ * fastest (reported by su2_batch_launch_info). */
+su2_status su2_batch_set_launch(su2_batch *b, int queue_depth, int threads, int grid);
 su2_status su2_batch_set_config(su2_batch *b, int queue_depth, int grid);
+su2_status su2_batch_launch_info(su2_batch *b, int *queue_depth, int *threads, int *grid);
 su2_status su2_batch_autotune(su2_batch *b, int sweeps, int *queue_depth, int *grid);
 su2_status su2_batch_info(su2_batch *b, int *n, uint32_t *sweep, int *queue_depth, int *grid, int *graphs);
 

@@ -105,6 +105,24 @@ def interleaved_offset(test_means, ref_means, position: float):
     return float(d.mean()), float(d.std(ddof=1) / math.sqrt(d.size))
 
 
+def block_drift(block_means):
+    """Linear drift of a chain's block means b_k (k = 0..n-1, one block per
+    round of interleaved blocks): least-squares slope per round, its standard
+    error, and the scatter of one block mean about the line (its error).
+    A chain in equilibrium has |slope| well below that block error."""
+    b = np.asarray(block_means, dtype=np.float64)
+    n = b.size
+    if n < 3:
+        raise ValueError("need at least 3 blocks")
+    k = np.arange(n, dtype=np.float64)
+    kc = k - k.mean()
+    slope = float((kc * (b - b.mean())).sum() / (kc * kc).sum())
+    resid = b - (b.mean() + slope * kc)
+    block_err = float(math.sqrt((resid * resid).sum() / (n - 2)))
+    slope_err = block_err / math.sqrt(float((kc * kc).sum()))
+    return slope, slope_err, block_err
+
+
 def effective_potential(w) -> np.ndarray:
     """Static-potential estimates from Wilson loops W[R-1, T-1]:
     V_eff(R, T) = log(W(R, T) / W(R, T+1)), shape (rmax, tmax - 1).  For large

@@ -26,10 +26,10 @@
 
 namespace su2 {
 
-#ifndef SU2_BATCH_MIN_BLOCKS
-#define SU2_BATCH_MIN_BLOCKS 6
-#endif
-constexpr int kBatchMinBlocks = SU2_BATCH_MIN_BLOCKS;  // blocks per SM the register budget is set for
+// Threads per SM the register budget is set for (six blocks of 128): every
+// block size T keeps it, with 768 / T blocks per SM.
+constexpr int kBatchThreadsPerSm = 768;
+constexpr int kBatchBlockSizes[3] = {64, 128, 256};
 
 struct LatDesc {
     Geom g;
@@ -394,11 +394,11 @@ __device__ void batch_measure_final(const BatchParams &bp, unsigned int slot)
     }
 }
 
-template <int R>
-__global__ void __launch_bounds__(kHbThreads, kBatchMinBlocks) batch_sweep_kernel(const BatchParams bp)
+template <int R, int T>
+__global__ void __launch_bounds__(T, kBatchThreadsPerSm / T) batch_sweep_kernel(const BatchParams bp)
 {
-    __shared__ CrQueues s_q[kHbThreads / 32];
-    __shared__ LatDesc s_desc[kHbThreads / 32];
+    __shared__ CrQueues s_q[T / 32];
+    __shared__ LatDesc s_desc[T / 32];
     const int wib = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -503,8 +503,9 @@ struct su2_batch {
     int total_mrounds = 0;
     int total_chunks = 0;
     int R = 4;
+    int threads = 128;  // block size: 64, 128 or 256
     int grid = 0;
-    int max_grid[3] = {0, 0, 0};  // co-resident blocks for R = 2, 4, 8
+    int max_grid[3][3] = {};  // co-resident blocks for R = 2, 4, 8 x block sizes 64, 128, 256
     uint32_t sweep = 0;
     unsigned long long timeout_ns = 2000000000ull;
     bool use_graph = true;
@@ -517,12 +518,21 @@ namespace su2 {
 namespace {
 
 int r_index(int R) { return R == 2 ? 0 : (R == 4 ? 1 : 2); }
+int t_index(int T) { return T == 64 ? 0 : (T == 128 ? 1 : 2); }
 
-void *kernel_for(int R)
+template <int R>
+void *kernel_for_t(int T)
 {
-    if (R == 2) return (void *)batch_sweep_kernel<2>;
-    if (R == 8) return (void *)batch_sweep_kernel<8>;
-    return (void *)batch_sweep_kernel<4>;
+    if (T == 64) return (void *)batch_sweep_kernel<R, 64>;
+    if (T == 256) return (void *)batch_sweep_kernel<R, 256>;
+    return (void *)batch_sweep_kernel<R, 128>;
+}
+
+void *kernel_for(int R, int T)
+{
+    if (R == 2) return kernel_for_t<2>(T);
+    if (R == 8) return kernel_for_t<8>(T);
+    return kernel_for_t<4>(T);
 }
 
 void drop_graphs(su2_batch *b)
@@ -534,8 +544,8 @@ void drop_graphs(su2_batch *b)
         }
 }
 
-// Recomputes the heat-bath chunk table for queue depth R.
-su2_status set_depth(su2_batch *b, int R, int grid)
+// Recomputes the heat-bath chunk table for queue depth R; block size T.
+su2_status set_depth(su2_batch *b, int R, int T, int grid)
 {
     std::vector<int> prefix(b->n + 1, 0);
     for (int l = 0; l < b->n; ++l) prefix[l + 1] = prefix[l] + (b->geom[l].vh + 32 * R - 1) / (32 * R);
@@ -549,6 +559,7 @@ su2_status set_depth(su2_batch *b, int R, int grid)
     SU2_CUDA(cudaStreamSynchronize(b->stream));
     b->total_chunks = prefix[b->n];
     b->R = R;
+    b->threads = T;
     b->grid = grid;
     drop_graphs(b);
     return SU2_OK;
@@ -590,7 +601,8 @@ cudaError_t enqueue_launch(su2_batch *b, int do_sweep, int measure)
     if (e != cudaSuccess) return e;
     BatchParams p = params_of(b, do_sweep, measure);
     void *args[] = {&p};
-    return cudaLaunchCooperativeKernel(kernel_for(b->R), dim3(b->grid), dim3(kHbThreads), args, 0, b->stream);
+    return cudaLaunchCooperativeKernel(kernel_for(b->R, b->threads), dim3(b->grid), dim3(b->threads), args, 0,
+                                       b->stream);
 }
 
 su2_status launch_sweep(su2_batch *b, int measure)
@@ -817,16 +829,19 @@ su2_status su2_batch_create(int n, const int *ns, const int *nt, const double *b
         e = start_links(b->links + b->link_offset[l], b->geom[l], start == SU2_HOT, seed[l], b->d_counters + 2,
                         b->stream);  // the hot-start kernel counts failures in flags[1] = counter 3
     if (e == cudaSuccess) {
-        for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
-            const int R = i == 0 ? 2 : (i == 1 ? 4 : 8);
-            int per_sm = 0, sms = 0;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_for(R), kHbThreads, 0);
-            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            b->max_grid[i] = std::max(1, per_sm * sms);
-        }
+        int sms = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+            for (int j = 0; j < 3 && e == cudaSuccess; ++j) {
+                const int R = i == 0 ? 2 : (i == 1 ? 4 : 8);
+                int per_sm = 0;
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_for(R, kBatchBlockSizes[j]),
+                                                                  kBatchBlockSizes[j], 0);
+                b->max_grid[i][j] = std::max(1, per_sm * sms);
+            }
     }
     if (e != cudaSuccess) st = cuda_fail(e, "su2_batch_create");
-    if (st == SU2_OK) st = set_depth(b, 4, b->max_grid[r_index(4)]);
+    if (st == SU2_OK) st = set_depth(b, 4, 128, b->max_grid[r_index(4)][t_index(128)]);
     if (st == SU2_OK) {
         unsigned int c[4];
         if (cudaMemcpyAsync(c, b->d_counters, sizeof c, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
@@ -952,18 +967,35 @@ su2_status su2_batch_info(su2_batch *b, int *n, uint32_t *sweep, int *queue_dept
     return SU2_OK;
 }
 
-su2_status su2_batch_set_config(su2_batch *b, int queue_depth, int grid)
+su2_status su2_batch_set_launch(su2_batch *b, int queue_depth, int threads, int grid)
 {
-    if (!b || (queue_depth != 2 && queue_depth != 4 && queue_depth != 8)) return SU2_E_INVAL;
-    const int most = b->max_grid[r_index(queue_depth)];
+    if (!b || (queue_depth != 2 && queue_depth != 4 && queue_depth != 8) ||
+        (threads != 64 && threads != 128 && threads != 256))
+        return SU2_E_INVAL;
+    const int most = b->max_grid[r_index(queue_depth)][t_index(threads)];
     if (grid <= 0 || grid > most) grid = most;
     DeviceGuard guard(b->device);
-    return set_depth(b, queue_depth, grid);
+    return set_depth(b, queue_depth, threads, grid);
 }
 
-// Times each candidate (queue depth 2/4/8 x full or half of the co-resident
-// grid) over `sweeps` sweeps of the batch, then restores the links and the
-// sweep counter, and keeps the fastest.
+su2_status su2_batch_set_config(su2_batch *b, int queue_depth, int grid)
+{
+    if (!b) return SU2_E_INVAL;
+    return su2_batch_set_launch(b, queue_depth, b->threads, grid);
+}
+
+su2_status su2_batch_launch_info(su2_batch *b, int *queue_depth, int *threads, int *grid)
+{
+    if (!b) return SU2_E_INVAL;
+    if (queue_depth) *queue_depth = b->R;
+    if (threads) *threads = b->threads;
+    if (grid) *grid = b->grid;
+    return SU2_OK;
+}
+
+// Times each candidate (queue depth 2/4/8 x block size 64/128/256 x full or
+// half of the co-resident grid) over `sweeps` sweeps of the batch, then
+// restores the links and the sweep counter, and keeps the fastest.
 su2_status su2_batch_autotune(su2_batch *b, int sweeps, int *queue_depth, int *grid)
 {
     if (!b || sweeps < 1) return SU2_E_INVAL;
@@ -974,17 +1006,17 @@ su2_status su2_batch_autotune(su2_batch *b, int sweeps, int *queue_depth, int *g
     su2_status st = SU2_OK;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     float best = 1e30f;
-    int best_r = b->R, best_grid = b->grid;
+    int best_r = b->R, best_t = b->threads, best_grid = b->grid;
     const uint32_t sweep0 = b->sweep;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
         cudaMemcpyAsync(saved, b->links, bytes, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess)
         st = cuda_fail(cudaGetLastError(), "su2_batch_autotune");
     const int depths[3] = {2, 4, 8};
-    for (int i = 0; i < 3 && st == SU2_OK; ++i)
-        for (int half = 0; half < 2 && st == SU2_OK; ++half) {
-            const int R = depths[i];
-            const int grid = half ? std::max(1, b->max_grid[i] / 2) : b->max_grid[i];
-            if ((st = set_depth(b, R, grid)) != SU2_OK) break;
+    for (int c = 0; c < 18 && st == SU2_OK; ++c) {
+            const int i = c / 6, j = (c / 2) % 3, half = c % 2;
+            const int R = depths[i], T = kBatchBlockSizes[j];
+            const int grid = half ? std::max(1, b->max_grid[i][j] / 2) : b->max_grid[i][j];
+            if ((st = set_depth(b, R, T, grid)) != SU2_OK) break;
             if ((st = launch_sweep(b, 0)) != SU2_OK) break;  // warm-up (and graph capture)
             cudaEventRecord(e0, b->stream);
             for (int s = 0; s < sweeps && st == SU2_OK; ++s) st = launch_sweep(b, 0);
@@ -998,6 +1030,7 @@ su2_status su2_batch_autotune(su2_batch *b, int sweeps, int *queue_depth, int *g
             if (ms < best) {
                 best = ms;
                 best_r = R;
+                best_t = T;
                 best_grid = grid;
             }
             // restore the configuration the candidates started from
@@ -1014,7 +1047,7 @@ su2_status su2_batch_autotune(su2_batch *b, int sweeps, int *queue_depth, int *g
     device_free(saved, bytes, b->device, b->stream);
     cudaStreamSynchronize(b->stream);
     b->sweep = sweep0;
-    if (st == SU2_OK) st = set_depth(b, best_r, best_grid);
+    if (st == SU2_OK) st = set_depth(b, best_r, best_t, best_grid);
     if (st == SU2_OK) st = clear_stats(b);
     if (queue_depth) *queue_depth = b->R;
     if (grid) *grid = b->grid;

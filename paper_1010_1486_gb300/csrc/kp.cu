@@ -65,10 +65,13 @@ constexpr int kRetryCap = 64;  // per warp: at most 31 left over + 32 pushed by 
 // latency:
 //   part 0  k, beta k, U~^dag; the Philox blocks of the first trial and of
 //           the direction;
-//   part 1  the first trial (Creutz's method instead if beta k < 2);
+//   part 1  the first trial;
 //   part 2  the direction and the store of every accepted link.
 // A link whose first trial is rejected is parked in the warp's retry queue
-// in shared memory (U~^dag, beta k, index).  Once 32 links wait, the whole
+// in shared memory (U~^dag, beta k, index), and so is a link with beta k < 2
+// (its staple in place of U~^dag), which the retry pass draws by Creutz's
+// method exactly as the plain kernel does; keeping that rare draw out of the
+// main loop leaves its registers to the pipeline (no spills).  Once 32 links wait, the whole
 // warp runs their further trials 1, 2, ... together, so no warp spins on one
 // lane's rejections.  Every draw depends only on the link's counters, so the
 // phase computes exactly the one-thread-per-link definition.  Lanes past the
@@ -107,14 +110,31 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
         if (lane < n) {
             const int q = first + lane;
             const float4 ut = s_ut[wib][q];
-            const float two_bk = __fmul_rn(2.0f, s_bk[wib][q]);
+            const float bk_q = s_bk[wib][q];
+            const float two_bk = __fmul_rn(2.0f, bk_q);
             const int eo = s_eo[wib][q];
             float a0 = 0.0f;
             int t = 1;
-            for (; t < p.max_trials; ++t)
-                if (kp_trial(philox_rk(make_uint4((uint32_t)eo + rng_eo, sweep, sw_kp, (uint32_t)t), p.rk), two_bk, a0))
-                    break;
-            if (t < p.max_trials) {
+            if (!(bk_q >= kKpMinBk)) {  // beta k < 2: Creutz's method; the queue holds the staple
+                float4 out;
+                const int n = heatbath_draw(ut, p.beta, p.rk, (uint32_t)eo + rng_eo, sweep, rng_parity, MU, out);
+                if (n > 0) {
+                    p.links[link_index(p.g, MU, p.parity, eo)] = out;
+                    if (MEAS) plaq += (double)qmul_re(out, s_sp[MEAS ? wib : 0][q]);
+                    trials += (unsigned int)n;
+                } else {
+                    atomicAdd(&p.flags[0], 1u);
+                    trials += (unsigned int)kMaxTrials;
+                }
+                t = -1;
+            } else {
+                for (; t < p.max_trials; ++t)
+                    if (kp_trial(philox_rk(make_uint4((uint32_t)eo + rng_eo, sweep, sw_kp, (uint32_t)t), p.rk), two_bk,
+                                 a0))
+                        break;
+            }
+            if (t < 0) {
+            } else if (t < p.max_trials) {
                 const float4 out =
                     direction_update(a0, ut, philox_rk(make_uint4((uint32_t)eo + rng_eo, sweep, sw_dir, 0u), p.rk));
                 p.links[link_index(p.g, MU, p.parity, eo)] = out;
@@ -167,23 +187,11 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
         float a0;
         const bool first_ok = kp_trial(w, __fmul_rn(2.0f, bk), a0);
         const bool accepted = valid && use_kp && first_ok;
-        const bool park = valid && use_kp && !first_ok;
-        if (valid && !use_kp) {  // beta k < 2: Creutz's method
-            float4 out;
-            const int n = heatbath_draw(v_cur, p.beta, p.rk, (uint32_t)cur + rng_eo, sweep, rng_parity, MU, out);
-            if (n > 0) {
-                p.links[link_index(p.g, MU, p.parity, cur)] = out;
-                if (MEAS) plaq += (double)qmul_re(out, sp_cur);
-                trials += (unsigned int)n;
-            } else {
-                atomicAdd(&p.flags[0], 1u);
-                trials += (unsigned int)kMaxTrials;
-            }
-        }
+        const bool park = valid && !(use_kp && first_ok);  // rejected, or beta k < 2 (Creutz, in the queue)
         const unsigned int parked = __ballot_sync(0xffffffffu, park);
         if (park) {
             const int q = queued + __popc(parked & lanes_below);
-            s_ut[wib][q] = ut;
+            s_ut[wib][q] = use_kp ? ut : v_cur;
             s_bk[wib][q] = bk;
             s_eo[wib][q] = cur;
             if (MEAS) s_sp[MEAS ? wib : 0][q] = sp_cur;

@@ -116,6 +116,8 @@ _SIGS = {
     "su2_batch_polyakov": [_P, _P],
     "su2_batch_get_links": [_P, _i32, _P],
     "su2_batch_set_config": [_P, _i32, _i32],
+    "su2_batch_set_launch": [_P, _i32, _i32, _i32],
+    "su2_batch_launch_info": [_P, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)],
     "su2_batch_autotune": [_P, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)],
     "su2_batch_info": [_P, ctypes.POINTER(_i32), ctypes.POINTER(_u32), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
                        ctypes.POINTER(_i32)],
@@ -613,6 +615,17 @@ def su2_batch_get_links(b: int, i: int, ns: int, nt: int) -> np.ndarray:
 
 def su2_batch_set_config(b: int, queue_depth: int, grid: int = 0) -> None:
     _check(_lib.su2_batch_set_config(b, queue_depth, grid), "su2_batch_set_config")
+
+
+def su2_batch_set_launch(b: int, queue_depth: int, threads: int, grid: int = 0) -> None:
+    _check(_lib.su2_batch_set_launch(b, queue_depth, threads, grid), "su2_batch_set_launch")
+
+
+def su2_batch_launch_info(b: int):
+    """(queue depth, threads per block, grid) of the current launch."""
+    r, t, g = _i32(), _i32(), _i32()
+    _check(_lib.su2_batch_launch_info(b, ctypes.byref(r), ctypes.byref(t), ctypes.byref(g)), "su2_batch_launch_info")
+    return r.value, t.value, g.value
 
 
 def su2_batch_autotune(b: int, sweeps: int = 3):

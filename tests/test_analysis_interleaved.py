@@ -34,3 +34,16 @@ def test_block_counts_are_checked():
         interleaved_offset([1.0, 2.0], [1.0, 2.0], 0.5)
     with pytest.raises(ValueError):
         interleaved_offset([1.0], [1.0, 2.0], 0.5)
+
+
+def test_block_drift_recovers_a_linear_trend():
+    from paper_1010_1486_gb300.analysis import block_drift
+
+    rng = np.random.default_rng(3)
+    k = np.arange(40)
+    b = 0.5 + 2e-3 * k + rng.normal(0, 1e-3, 40)
+    slope, err, block_err = block_drift(b)
+    assert abs(slope - 2e-3) < 4 * err
+    assert 0.6e-3 < block_err < 1.4e-3
+    flat = block_drift(0.5 + rng.normal(0, 1e-3, 40))
+    assert abs(flat[0]) < 4 * flat[1]
