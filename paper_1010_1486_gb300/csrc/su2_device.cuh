@@ -84,10 +84,12 @@ __device__ __forceinline__ uint4 philox_key(uint4 c, uint32_t k0, uint32_t k1)
     return c;
 }
 
-// Uniform in (0, 1]: the top 24 bits plus one, times 2^-24 (exact).
+// Uniform in (0, 1]: the top 24 bits plus one, times 2^-24, formed as
+// (w >> 8) 2^-24 + 2^-24 with one fused multiply-add (every step exact, so it
+// is the same number as ((w >> 8) + 1) 2^-24).
 __device__ __forceinline__ float uniform01(uint32_t w)
 {
-    return __fmul_rn(__uint2float_rn((w >> 8) + 1u), 5.9604644775390625e-8f);
+    return __fmaf_rn(__uint2float_rn(w >> 8), 5.9604644775390625e-8f, 5.9604644775390625e-8f);
 }
 
 // Uniform for the argument of a logarithm: w 2^-32 + 2^-33 from the whole
@@ -179,12 +181,13 @@ __device__ __forceinline__ void sincos_2pi(float u, float &sn, float &cs)
     pc = __fmaf_rn(pc, z, 1.0f / 24.0f);
     pc = __fmaf_rn(pc, z, -0.5f);
     const float c = __fmaf_rn(z, pc, 1.0f);
-    switch (((int)q) & 3) {
-    case 0: sn = s; cs = c; break;
-    case 1: sn = c; cs = -s; break;
-    case 2: sn = -s; cs = -c; break;
-    default: sn = -c; cs = s; break;
-    }
+    // q quarter turns: (s, c), (c, -s), (-s, -c), (-c, s) for q mod 4 = 0..3,
+    // as selects (negation is exact)
+    const int qi = (int)q;
+    const float a = (qi & 1) ? c : s;
+    const float b = (qi & 1) ? s : c;
+    sn = (qi & 2) ? -a : a;
+    cs = ((qi + 1) & 2) ? -b : b;
 }
 
 // ------------------------------------------------------------- quaternions
