@@ -473,6 +473,7 @@ def run_batched(args, dist, su2, torch):
     stream = torch.cuda.Stream()
     b = su2.su2_batch_create(cfg["ns"], cfg["nt"], cfg["beta"], cfg["seed"], cfg["start"], stream=stream)
     try:
+        su2.su2_batch_set_sampler(b, su2.SU2_SAMPLER_KP if args.sampler == "kp" else su2.SU2_SAMPLER_CREUTZ)
         su2.su2_batch_sweep(b, 20)
         # the fixed baseline first: 256-thread blocks, queue depth 4, all co-resident blocks
         su2.su2_batch_set_launch(b, 4, 256, 0)
@@ -498,6 +499,7 @@ def run_batched(args, dist, su2, torch):
     achieved = BYTES_PER_UPDATE * updates / dist.world / (ms * 1e-3) / 1e9
     return {"workload": "64 lattices: 8^4, 12^3x4, 16^3x6, 16^4, 24^3x8 (13/13/13/13/12), beta uniform in [1.5, 3], "
                         "cold start, plaquette and Polyakov loop of every lattice every sweep",
+            "sampler": SAMPLERS[args.sampler]["name"],
             "sites": sites, "value": value, "unit": UNIT, "sweeps_per_s": args.batched_steps / (ms * 1e-3),
             "ms_per_sweep": ms / args.batched_steps,
             "autotuned": {"queue_depth": tuned[0], "threads_per_block": tuned[1], "grid_blocks": tuned[2],
@@ -559,12 +561,13 @@ def run_small(args, dist, su2, torch):
     b = su2.su2_batch_create([c4["ns"]] * nb, [c4["nt"]] * nb, list(c4["betas"]),
                              [c4["seed0"] + i for i in range(nb)], c4["start"], stream=bst)
     try:
+        su2.su2_batch_set_sampler(b, sampler)
         su2.su2_batch_generate(b, nb, 500, 0)
         ms, (plaq, poly, _) = timed(bst, torch, dist, lambda: su2.su2_batch_generate(b, nb, 2000, 1))
     finally:
         su2.su2_batch_destroy(b)
     out["32^3x4_beta_scan"] = {
-        "workload": "nine 32^3 x 4 lattices, beta 2.20 .. 2.60, cold, one batch (Creutz sampler): 500 + 2000 "
+        "workload": "nine 32^3 x 4 lattices, beta 2.20 .. 2.60, cold, one batch (headline sampler): 500 + 2000 "
                     "sweeps, plaquette and Polyakov loop of every lattice every sweep",
         "sweeps_per_s": 2000 / (ms * 1e-3), "us_per_sweep_of_the_scan": ms * 1e3 / 2000,
         "link_updates_per_s": 2000 * nb * 4 * 32 ** 3 * 4 / (ms * 1e-3),

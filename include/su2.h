@@ -406,6 +406,11 @@ su2_status su2_batch_get_links(su2_batch *b, int i, float *host);
  * `sweeps` sweeps each, restores the links and sweep counter, and keeps the
  * fastest (reported by su2_batch_launch_info). */
 su2_status su2_batch_set_launch(su2_batch *b, int queue_depth, int threads, int grid);
+/* a0 sampler of every lattice of the batch: SU2_SAMPLER_CREUTZ (default) or
+ * SU2_SAMPLER_KP, as su2_set_sampler for one lattice (each lattice's chain is
+ * then that of su2_heatbath_sweep with the same sampler).  Keeps the launch
+ * shape, clamped to the co-resident blocks of that sampler's kernel. */
+su2_status su2_batch_set_sampler(su2_batch *b, int sampler);
 su2_status su2_batch_set_config(su2_batch *b, int queue_depth, int grid);
 su2_status su2_batch_launch_info(su2_batch *b, int *queue_depth, int *threads, int *grid);
 su2_status su2_batch_autotune(su2_batch *b, int sweeps, int *queue_depth, int *grid);

@@ -10,6 +10,7 @@
 // beta k < 2 are drawn by Creutz's method exactly as the plain kernel does.
 #include <algorithm>
 
+#include "kp_device.cuh"
 #include "observables.cuh"
 #include "staple.cuh"
 #include "su2_device.cuh"
@@ -22,8 +23,6 @@ constexpr int kKpThreads = 256;
 #define SU2_KP_MIN_BLOCKS 3
 #endif
 constexpr int kKpMinBlocks = SU2_KP_MIN_BLOCKS;  // blocks per SM the register budget is set for
-constexpr float kKpMinBk = 2.0f;
-constexpr uint32_t kKennedyPendleton = 5u;
 
 struct KpParams {
     float4 *links;
@@ -40,19 +39,6 @@ struct KpParams {
     double *plaq;              // measuring phases: block partials of the plaquettes of planes (nu < mu, mu)
     SlabRange slab;            // SLAB kernels: the interior eo range and the global keys of its random numbers
 };
-
-// One trial (block t of the KP stream): a0 = 1 - 2 u, and whether it is
-// accepted.
-__device__ __forceinline__ bool kp_trial(uint4 w, float two_bk, float &a0)
-{
-    float sn, cs;
-    sincos_2pi(uniform01(w.y), sn, cs);
-    const float num = __fmaf_rn(__fmul_rn(cs, cs), log_series(uniform_log(w.z)), log_series(uniform_log(w.x)));
-    const float lam2 = __fdiv_rn(-num, two_bk);
-    const float r4 = uniform01(w.w);
-    a0 = __fmaf_rn(-2.0f, lam2, 1.0f);
-    return lam2 <= 1.0f && __fmul_rn(r4, r4) <= __fsub_rn(1.0f, lam2);
-}
 
 constexpr int kKpWarps = kKpThreads / 32;
 constexpr int kRetryCap = 64;  // per warp: at most 31 left over + 32 pushed by one round

@@ -404,9 +404,11 @@ __device__ __forceinline__ float4 direction_update(float a0, float4 ut, uint4 d)
 // The whole heat-bath draw of one link from its staple v (Sec. 2), trial by
 // trial: trial t uses words 2(t&1), 2(t&1)+1 of Creutz block t>>1; the
 // direction uses words 0, 1 of direction block 0.  Returns the number of
-// trials, or 0 if kMaxTrials were all rejected (out untouched).
-__device__ __forceinline__ int heatbath_draw(float4 v, float beta, const RoundKeys &rk, uint32_t eo, uint32_t sweep,
-                                             uint32_t parity, uint32_t mu, float4 &out)
+// trials, or 0 if kMaxTrials were all rejected (out untouched).  gen(counter)
+// is the Philox generator under the lattice's key.
+template <class Gen>
+__device__ __forceinline__ int heatbath_draw_gen(float4 v, float beta, Gen gen, uint32_t eo, uint32_t sweep,
+                                                 uint32_t parity, uint32_t mu, float4 &out)
 {
     const DrawSetup s = prepare_draw(v, beta);
     const bool haar = s.bk < kHaarBelow;
@@ -414,7 +416,7 @@ __device__ __forceinline__ int heatbath_draw(float4 v, float beta, const RoundKe
     float a0 = 0.0f;
     int trials = 0;
     for (int b = 0; b < kMaxTrials / 2 && trials == 0; ++b) {
-        const uint4 w = philox_rk(make_uint4(eo, sweep, stream_word(kCreutz, parity, mu), (uint32_t)b), rk);
+        const uint4 w = gen(make_uint4(eo, sweep, stream_word(kCreutz, parity, mu), (uint32_t)b));
         float cand;
         if (creutz_trial(uniform_log(w.x), uniform01(w.y), s.ibk, s.e, ome, haar, cand)) {
             a0 = cand;
@@ -425,8 +427,31 @@ __device__ __forceinline__ int heatbath_draw(float4 v, float beta, const RoundKe
         }
     }
     if (trials == 0) return 0;
-    out = direction_update(a0, s.ut, philox_rk(make_uint4(eo, sweep, stream_word(kDirection, parity, mu), 0u), rk));
+    out = direction_update(a0, s.ut, gen(make_uint4(eo, sweep, stream_word(kDirection, parity, mu), 0u)));
     return trials;
+}
+
+__device__ __forceinline__ int heatbath_draw(float4 v, float beta, const RoundKeys &rk, uint32_t eo, uint32_t sweep,
+                                             uint32_t parity, uint32_t mu, float4 &out)
+{
+    return heatbath_draw_gen(v, beta, [&](uint4 c) { return philox_rk(c, rk); }, eo, sweep, parity, mu, out);
+}
+
+// Two blocks under the key (k0, k1) with the key schedule computed on the fly,
+// round by round (batched kernels: one key per lattice).
+__device__ __forceinline__ void philox2_key(uint4 &a, uint4 &b, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t alo0 = 0xD2511F53u * a.x, ahi0 = __umulhi(0xD2511F53u, a.x);
+        const uint32_t alo1 = 0xCD9E8D57u * a.z, ahi1 = __umulhi(0xCD9E8D57u, a.z);
+        const uint32_t blo0 = 0xD2511F53u * b.x, bhi0 = __umulhi(0xD2511F53u, b.x);
+        const uint32_t blo1 = 0xCD9E8D57u * b.z, bhi1 = __umulhi(0xCD9E8D57u, b.z);
+        a = make_uint4(ahi1 ^ a.y ^ k0, alo1, ahi0 ^ a.w ^ k1, alo0);
+        b = make_uint4(bhi1 ^ b.y ^ k0, blo1, bhi0 ^ b.w ^ k1, blo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
 }
 
 // Haar-random link (Marsaglia 1972), the hot start (Sec. 4.1): two points

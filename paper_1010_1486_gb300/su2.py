@@ -117,6 +117,7 @@ _SIGS = {
     "su2_batch_get_links": [_P, _i32, _P],
     "su2_batch_set_config": [_P, _i32, _i32],
     "su2_batch_set_launch": [_P, _i32, _i32, _i32],
+    "su2_batch_set_sampler": [_P, _i32],
     "su2_batch_launch_info": [_P, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)],
     "su2_batch_autotune": [_P, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)],
     "su2_batch_info": [_P, ctypes.POINTER(_i32), ctypes.POINTER(_u32), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
@@ -619,6 +620,10 @@ def su2_batch_set_config(b: int, queue_depth: int, grid: int = 0) -> None:
 
 def su2_batch_set_launch(b: int, queue_depth: int, threads: int, grid: int = 0) -> None:
     _check(_lib.su2_batch_set_launch(b, queue_depth, threads, grid), "su2_batch_set_launch")
+
+
+def su2_batch_set_sampler(b: int, sampler: int) -> None:
+    _check(_lib.su2_batch_set_sampler(b, int(sampler)), "su2_batch_set_sampler")
 
 
 def su2_batch_launch_info(b: int):

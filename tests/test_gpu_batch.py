@@ -138,3 +138,60 @@ def test_batch_rejects_bad_arguments():
         su2.su2_batch_create([4, 5], [4, 4], [2.0, 2.0], [1, 2])
     with pytest.raises(su2.SU2Error):
         su2.su2_batch_create([4], [4], [float("nan")], [1])
+
+
+def oracle_chains_kp(cfg, sweeps):
+    out = []
+    for ns, nt, beta, seed in zip(cfg["ns"], cfg["nt"], cfg["beta"], cfg["seed"]):
+        links = oracle.hot_start(ns, nt, seed) if cfg["start"] == 1 else oracle.cold_start(ns, nt)
+        trials = np.zeros(8, dtype=np.int64)
+        plaq = []
+        for s in range(sweeps):
+            trials += oracle.heatbath_sweep_kp(ns, nt, beta, seed, s, links, nthreads=threads())
+            plaq.append(oracle.plaquette(ns, nt, links))
+        out.append(dict(links=links, trials=trials, plaq=plaq))
+    return out
+
+
+@pytest.mark.parametrize("depth,block", [(4, 128), (2, 256), (8, 64)])
+def test_kennedy_pendleton_batch_matches_the_oracle(depth, block):
+    """The batch with the Kennedy-Pendleton sampler: every lattice bitwise the
+    oracle's KP chain (beta k < 2 links by Creutz's method included: beta 0
+    and 0.5 lattices), trial counts equal, fused plaquettes within 1e-6."""
+    cfg = dict(SMALL)
+    cfg["beta"] = [2.3, 1.7, 6.0, 0.0, 3.0, 0.5]
+    sweeps = 3
+    b = su2.su2_batch_create(cfg["ns"], cfg["nt"], cfg["beta"], cfg["seed"], cfg["start"])
+    try:
+        su2.su2_batch_set_sampler(b, su2.SU2_SAMPLER_KP)
+        su2.su2_batch_set_launch(b, depth, block, 0)
+        assert su2.su2_batch_launch_info(b)[:2] == (depth, block)
+        n = len(cfg["ns"])
+        plaq, _, st = su2.su2_batch_generate(b, n, sweeps, 1)
+        ref = oracle_chains_kp(cfg, sweeps)
+        for i, r in enumerate(ref):
+            assert np.array_equal(su2.su2_batch_get_links(b, i, cfg["ns"][i], cfg["nt"][i]), r["links"]), i
+            for s in range(sweeps):
+                assert close(plaq[s, i], r["plaq"][s]), (i, s)
+        assert st["trials"] == [int(x) for x in sum(r["trials"] for r in ref)]
+        assert st["sampler_failures"] == 0
+    finally:
+        su2.su2_batch_destroy(b)
+
+
+def test_kennedy_pendleton_batch_of_64_uneven_lattices():
+    cfg = workloads.batched(64, seed=5)
+    sweeps = 2
+    b = su2.su2_batch_create(cfg["ns"], cfg["nt"], cfg["beta"], cfg["seed"], cfg["start"])
+    try:
+        su2.su2_batch_set_sampler(b, su2.SU2_SAMPLER_KP)
+        su2.su2_batch_autotune(b, 2)
+        su2.su2_batch_sweep(b, sweeps)
+        for i in range(0, 64, 7):
+            links = oracle.cold_start(cfg["ns"][i], cfg["nt"][i])
+            for s in range(sweeps):
+                oracle.heatbath_sweep_kp(cfg["ns"][i], cfg["nt"][i], cfg["beta"][i], cfg["seed"][i], s, links,
+                                         nthreads=threads())
+            assert np.array_equal(su2.su2_batch_get_links(b, i, cfg["ns"][i], cfg["nt"][i]), links), i
+    finally:
+        su2.su2_batch_destroy(b)
