@@ -52,8 +52,8 @@ TRAIN_BATCH = 16384  # training mini-batch of the learned proposal
 # digest that ties a committed ncu summary to the current kernel) and summary
 SAMPLERS = {
     "kp": {"kernel": "kp_phase_kernel", "name": "Kennedy-Pendleton",
-           "sources": ["paper_1010_1486_gb300/csrc/kp.cu", "paper_1010_1486_gb300/csrc/su2_device.cuh",
-                       "paper_1010_1486_gb300/csrc/staple.cuh"],
+           "sources": ["paper_1010_1486_gb300/csrc/kp.cu", "paper_1010_1486_gb300/csrc/kp_device.cuh",
+                       "paper_1010_1486_gb300/csrc/su2_device.cuh", "paper_1010_1486_gb300/csrc/staple.cuh"],
            "profile": os.path.join(ROOT, "profiles", "kp_phase_48x48x48x48_beta6.md")},
     "creutz": {"kernel": "hb_phase_kernel", "name": "Creutz",
                "sources": ["paper_1010_1486_gb300/csrc/heatbath.cu", "paper_1010_1486_gb300/csrc/su2_device.cuh",

@@ -165,29 +165,27 @@ __device__ void batch_phase(const BatchParams &bp, int parity, uint32_t sweep, C
         int retry_n = 0, done_n = 0;
         double plaq = 0.0;
 
+        // lanes that push nothing write to the last slot, which no live entry
+        // reaches (at most 31 left over + 32 pushed), so the stores need no branch
         auto push_done = [&](bool ok, float4 ut, float val, float ibk, int eo, float4 sp) {
             const unsigned int m = __ballot_sync(0xffffffffu, ok);
-            if (ok) {
-                const int q = done_n + __popc(m & lanes_below);
-                Q.d_ut[q] = ut;
-                Q.d_val[q] = val;
-                Q.d_ibk[q] = ibk;
-                Q.d_eo[q] = eo;
-                if (MEAS) Q.d_sp[q] = sp;
-            }
+            const int q = ok ? done_n + __popc(m & lanes_below) : kCrQueue - 1;
+            Q.d_ut[q] = ut;
+            Q.d_val[q] = val;
+            Q.d_ibk[q] = ibk;
+            Q.d_eo[q] = eo;
+            if (MEAS) Q.d_sp[q] = sp;
             done_n += __popc(m);
         };
         auto push_retry = [&](bool again, float4 ut, float ibk, float e, int eo, int blk, float4 sp) {
             const unsigned int m = __ballot_sync(0xffffffffu, again);
-            if (again) {
-                const int q = retry_n + __popc(m & lanes_below);
-                Q.r_ut[q] = ut;
-                Q.r_ibk[q] = ibk;
-                Q.r_e[q] = e;
-                Q.r_eo[q] = eo;
-                Q.r_blk[q] = blk;
-                if (MEAS) Q.r_sp[q] = sp;
-            }
+            const int q = again ? retry_n + __popc(m & lanes_below) : kCrQueue - 1;
+            Q.r_ut[q] = ut;
+            Q.r_ibk[q] = ibk;
+            Q.r_e[q] = e;
+            Q.r_eo[q] = eo;
+            Q.r_blk[q] = blk;
+            if (MEAS) Q.r_sp[q] = sp;
             retry_n += __popc(m);
         };
         auto direction_pass = [&](int first, int n) {

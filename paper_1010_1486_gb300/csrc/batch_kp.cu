@@ -138,7 +138,7 @@ __device__ void batch_phase_kp(const BatchParams &bp, int parity, uint32_t sweep
             const bool accepted = valid && use_kp && first_ok;
             const bool park = valid && !(use_kp && first_ok);
             const unsigned int parked = __ballot_sync(0xffffffffu, park);
-            if (park) {
+            if (park) {  // rare at large beta k: a branch costs less than stores from every lane
                 const int q = queued + __popc(parked & lanes_below);
                 Q.r_ut[q] = use_kp ? ut : v_cur;
                 Q.r_ibk[q] = bk;

@@ -36,6 +36,8 @@ struct HbParams {
     const unsigned int *gate;  // if non-NULL and *gate == 1 the phase is left to the learned kernel
     double *plaq;              // measuring phases: block partials of the plaquettes of planes (nu < mu, mu)
     SlabRange slab;            // SLAB kernels: the interior eo range and the global keys of its random numbers
+    const float4 *same[4];     // links of direction d at the phase's parity
+    const float4 *other[4];    // ... at the opposite parity
 };
 
 constexpr int kCrThreads = 256;
@@ -94,29 +96,28 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
     double plaq = 0.0;
     int retry_n = 0, done_n = 0;  // warp-uniform queue lengths
 
+    // Lanes that push nothing write to the last slot, which no live entry
+    // reaches (at most 31 left over + 32 pushed = 63), so the stores need no
+    // branch.
     auto push_done = [&](bool ok, float4 ut, float val, float ibk, int eo, float4 sp) {
         const unsigned int m = __ballot_sync(0xffffffffu, ok);
-        if (ok) {
-            const int q = done_n + __popc(m & lanes_below);
-            Q.d_ut[q] = ut;
-            Q.d_val[q] = val;
-            Q.d_ibk[q] = ibk;
-            Q.d_eo[q] = eo;
-            if (MEAS) Q.d_sp[q] = sp;
-        }
+        const int q = ok ? done_n + __popc(m & lanes_below) : kCrQueue - 1;
+        Q.d_ut[q] = ut;
+        Q.d_val[q] = val;
+        Q.d_ibk[q] = ibk;
+        Q.d_eo[q] = eo;
+        if (MEAS) Q.d_sp[q] = sp;
         done_n += __popc(m);
     };
     auto push_retry = [&](bool again, float4 ut, float ibk, float e, int eo, int blk, float4 sp) {
         const unsigned int m = __ballot_sync(0xffffffffu, again);
-        if (again) {
-            const int q = retry_n + __popc(m & lanes_below);
-            Q.r_ut[q] = ut;
-            Q.r_ibk[q] = ibk;
-            Q.r_e[q] = e;
-            Q.r_eo[q] = eo;
-            Q.r_blk[q] = blk;
-            if (MEAS) Q.r_sp[q] = sp;
-        }
+        const int q = again ? retry_n + __popc(m & lanes_below) : kCrQueue - 1;
+        Q.r_ut[q] = ut;
+        Q.r_ibk[q] = ibk;
+        Q.r_e[q] = e;
+        Q.r_eo[q] = eo;
+        Q.r_blk[q] = blk;
+        if (MEAS) Q.r_sp[q] = sp;
         retry_n += __popc(m);
     };
     // directions and stores of direction-queue entries [first, first + n)
@@ -184,11 +185,11 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
         const int e = min(cur, last);
         const Coord x = eo_to_coord(p.g, e, p.parity);
         const int e_p = eo_fwd<MU>(p.g, x, e);
-        v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 0>::value>(p.links, p.g, x, e, e_p, p.parity));
+        v_cur = add_nu_terms(v_cur, load_nu_bases<MU, OtherDir<MU, 0>::value>(p.same, p.other, p.g, x, e, e_p));
         if (MU == 1) sp_cur = v_cur;
-        v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 1>::value>(p.links, p.g, x, e, e_p, p.parity));
+        v_cur = add_nu_terms(v_cur, load_nu_bases<MU, OtherDir<MU, 1>::value>(p.same, p.other, p.g, x, e, e_p));
         if (MU == 2) sp_cur = v_cur;
-        v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 2>::value>(p.links, p.g, x, e, e_p, p.parity));
+        v_cur = add_nu_terms(v_cur, load_nu_bases<MU, OtherDir<MU, 2>::value>(p.same, p.other, p.g, x, e, e_p));
         if (MU == 3) sp_cur = v_cur;
     }
     while (base < eo_end) {  // warp-uniform
@@ -198,13 +199,13 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
         const Coord xn = eo_to_coord(p.g, en, p.parity);
         const int en_p = eo_fwd<MU>(p.g, xn, en);
         // ---- part 0
-        NuLinks nl = load_nu_eo<MU, OtherDir<MU, 0>::value>(p.links, p.g, xn, en, en_p, p.parity);
+        NuLinks nl = load_nu_bases<MU, OtherDir<MU, 0>::value>(p.same, p.other, p.g, xn, en, en_p);
         const DrawSetup d = prepare_draw(v_cur, p.beta);
         const uint4 w = philox_rk(make_uint4((uint32_t)cur + rng_eo, sweep, sw_creutz, 0u), p.rk);
         float4 v_next = add_nu_terms(make_float4(0.0f, 0.0f, 0.0f, 0.0f), nl);
         float4 sp_next = v_next;
         // ---- part 1
-        nl = load_nu_eo<MU, OtherDir<MU, 1>::value>(p.links, p.g, xn, en, en_p, p.parity);
+        nl = load_nu_bases<MU, OtherDir<MU, 1>::value>(p.same, p.other, p.g, xn, en, en_p);
         {
             bool first_ok;
             float val;
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
         v_next = add_nu_terms(v_next, nl);
         if (MU == 2) sp_next = v_next;
         // ---- part 2
-        nl = load_nu_eo<MU, OtherDir<MU, 2>::value>(p.links, p.g, xn, en, en_p, p.parity);
+        nl = load_nu_bases<MU, OtherDir<MU, 2>::value>(p.same, p.other, p.g, xn, en, en_p);
         flush_done();
         v_next = add_nu_terms(v_next, nl);
         if (MU == 3) sp_next = v_next;
@@ -284,6 +285,7 @@ su2_status launch_hb_phase(su2_lattice *lat, int mu, int parity, uint32_t sweep,
     p.trial_slots = lat->scratch.trials;
     p.flags = lat->scratch.flags;
     p.plaq = fused_slot(lat, mu, parity, 0);
+    set_bases(p.same, p.other, lat, parity);
     cudaError_t e;
     if (p.plaq) {
         switch (mu) {
@@ -320,6 +322,7 @@ su2_status launch_hb_phase_slab(su2_lattice *lat, int mu, int parity_local, uint
     p.flags = lat->scratch.flags;
     p.plaq = nullptr;
     p.slab = r;
+    set_bases(p.same, p.other, lat, parity_local);
     cudaError_t e;
     switch (mu) {
     case 0: e = launch_hb<0, false, true>(p, lat->device, lat->stream); break;

@@ -38,6 +38,8 @@ struct KpParams {
     const unsigned int *gate;  // skip the phase while *gate == 1 (learned sweeps)
     double *plaq;              // measuring phases: block partials of the plaquettes of planes (nu < mu, mu)
     SlabRange slab;            // SLAB kernels: the interior eo range and the global keys of its random numbers
+    const float4 *same[4];     // links of direction d at the phase's parity
+    const float4 *other[4];    // ... at the opposite parity
 };
 
 constexpr int kKpWarps = kKpThreads / 32;
@@ -142,11 +144,11 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
         const int e = min(cur, last);
         const Coord x = eo_to_coord(p.g, e, p.parity);
         const int e_p = eo_fwd<MU>(p.g, x, e);
-        v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 0>::value>(p.links, p.g, x, e, e_p, p.parity));
+        v_cur = add_nu_terms(v_cur, load_nu_bases<MU, OtherDir<MU, 0>::value>(p.same, p.other, p.g, x, e, e_p));
         if (MU == 1) sp_cur = v_cur;
-        v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 1>::value>(p.links, p.g, x, e, e_p, p.parity));
+        v_cur = add_nu_terms(v_cur, load_nu_bases<MU, OtherDir<MU, 1>::value>(p.same, p.other, p.g, x, e, e_p));
         if (MU == 2) sp_cur = v_cur;
-        v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 2>::value>(p.links, p.g, x, e, e_p, p.parity));
+        v_cur = add_nu_terms(v_cur, load_nu_bases<MU, OtherDir<MU, 2>::value>(p.same, p.other, p.g, x, e, e_p));
         if (MU == 3) sp_cur = v_cur;
     }
     while (base < eo_end) {  // warp-uniform
@@ -156,7 +158,7 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
         const Coord xn = eo_to_coord(p.g, en, p.parity);
         const int en_p = eo_fwd<MU>(p.g, xn, en);
         // ---- part 0
-        NuLinks nl = load_nu_eo<MU, OtherDir<MU, 0>::value>(p.links, p.g, xn, en, en_p, p.parity);
+        NuLinks nl = load_nu_bases<MU, OtherDir<MU, 0>::value>(p.same, p.other, p.g, xn, en, en_p);
         const float k = __fsqrt_rn(qnorm2(v_cur));
         const float bk = __fmul_rn(p.beta, k);
         const bool use_kp = bk >= kKpMinBk;
@@ -169,13 +171,13 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
         float4 v_next = add_nu_terms(make_float4(0.0f, 0.0f, 0.0f, 0.0f), nl);
         float4 sp_next = v_next;
         // ---- part 1
-        nl = load_nu_eo<MU, OtherDir<MU, 1>::value>(p.links, p.g, xn, en, en_p, p.parity);
+        nl = load_nu_bases<MU, OtherDir<MU, 1>::value>(p.same, p.other, p.g, xn, en, en_p);
         float a0;
         const bool first_ok = kp_trial(w, __fmul_rn(2.0f, bk), a0);
         const bool accepted = valid && use_kp && first_ok;
         const bool park = valid && !(use_kp && first_ok);  // rejected, or beta k < 2 (Creutz, in the queue)
         const unsigned int parked = __ballot_sync(0xffffffffu, park);
-        if (park) {
+        if (park) {  // rare at large beta k: a branch costs less than stores from every lane
             const int q = queued + __popc(parked & lanes_below);
             s_ut[wib][q] = use_kp ? ut : v_cur;
             s_bk[wib][q] = bk;
@@ -186,7 +188,7 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
         v_next = add_nu_terms(v_next, nl);
         if (MU == 2) sp_next = v_next;
         // ---- part 2
-        nl = load_nu_eo<MU, OtherDir<MU, 2>::value>(p.links, p.g, xn, en, en_p, p.parity);
+        nl = load_nu_bases<MU, OtherDir<MU, 2>::value>(p.same, p.other, p.g, xn, en, en_p);
         const float4 out = direction_update(a0, ut, wd);
         if (accepted) p.links[link_index(p.g, MU, p.parity, cur)] = out;
         if (MEAS && accepted) plaq += (double)qmul_re(out, sp_cur);
@@ -250,6 +252,7 @@ su2_status launch_kp_phase(su2_lattice *lat, int mu, int parity, uint32_t sweep,
     p.flags = lat->scratch.flags;
     p.gate = gate;
     p.plaq = fused_slot(lat, mu, parity, 0);
+    set_bases(p.same, p.other, lat, parity);
     cudaError_t e;
     if (p.plaq) {
         switch (mu) {
@@ -285,6 +288,7 @@ su2_status launch_kp_phase_slab(su2_lattice *lat, int mu, int parity_local, uint
     p.gate = nullptr;
     p.plaq = nullptr;
     p.slab = r;
+    set_bases(p.same, p.other, lat, parity_local);
     cudaError_t e;
     switch (mu) {
     case 0: e = launch_kp<0, false, true>(p, lat->device, lat->stream); break;

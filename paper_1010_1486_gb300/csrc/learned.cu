@@ -50,6 +50,8 @@ struct LearnedParams {
     unsigned long long *acc_slots;     // [8][64]: accepted links per phase (call total)
     unsigned long long *sweep_slots;   // [64]: accepted links of this sweep
     double *plaq;                      // measuring phases: block partials of the plaquettes of planes (nu < mu, mu)
+    const float4 *same[4];             // links of direction d at the phase's parity
+    const float4 *other[4];            // ... at the opposite parity
 };
 
 __device__ __forceinline__ unsigned int block_sum_u32(unsigned int v)
@@ -104,11 +106,11 @@ __global__ void __launch_bounds__(kLearnThreads, kLearnMinBlocks) learned_phase_
         const int e = min(cur, last);
         const Coord x = eo_to_coord(p.g, e, p.parity);
         const int e_p = eo_fwd<MU>(p.g, x, e);
-        v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 0>::value>(p.links, p.g, x, e, e_p, p.parity));
+        v_cur = add_nu_terms(v_cur, load_nu_bases<MU, OtherDir<MU, 0>::value>(p.same, p.other, p.g, x, e, e_p));
         if (MU == 1) sp_cur = v_cur;
-        v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 1>::value>(p.links, p.g, x, e, e_p, p.parity));
+        v_cur = add_nu_terms(v_cur, load_nu_bases<MU, OtherDir<MU, 1>::value>(p.same, p.other, p.g, x, e, e_p));
         if (MU == 2) sp_cur = v_cur;
-        v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 2>::value>(p.links, p.g, x, e, e_p, p.parity));
+        v_cur = add_nu_terms(v_cur, load_nu_bases<MU, OtherDir<MU, 2>::value>(p.same, p.other, p.g, x, e, e_p));
         if (MU == 3) sp_cur = v_cur;
     }
     while (base < p.g.vh) {  // warp-uniform
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(kLearnThreads, kLearnMinBlocks) learned_phase_
         const Coord xn = eo_to_coord(p.g, en, p.parity);
         const int en_p = eo_fwd<MU>(p.g, xn, en);
         // ---- part 0
-        NuLinks nl = load_nu_eo<MU, OtherDir<MU, 0>::value>(p.links, p.g, xn, en, en_p, p.parity);
+        NuLinks nl = load_nu_bases<MU, OtherDir<MU, 0>::value>(p.same, p.other, p.g, xn, en, en_p);
         const uint32_t li = link_index(p.g, MU, p.parity, min(cur, last));
         const float4 old = p.links[li];
         const uint4 w = philox_rk(make_uint4((uint32_t)cur, p.sweep, sw, 0u), p.rk);
@@ -126,13 +128,13 @@ __global__ void __launch_bounds__(kLearnThreads, kLearnMinBlocks) learned_phase_
         float4 v_next = add_nu_terms(make_float4(0.0f, 0.0f, 0.0f, 0.0f), nl);
         float4 sp_next = v_next;
         // ---- part 1
-        nl = load_nu_eo<MU, OtherDir<MU, 1>::value>(p.links, p.g, xn, en, en_p, p.parity);
+        nl = load_nu_bases<MU, OtherDir<MU, 1>::value>(p.same, p.other, p.g, xn, en, en_p);
         const bool ok = learned::learned_accept(r, old, uniform01(w.y), valid);
         const bool accept = valid && ok;
         v_next = add_nu_terms(v_next, nl);
         if (MU == 2) sp_next = v_next;
         // ---- part 2
-        nl = load_nu_eo<MU, OtherDir<MU, 2>::value>(p.links, p.g, xn, en, en_p, p.parity);
+        nl = load_nu_bases<MU, OtherDir<MU, 2>::value>(p.same, p.other, p.g, xn, en, en_p);
         const float4 out = direction_from_uniforms(r.a_new, r.d.ut, uniform01(w.z), uniform01(w.w));
         if (accept) p.links[li] = out;
         if (MEAS && valid) plaq += (double)qmul_re(accept ? out : old, sp_cur);
@@ -244,6 +246,7 @@ static su2_status launch_learned_phase(su2_lattice *lat, int mu, int parity)
     p.acc_slots = lat->accept_slots;
     p.sweep_slots = lat->accept_slots + 8 * kAcceptSlots;
     p.plaq = fused_slot(lat, mu, parity, 1);
+    set_bases(p.same, p.other, lat, parity);
     const size_t smem = sizeof(float2) * (size_t)(p.G - 1) * learned::kParams;
     const int want = (p.g.vh + kLearnThreads - 1) / kLearnThreads;
     cudaError_t e;

@@ -24,6 +24,8 @@ struct OrParams {
     Geom g;
     int parity;
     double *plaq;  // measuring phases: block partials of the plaquettes of planes (nu < mu, mu)
+    const float4 *same[4];   // links of direction d at the phase's parity
+    const float4 *other[4];  // ... at the opposite parity
 };
 
 // U~^dag from the staple (identity if k = 0), as the heat bath's setup.
@@ -59,11 +61,11 @@ __global__ void __launch_bounds__(kOrThreads, kOrMinBlocks) or_phase_kernel(cons
         const int e = min(cur, last);
         const Coord x = eo_to_coord(p.g, e, p.parity);
         const int e_p = eo_fwd<MU>(p.g, x, e);
-        v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 0>::value>(p.links, p.g, x, e, e_p, p.parity));
+        v_cur = add_nu_terms(v_cur, load_nu_bases<MU, OtherDir<MU, 0>::value>(p.same, p.other, p.g, x, e, e_p));
         if (MU == 1) sp_cur = v_cur;
-        v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 1>::value>(p.links, p.g, x, e, e_p, p.parity));
+        v_cur = add_nu_terms(v_cur, load_nu_bases<MU, OtherDir<MU, 1>::value>(p.same, p.other, p.g, x, e, e_p));
         if (MU == 2) sp_cur = v_cur;
-        v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 2>::value>(p.links, p.g, x, e, e_p, p.parity));
+        v_cur = add_nu_terms(v_cur, load_nu_bases<MU, OtherDir<MU, 2>::value>(p.same, p.other, p.g, x, e, e_p));
         if (MU == 3) sp_cur = v_cur;
     }
     while (base < p.g.vh) {  // warp-uniform
@@ -73,19 +75,19 @@ __global__ void __launch_bounds__(kOrThreads, kOrMinBlocks) or_phase_kernel(cons
         const Coord xn = eo_to_coord(p.g, en, p.parity);
         const int en_p = eo_fwd<MU>(p.g, xn, en);
         // ---- part 0
-        NuLinks nl = load_nu_eo<MU, OtherDir<MU, 0>::value>(p.links, p.g, xn, en, en_p, p.parity);
+        NuLinks nl = load_nu_bases<MU, OtherDir<MU, 0>::value>(p.same, p.other, p.g, xn, en, en_p);
         const uint32_t li = link_index(p.g, MU, p.parity, min(cur, last));
         const float4 old = p.links[li];
         const float4 ut = staple_direction(v_cur);
         float4 v_next = add_nu_terms(make_float4(0.0f, 0.0f, 0.0f, 0.0f), nl);
         float4 sp_next = v_next;
         // ---- part 1
-        nl = load_nu_eo<MU, OtherDir<MU, 1>::value>(p.links, p.g, xn, en, en_p, p.parity);
+        nl = load_nu_bases<MU, OtherDir<MU, 1>::value>(p.same, p.other, p.g, xn, en, en_p);
         const float4 t = qmul(ut, qdag(old));
         v_next = add_nu_terms(v_next, nl);
         if (MU == 2) sp_next = v_next;
         // ---- part 2
-        nl = load_nu_eo<MU, OtherDir<MU, 2>::value>(p.links, p.g, xn, en, en_p, p.parity);
+        nl = load_nu_bases<MU, OtherDir<MU, 2>::value>(p.same, p.other, p.g, xn, en, en_p);
         const float4 out = qmul(t, ut);
         if (valid) p.links[li] = out;
         if (MEAS && valid) plaq += (double)qmul_re(out, sp_cur);
@@ -128,6 +130,7 @@ su2_status launch_or_phase(su2_lattice *lat, int mu, int parity)
     p.g = geom_of(lat);
     p.parity = parity;
     p.plaq = fused_slot(lat, mu, parity, 0);
+    set_bases(p.same, p.other, lat, parity);
     cudaError_t e;
     if (p.plaq) {
         switch (mu) {

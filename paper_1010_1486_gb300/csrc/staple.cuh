@@ -87,6 +87,23 @@ __device__ __forceinline__ NuLinks load_nu_eo(const float4 *__restrict__ L, cons
     return n;
 }
 
+// As load_nu_eo with the launch's array bases precomputed: same[d] = links of
+// direction d at the phase's parity, other[d] = at the opposite parity.
+template <int MU, int NU>
+__device__ __forceinline__ NuLinks load_nu_bases(const float4 *const *same, const float4 *const *other, const Geom &g,
+                                                 const Coord &x, int eo, int e_p)
+{
+    const int off_m = eo_bwd_offset<NU>(g, x);
+    NuLinks n;
+    n.nu_xp = __ldg(other[NU] + (uint32_t)e_p);
+    n.mu_xn = __ldg(other[MU] + (uint32_t)eo_fwd<NU>(g, x, eo));
+    n.nu_x = __ldg(same[NU] + (uint32_t)eo);
+    n.nu_xpm = __ldg(same[NU] + (uint32_t)(e_p + off_m));
+    n.mu_xm = __ldg(other[MU] + (uint32_t)(eo + off_m));
+    n.nu_xm = __ldg(other[NU] + (uint32_t)(eo + off_m));
+    return n;
+}
+
 // The three directions nu != MU in ascending order.
 template <int MU, int J>
 struct OtherDir {

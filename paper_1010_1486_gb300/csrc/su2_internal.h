@@ -149,6 +149,17 @@ inline Geom make_geom(int ns, int nt)
 
 inline Geom geom_of(const su2_lattice *lat) { return make_geom(lat->ns, lat->nt); }
 
+// The link arrays a phase of the given parity reads, by direction: same[d] at
+// that parity, other[d] at the opposite one (kernel parameters, so the
+// kernels address them from the constant bank instead of recomputing them).
+inline void set_bases(const float4 **same, const float4 **other, const su2_lattice *lat, int parity)
+{
+    for (int d = 0; d < 4; ++d) {
+        same[d] = lat->links + (size_t)(2 * d + parity) * (size_t)lat->vh;
+        other[d] = lat->links + (size_t)(2 * d + (parity ^ 1)) * (size_t)lat->vh;
+    }
+}
+
 inline int grid_for(int64_t n, int threads, int64_t cap = 152 * 64)
 {
     int64_t b = (n + threads - 1) / threads;
