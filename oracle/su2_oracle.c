@@ -379,13 +379,35 @@ void orc_staple(int ns, int nt, const float *links, int64_t s, int mu, float v[4
 /*   a = (a0, r sqrt(1-c^2) cos phi, r sqrt(1-c^2) sin phi, r c), r=sqrt(1-a0^2),*/
 /*   c uniform in [-1,1], phi uniform in [0,2pi);  U' = a U~^dag.             */
 /* Trial t uses uniforms 2(t&1), 2(t&1)+1 of block t>>1 of the Creutz stream; */
-/* the direction uses uniforms 0,1 of block 0 of the direction stream.        */
+/* the direction uses uniforms 2(eo&1), 2(eo&1)+1 of direction block eo>>1.   */
 /* beta k < 1e-6 (e.g. beta = 0): a0 = 2 r1 - 1, same acceptance test (Haar). */
 /* beta k > 43: exp(-2 beta k) is taken as 0 (below the binary32 normal range).*/
 /* Returns the number of trials, or -1 if 4096 trials were all rejected, in   */
 /* which case out[] is left untouched.                                         */
 /* ------------------------------------------------------------------------ */
 #define ORC_MAX_TRIALS 4096
+
+/* The new link from its a0 (Sec. 2): the vector part uniform on the sphere of
+ * radius r = sqrt(1 - a0^2), a = (a0, r sqrt(1-c^2) cos phi, r sqrt(1-c^2)
+ * sin phi, r c) with c = 2 u - 1 and phi = 2 pi v, and U' = a U~^dag.  The
+ * uniforms (u, v) of the link with even/odd index eo are words 0, 1 of
+ * direction block eo/2 for even eo and words 2, 3 for odd eo: the two links
+ * of a pair share one Philox block, each using words the other does not. */
+static void heatbath_direction(float a0, const float ut[4], uint64_t seed, uint32_t eo, uint32_t sweep, int parity,
+                               int mu, float out[4])
+{
+    float d[4];
+    draw_block(seed, eo >> 1, sweep, ORC_KIND_DIRECTION, parity, mu, 0u, d);
+    const float u = d[2 * (eo & 1u)], v = d[2 * (eo & 1u) + 1];
+    float r = sqrtf(fmaf(-a0, a0, 1.0f));
+    float c = 2.0f * u - 1.0f;
+    float st = sqrtf(fmaf(-c, c, 1.0f));
+    float sn, cs;
+    orc_sincos2pi(v, &sn, &cs);
+    float rs = r * st;
+    float a[4] = {a0, rs * cs, rs * sn, r * c};
+    orc_quat_mul(a, ut, out);
+}
 
 /* What a link's Creutz trials need from beta k (Sec. 2): e = exp(-2 beta k)
  * (0 on the Haar branch and above beta k = 43), 1 - e and 1/(beta k). */
@@ -461,16 +483,7 @@ int orc_heatbath_link(float beta, const float v[4], uint64_t seed, uint32_t eo, 
     }
     if (!accepted) return -1;
 
-    float d[4];
-    draw_block(seed, eo, sweep, ORC_KIND_DIRECTION, parity, mu, 0u, d);
-    float r = sqrtf(fmaf(-a0, a0, 1.0f));
-    float c = 2.0f * d[0] - 1.0f;
-    float st = sqrtf(fmaf(-c, c, 1.0f));
-    float sn, cs;
-    orc_sincos2pi(d[1], &sn, &cs);
-    float rs = r * st;
-    float a[4] = {a0, rs * cs, rs * sn, r * c};
-    orc_quat_mul(a, ut, out);
+    heatbath_direction(a0, ut, seed, eo, sweep, parity, mu, out);
     return trials;
 }
 
@@ -748,16 +761,7 @@ int orc_heatbath_link_kp(float beta, const float v[4], uint64_t seed, uint32_t e
         }
     }
     if (trials == 0) return -1;
-    float d[4];
-    draw_block(seed, eo, sweep, ORC_KIND_DIRECTION, parity, mu, 0u, d);
-    float r = sqrtf(fmaf(-a0, a0, 1.0f));
-    float c = 2.0f * d[0] - 1.0f;
-    float st = sqrtf(fmaf(-c, c, 1.0f));
-    float sn, cs;
-    orc_sincos2pi(d[1], &sn, &cs);
-    float rs = r * st;
-    float a[4] = {a0, rs * cs, rs * sn, r * c};
-    orc_quat_mul(a, ut, out);
+    heatbath_direction(a0, ut, seed, eo, sweep, parity, mu, out);
     return trials;
 }
 

@@ -193,8 +193,8 @@ __device__ void batch_phase(const BatchParams &bp, int parity, uint32_t sweep, C
             if (lane < n) {
                 const int q = first + lane;
                 const int eo = Q.d_eo[q];
-                const uint4 wd = philox_key(make_uint4((uint32_t)eo, sweep, sw_dir, 0u), k0, k1);
-                const float4 out = direction_update(deferred_a0(Q.d_val[q], Q.d_ibk[q]), Q.d_ut[q], wd);
+                const uint4 wd = philox_key(make_uint4(direction_pair((uint32_t)eo), sweep, sw_dir, 0u), k0, k1);
+                const float4 out = direction_update(deferred_a0(Q.d_val[q], Q.d_ibk[q]), Q.d_ut[q], wd, (uint32_t)eo);
                 links[link_index(g, MU, parity, eo)] = out;
                 if (MEAS) plaq += (double)qmul_re(out, Q.d_sp[q]);
             }

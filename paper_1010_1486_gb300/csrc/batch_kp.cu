@@ -85,7 +85,8 @@ __device__ void batch_phase_kp(const BatchParams &bp, int parity, uint32_t sweep
                 }
                 if (t < 0) {
                 } else if (t < kMaxTrials) {
-                    const float4 out = direction_update(a0, ut, gen(make_uint4((uint32_t)eo, sweep, sw_dir, 0u)));
+                    const float4 out = direction_update(
+                        a0, ut, gen(make_uint4(direction_pair((uint32_t)eo), sweep, sw_dir, 0u)), (uint32_t)eo);
                     links[link_index(g, MU, parity, eo)] = out;
                     if (MEAS) plaq += (double)qmul_re(out, Q.r_sp[q]);
                     my_trials += (unsigned int)(t + 1);
@@ -111,9 +112,13 @@ __device__ void batch_phase_kp(const BatchParams &bp, int parity, uint32_t sweep
             v_cur = add_nu_terms(v_cur, load_nu_eo<MU, OtherDir<MU, 2>::value, false>(links, g, x, e, e_p, parity));
             if (MU == 3) sp_cur = v_cur;
         }
+        // one direction block per pair of links, as in kp_phase_kernel: in even
+        // rounds lanes 0..15 draw this round's pairs, lanes 16..31 the next's
+        uint4 dblk = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll 1
         for (int r = 0; r < rounds; ++r) {
             const bool valid = cur <= last;
+            const bool even_round = (r & 1) == 0;
             const int nxt = cur + 32;
             const int en = min(nxt, last);  // the last round reloads its own links: harmless
             const Coord xn = eo_to_coord(g, en, parity);
@@ -127,8 +132,13 @@ __device__ void batch_phase_kp(const BatchParams &bp, int parity, uint32_t sweep
             const float4 ut = make_float4(__fmul_rn(v_cur.x, inv_k), __fmul_rn(-v_cur.y, inv_k),
                                           __fmul_rn(-v_cur.z, inv_k), __fmul_rn(-v_cur.w, inv_k));
             uint4 w = make_uint4((uint32_t)cur, sweep, sw_kp, 0u);
-            uint4 wd = make_uint4((uint32_t)cur, sweep, sw_dir, 0u);
-            philox2_key(w, wd, k0, k1);
+            if (even_round) {  // warp-uniform
+                const int rb = base0 + 32 * r + (lane < 16 ? 0 : 32);
+                dblk = make_uint4(direction_pair((uint32_t)rb) + (uint32_t)(lane & 15), sweep, sw_dir, 0u);
+                philox2_key(w, dblk, k0, k1);
+            } else {
+                w = gen(w);
+            }
             float4 v_next = add_nu_terms(make_float4(0.0f, 0.0f, 0.0f, 0.0f), nl);
             float4 sp_next = v_next;
             // ---- part 1
@@ -150,7 +160,10 @@ __device__ void batch_phase_kp(const BatchParams &bp, int parity, uint32_t sweep
             if (MU == 2) sp_next = v_next;
             // ---- part 2
             nl = load_nu_eo<MU, OtherDir<MU, 2>::value, false>(links, g, xn, en, en_p, parity);
-            const float4 out = direction_update(a0, ut, wd);
+            const int src = (even_round ? 0 : 16) + (lane >> 1);
+            const uint4 wd = make_uint4(__shfl_sync(0xffffffffu, dblk.x, src), __shfl_sync(0xffffffffu, dblk.y, src),
+                                        __shfl_sync(0xffffffffu, dblk.z, src), __shfl_sync(0xffffffffu, dblk.w, src));
+            const float4 out = direction_update(a0, ut, wd, (uint32_t)cur);
             if (accepted) links[link_index(g, MU, parity, cur)] = out;
             if (MEAS && accepted) plaq += (double)qmul_re(out, sp_cur);
             my_trials += accepted ? 1u : 0u;

@@ -126,8 +126,9 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
         if (lane < n) {
             const int q = first + lane;
             const int eo = Q.d_eo[q];
-            const uint4 wd = philox_rk(make_uint4((uint32_t)eo + rng_eo, sweep, sw_dir, 0u), p.rk);
-            const float4 out = direction_update(deferred_a0(Q.d_val[q], Q.d_ibk[q]), Q.d_ut[q], wd);
+            const uint32_t eo_g = (uint32_t)eo + rng_eo;
+            const uint4 wd = philox_rk(make_uint4(direction_pair(eo_g), sweep, sw_dir, 0u), p.rk);
+            const float4 out = direction_update(deferred_a0(Q.d_val[q], Q.d_ibk[q]), Q.d_ut[q], wd, eo_g);
             p.links[link_index(p.g, MU, p.parity, eo)] = out;
             if (MEAS) plaq += (double)qmul_re(out, Q.d_sp[q]);
         }

@@ -124,7 +124,9 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
             if (t < 0) {
             } else if (t < p.max_trials) {
                 const float4 out =
-                    direction_update(a0, ut, philox_rk(make_uint4((uint32_t)eo + rng_eo, sweep, sw_dir, 0u), p.rk));
+                    direction_update(a0, ut,
+                                     philox_rk(make_uint4(direction_pair((uint32_t)eo + rng_eo), sweep, sw_dir, 0u), p.rk),
+                                     (uint32_t)eo + rng_eo);
                 p.links[link_index(p.g, MU, p.parity, eo)] = out;
                 if (MEAS) plaq += (double)qmul_re(out, s_sp[MEAS ? wib : 0][q]);
                 trials += (unsigned int)(t + 1);
@@ -151,6 +153,13 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
         v_cur = add_nu_terms(v_cur, load_nu_bases<MU, OtherDir<MU, 2>::value>(p.same, p.other, p.g, x, e, e_p));
         if (MU == 3) sp_cur = v_cur;
     }
+    // Direction blocks, one per pair of links (2j, 2j + 1) of a round: in an
+    // even round of the warp, lanes 0..15 draw the blocks of this round's 16
+    // pairs and lanes 16..31 those of the next round's (base + stride), so a
+    // lane draws three Philox blocks per two links; each link takes its two
+    // words from the lane that drew its pair's block.
+    bool even_round = true;
+    uint4 dblk = make_uint4(0u, 0u, 0u, 0u);
     while (base < eo_end) {  // warp-uniform
         const bool valid = cur <= last;
         const int nxt = cur + stride;
@@ -166,8 +175,13 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
         const float4 ut = make_float4(__fmul_rn(v_cur.x, inv_k), __fmul_rn(-v_cur.y, inv_k),
                                       __fmul_rn(-v_cur.z, inv_k), __fmul_rn(-v_cur.w, inv_k));
         uint4 w = make_uint4((uint32_t)cur + rng_eo, sweep, sw_kp, 0u);
-        uint4 wd = make_uint4((uint32_t)cur + rng_eo, sweep, sw_dir, 0u);
-        philox2_rk(w, wd, p.rk);
+        if (even_round) {  // warp-uniform
+            const uint32_t pair0 = direction_pair((uint32_t)(lane < 16 ? base : base + stride) + rng_eo);
+            dblk = make_uint4(pair0 + (uint32_t)(lane & 15), sweep, sw_dir, 0u);
+            philox2_rk(w, dblk, p.rk);
+        } else {
+            w = philox_rk(w, p.rk);
+        }
         float4 v_next = add_nu_terms(make_float4(0.0f, 0.0f, 0.0f, 0.0f), nl);
         float4 sp_next = v_next;
         // ---- part 1
@@ -189,7 +203,10 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
         if (MU == 2) sp_next = v_next;
         // ---- part 2
         nl = load_nu_bases<MU, OtherDir<MU, 2>::value>(p.same, p.other, p.g, xn, en, en_p);
-        const float4 out = direction_update(a0, ut, wd);
+        const int src = (even_round ? 0 : 16) + (lane >> 1);
+        const uint4 wd = make_uint4(__shfl_sync(0xffffffffu, dblk.x, src), __shfl_sync(0xffffffffu, dblk.y, src),
+                                    __shfl_sync(0xffffffffu, dblk.z, src), __shfl_sync(0xffffffffu, dblk.w, src));
+        const float4 out = direction_update(a0, ut, wd, (uint32_t)cur + rng_eo);
         if (accepted) p.links[link_index(p.g, MU, p.parity, cur)] = out;
         if (MEAS && accepted) plaq += (double)qmul_re(out, sp_cur);
         trials += accepted ? 1u : 0u;
@@ -204,6 +221,7 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
         cur = nxt;
         v_cur = v_next;
         sp_cur = sp_next;
+        even_round = !even_round;
     }
     if (queued > 0) retry(0, queued);
     const unsigned int wsum = __reduce_add_sync(0xffffffffu, trials);

@@ -396,14 +396,20 @@ __device__ __forceinline__ float4 direction_from_uniforms(float a0, float4 ut, f
     return qmul(a, ut);
 }
 
-__device__ __forceinline__ float4 direction_update(float a0, float4 ut, uint4 d)
+// The direction block of the link with (global) even/odd index eo is block 0
+// of the direction stream at counter eo >> 1, shared by the pair of links
+// eo = 2j, 2j + 1: the even one takes words 0, 1, the odd one words 2, 3.
+__device__ __forceinline__ uint32_t direction_pair(uint32_t eo) { return eo >> 1; }
+
+__device__ __forceinline__ float4 direction_update(float a0, float4 ut, uint4 d, uint32_t eo)
 {
-    return direction_from_uniforms(a0, ut, uniform01(d.x), uniform01(d.y));
+    const bool odd = (eo & 1u) != 0u;
+    return direction_from_uniforms(a0, ut, uniform01(odd ? d.z : d.x), uniform01(odd ? d.w : d.y));
 }
 
 // The whole heat-bath draw of one link from its staple v (Sec. 2), trial by
 // trial: trial t uses words 2(t&1), 2(t&1)+1 of Creutz block t>>1; the
-// direction uses words 0, 1 of direction block 0.  Returns the number of
+// direction uses the link's two words of its pair's direction block.  Returns the number of
 // trials, or 0 if kMaxTrials were all rejected (out untouched).  gen(counter)
 // is the Philox generator under the lattice's key.
 template <class Gen>
@@ -427,7 +433,8 @@ __device__ __forceinline__ int heatbath_draw_gen(float4 v, float beta, Gen gen, 
         }
     }
     if (trials == 0) return 0;
-    out = direction_update(a0, s.ut, gen(make_uint4(eo, sweep, stream_word(kDirection, parity, mu), 0u)));
+    out = direction_update(a0, s.ut, gen(make_uint4(direction_pair(eo), sweep, stream_word(kDirection, parity, mu), 0u)),
+                           eo);
     return trials;
 }
 

@@ -10,6 +10,7 @@
 - The tau_int estimator on an AR(1) series with known tau_int.
 """
 import numpy as np
+from scipy import stats
 import pytest
 
 import oracle
@@ -173,3 +174,37 @@ def test_kennedy_pendleton_chain_matches_creutz_chain():
         res.append((series.mean(), err))
     (m1, e1), (m2, e2) = res
     assert abs(m1 - m2) < 4 * np.hypot(e1, e2), res
+
+
+def _direction(out, ut):
+    """(c, phi) of the vector part of a = U' U~ (U' = a U~^dag): a3 = r c,
+    (a1, a2) = r sqrt(1 - c^2) (cos phi, sin phi)."""
+    a = oracle.quat_mul(out, ut)
+    r = np.sqrt(max(1.0 - float(a[0]) ** 2, 1e-30))
+    return float(a[3]) / r, float(np.arctan2(a[2], a[1])) % (2 * np.pi)
+
+
+def test_paired_links_draw_independent_uniform_directions():
+    """The two links of a pair (even/odd indices 2j, 2j + 1) take their
+    direction uniforms from different words of one Philox block: each
+    direction is uniform on the sphere (c uniform in [-1, 1], phi in
+    [0, 2 pi)) and the pair's directions are independent (2-D chi^2 on
+    (c_even, c_odd), (phi_even, phi_odd) and (c_even, phi_odd))."""
+    v = np.array([2.1, -0.7, 0.4, 1.3], dtype=np.float32)
+    k = float(np.sqrt(np.dot(v.astype(np.float64), v)))
+    ut = np.array([v[0] / k, v[1] / k, v[2] / k, v[3] / k], dtype=np.float32)  # U~ = V / k
+    n = 12_000
+    ce, co, pe, po = np.empty(n), np.empty(n), np.empty(n), np.empty(n)
+    for j in range(n):
+        a, _ = oracle.heatbath_link(1.5, v, 77, 2 * j, 3, 1, 2)
+        b, _ = oracle.heatbath_link(1.5, v, 77, 2 * j + 1, 3, 1, 2)
+        ce[j], pe[j] = _direction(a, ut)
+        co[j], po[j] = _direction(b, ut)
+    for x, lo, hi in ((ce, -1, 1), (co, -1, 1), (pe, 0, 2 * np.pi), (po, 0, 2 * np.pi)):
+        assert chi2_pvalue_uniform(x, lo, hi, nbins=40) > 1e-3
+    for x, y, xr, yr in ((ce, co, (-1, 1), (-1, 1)), (pe, po, (0, 2 * np.pi), (0, 2 * np.pi)),
+                         (ce, po, (-1, 1), (0, 2 * np.pi))):
+        h, _, _ = np.histogram2d(x, y, bins=8, range=(xr, yr))
+        e = n / 64.0
+        assert stats.chi2.sf(((h - e) ** 2 / e).sum(), 63) > 1e-3
+    assert np.corrcoef(ce, co)[0, 1] ** 2 < 1e-3
