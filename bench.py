@@ -503,7 +503,7 @@ def run_batched(args, dist, su2, torch):
             "sites": sites, "value": value, "unit": UNIT, "sweeps_per_s": args.batched_steps / (ms * 1e-3),
             "ms_per_sweep": ms / args.batched_steps,
             "autotuned": {"queue_depth": tuned[0], "threads_per_block": tuned[1], "grid_blocks": tuned[2],
-                          "search": "queue depth 2/4/8 x 64/128/256 threads x full or half grid, 5 sweeps each"},
+                          "search": "queue depth 1/2/4/8 x 64/128/256 threads x full or half grid, 5 sweeps each"},
             "fixed_config": {"queue_depth": fixed[0], "threads_per_block": fixed[1], "grid_blocks": fixed[2],
                              "ms_per_sweep": fixed_ms},
             "autotuned_speedup_vs_fixed": fixed_ms / (ms / args.batched_steps),

@@ -396,13 +396,13 @@ su2_status su2_batch_polyakov(su2_batch *b, double *out_n);
 /* Links of lattice i in the layout of su2_get_links. */
 su2_status su2_batch_get_links(su2_batch *b, int i, float *host);
 
-/* Launch configuration: queue depth (2, 4 or 8: the work is split into chunks
- * of 32 x depth sites, and each warp takes a contiguous range of chunks),
+/* Launch configuration: queue depth (1, 2, 4 or 8: the work is split into
+ * chunks of 32 x depth sites, and each warp takes a contiguous range of chunks),
  * block size (64, 128 or 256 threads; the register budget is that of 768
  * threads per SM for every size) and grid (<= 0 or too large = all
  * co-resident blocks).  The default is depth 4, 128 threads, all co-resident
  * blocks.  su2_batch_set_config keeps the block size.  su2_batch_autotune
- * times all 18 combinations of depth, block size and full or half grid over
+ * times all 24 combinations of depth, block size and full or half grid over
  * `sweeps` sweeps each, restores the links and sweep counter, and keeps the
  * fastest (reported by su2_batch_launch_info). */
 su2_status su2_batch_set_launch(su2_batch *b, int queue_depth, int threads, int grid);

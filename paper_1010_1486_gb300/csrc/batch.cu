@@ -68,8 +68,8 @@ struct su2_batch {
     int *d_chunk_prefix = nullptr;
     int *d_mround_prefix = nullptr;
     double *d_partials = nullptr;
-    double *d_chunk_partials = nullptr;  // [3][chunks at queue depth 2, the most]
-    int *d_chunk_owner = nullptr;        // [chunks at queue depth 2]
+    double *d_chunk_partials = nullptr;  // [3][chunks at queue depth 1, the most]
+    int *d_chunk_owner = nullptr;        // [chunks at queue depth 1]
     int *d_mround_owner = nullptr;       // [total_mrounds]
     int2 *d_poly_rounds = nullptr;       // [total_poly_rounds]
     int total_poly_rounds = 0;
@@ -84,7 +84,7 @@ struct su2_batch {
     int threads = 128;  // block size: 64, 128 or 256
     int grid = 0;
     int sampler = SU2_SAMPLER_CREUTZ;
-    int max_grid[2][3][3] = {};  // co-resident blocks: sampler x R = 2, 4, 8 x block sizes 64, 128, 256
+    int max_grid[2][4][3] = {};  // co-resident blocks: sampler x R = 1, 2, 4, 8 x block sizes 64, 128, 256
     uint32_t sweep = 0;
     unsigned long long timeout_ns = 2000000000ull;
     bool use_graph = true;
@@ -96,12 +96,13 @@ struct su2_batch {
 namespace su2 {
 namespace {
 
-int r_index(int R) { return R == 2 ? 0 : (R == 4 ? 1 : 2); }
+int r_index(int R) { return R == 1 ? 0 : (R == 2 ? 1 : (R == 4 ? 2 : 3)); }
 int t_index(int T) { return T == 64 ? 0 : (T == 128 ? 1 : 2); }
 
 void *kernel_for(int sampler, int R, int T)
 {
-    return sampler == SU2_SAMPLER_KP ? batch_kernel_kp(R, T) : batch_kernel_creutz(R, T);
+    if (sampler == SU2_SAMPLER_KP) return R <= 2 ? batch_kernel_kp_12(R, T) : batch_kernel_kp_48(R, T);
+    return R <= 2 ? batch_kernel_creutz_12(R, T) : batch_kernel_creutz_48(R, T);
 }
 
 void drop_graphs(su2_batch *b)
@@ -263,22 +264,8 @@ su2_status ensure_history(su2_batch *b, int n)
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-template <int R>
-void *creutz_for_t(int T)
-{
-    if (T == 64) return (void *)batch_sweep_kernel<R, 64, kBatchCreutz>;
-    if (T == 256) return (void *)batch_sweep_kernel<R, 256, kBatchCreutz>;
-    return (void *)batch_sweep_kernel<R, 128, kBatchCreutz>;
-}
-
 }  // namespace
 
-void *batch_kernel_creutz(int R, int T)
-{
-    if (R == 2) return creutz_for_t<2>(T);
-    if (R == 8) return creutz_for_t<8>(T);
-    return creutz_for_t<4>(T);
-}
 
 }  // namespace su2
 
@@ -323,11 +310,11 @@ su2_status su2_batch_create(int n, const int *ns, const int *nt, const double *b
     b->beta.assign(beta, beta + n);
     b->seed.assign(seed, seed + n);
     size_t off = 0;
-    size_t max_chunks = 0;  // chunks of 64 sites (queue depth 2)
+    size_t max_chunks = 0;  // chunks of 32 sites (queue depth 1)
     std::vector<int> mprefix(n + 1, 0);
     for (int l = 0; l < n; ++l) {
         const Geom g = make_geom(ns[l], nt[l]);
-        max_chunks += ((size_t)g.vh + 63) / 64;
+        max_chunks += ((size_t)g.vh + 31) / 32;
         b->geom.push_back(g);
         b->link_offset.push_back(off);
         off += (8 * (size_t)g.vh + 15) & ~(size_t)15;  // keep each lattice 256-byte aligned
@@ -418,9 +405,9 @@ su2_status su2_batch_create(int n, const int *ns, const int *nt, const double *b
         int sms = 0;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         for (int sm = 0; sm < 2 && e == cudaSuccess; ++sm)
-            for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+            for (int i = 0; i < 4 && e == cudaSuccess; ++i)
                 for (int j = 0; j < 3 && e == cudaSuccess; ++j) {
-                    const int R = i == 0 ? 2 : (i == 1 ? 4 : 8);
+                    const int R = 1 << i;
                     int per_sm = 0;
                     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_for(sm, R, kBatchBlockSizes[j]),
                                                                       kBatchBlockSizes[j], 0);
@@ -556,7 +543,7 @@ su2_status su2_batch_info(su2_batch *b, int *n, uint32_t *sweep, int *queue_dept
 
 su2_status su2_batch_set_launch(su2_batch *b, int queue_depth, int threads, int grid)
 {
-    if (!b || (queue_depth != 2 && queue_depth != 4 && queue_depth != 8) ||
+    if (!b || (queue_depth != 1 && queue_depth != 2 && queue_depth != 4 && queue_depth != 8) ||
         (threads != 64 && threads != 128 && threads != 256))
         return SU2_E_INVAL;
     const int most = b->max_grid[b->sampler][r_index(queue_depth)][t_index(threads)];
@@ -590,7 +577,7 @@ su2_status su2_batch_set_sampler(su2_batch *b, int sampler)
     return su2_batch_set_launch(b, b->R, b->threads, b->grid);
 }
 
-// Times each candidate (queue depth 2/4/8 x block size 64/128/256 x full or
+// Times each candidate (queue depth 1/2/4/8 x block size 64/128/256 x full or
 // half of the co-resident grid) over `sweeps` sweeps of the batch, then
 // restores the links and the sweep counter, and keeps the fastest.
 su2_status su2_batch_autotune(su2_batch *b, int sweeps, int *queue_depth, int *grid)
@@ -608,8 +595,8 @@ su2_status su2_batch_autotune(su2_batch *b, int sweeps, int *queue_depth, int *g
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
         cudaMemcpyAsync(saved, b->links, bytes, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess)
         st = cuda_fail(cudaGetLastError(), "su2_batch_autotune");
-    const int depths[3] = {2, 4, 8};
-    for (int c = 0; c < 18 && st == SU2_OK; ++c) {
+    const int depths[4] = {1, 2, 4, 8};
+    for (int c = 0; c < 24 && st == SU2_OK; ++c) {
             const int i = c / 6, j = (c / 2) % 3, half = c % 2;
             const int R = depths[i], T = kBatchBlockSizes[j];
             const int most = b->max_grid[b->sampler][i][j];

@@ -163,7 +163,7 @@ __device__ void batch_phase(const BatchParams &bp, int parity, uint32_t sweep, C
         const int last = min((seg_end - lat_c0) * C, g.vh) - 1;
         const int rounds = (last - base0 + 32) >> 5;
         int retry_n = 0, done_n = 0;
-        double plaq = 0.0;
+        float plaq = 0.0f;  // per-thread partial in binary32; the block and grid sums are binary64
 
         // lanes that push nothing write to the last slot, which no live entry
         // reaches (at most 31 left over + 32 pushed), so the stores need no branch
@@ -196,7 +196,7 @@ __device__ void batch_phase(const BatchParams &bp, int parity, uint32_t sweep, C
                 const uint4 wd = philox_key(make_uint4(direction_pair((uint32_t)eo), sweep, sw_dir, 0u), k0, k1);
                 const float4 out = direction_update(deferred_a0(Q.d_val[q], Q.d_ibk[q]), Q.d_ut[q], wd, (uint32_t)eo);
                 links[link_index(g, MU, parity, eo)] = out;
-                if (MEAS) plaq += (double)qmul_re(out, Q.d_sp[q]);
+                if (MEAS) plaq = __fadd_rn(plaq, qmul_re(out, Q.d_sp[q]));
             }
             __syncwarp();
         };
@@ -303,7 +303,7 @@ __device__ void batch_phase(const BatchParams &bp, int parity, uint32_t sweep, C
         if (done_n > 0) direction_pass(0, done_n);
         if (MEAS) {
             // the segment's sum in the slot of its first chunk, zeros in the others
-            const double total = warp_sum(plaq);
+            const double total = warp_sum((double)plaq);
             for (int c = chunk + lane; c < seg_end; c += 32)
                 bp.chunk_partials[(MU - 1) * bp.total_chunks + c] = c == chunk ? total : 0.0;
         }
@@ -452,9 +452,19 @@ __global__ void __launch_bounds__(T, kBatchThreadsPerSm / T) batch_sweep_kernel(
 
 
 // Kernel entry points for the host code: the address of batch_sweep_kernel
-// for queue depth R (2, 4, 8) and block size T (64, 128, 256), from the
-// translation unit that instantiates that sampler's kernels.
-void *batch_kernel_creutz(int R, int T);
-void *batch_kernel_kp(int R, int T);
+// for sampler S, queue depth R and block size T (64, 128, 256), taken in the
+// translation unit that instantiates it.  The kernels are spread over four
+// units (batch_k_<sampler><depths>.cu) that compile in parallel.
+template <int R, int S>
+void *batch_kernel_t(int T)
+{
+    if (T == 64) return (void *)batch_sweep_kernel<R, 64, S>;
+    if (T == 256) return (void *)batch_sweep_kernel<R, 256, S>;
+    return (void *)batch_sweep_kernel<R, 128, S>;
+}
+void *batch_kernel_creutz_12(int R, int T);  // R = 1, 2
+void *batch_kernel_creutz_48(int R, int T);  // R = 4, 8
+void *batch_kernel_kp_12(int R, int T);
+void *batch_kernel_kp_48(int R, int T);
 
 }  // namespace su2

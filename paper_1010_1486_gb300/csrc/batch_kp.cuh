@@ -1,8 +1,11 @@
-// batch_kp.cu -- the batched sweep (batch.cu) with the Kennedy-Pendleton a0
-// sampler: the phase of every lattice runs the single-lattice Kennedy-Pendleton
+// batch_kp.cuh -- the batched phase with the Kennedy-Pendleton a0 sampler:
+// the phase of every lattice runs the single-lattice Kennedy-Pendleton
 // pipeline (kp.cu) on the warp's segments, with the lattice's own Philox key,
 // so each lattice's links equal those of su2_create + su2_set_sampler(KP) +
-// su2_heatbath_sweep with the same arguments.
+// su2_heatbath_sweep with the same arguments.  Included by the translation
+// units that instantiate the Kennedy-Pendleton batch kernels.
+#pragma once
+
 #include "batch_device.cuh"
 #include "kp_device.cuh"
 
@@ -53,7 +56,7 @@ __device__ void batch_phase_kp(const BatchParams &bp, int parity, uint32_t sweep
         const int last = min((seg_end - lat_c0) * C, g.vh) - 1;
         const int rounds = (last - base0 + 32) >> 5;
         int queued = 0;
-        double plaq = 0.0;
+        float plaq = 0.0f;  // per-thread partial in binary32; the block and grid sums are binary64
         auto gen = [&](uint4 c) { return philox_key(c, k0, k1); };
 
         // the queued links of lanes < n: further trials (or Creutz's method
@@ -71,7 +74,7 @@ __device__ void batch_phase_kp(const BatchParams &bp, int parity, uint32_t sweep
                     const int nt = heatbath_draw_gen(ut, beta, gen, (uint32_t)eo, sweep, (uint32_t)parity, MU, out);
                     if (nt > 0) {
                         links[link_index(g, MU, parity, eo)] = out;
-                        if (MEAS) plaq += (double)qmul_re(out, Q.r_sp[q]);
+                        if (MEAS) plaq = __fadd_rn(plaq, qmul_re(out, Q.r_sp[q]));
                         my_trials += (unsigned int)nt;
                     } else {
                         atomicAdd(&bp.flags[0], 1u);
@@ -88,7 +91,7 @@ __device__ void batch_phase_kp(const BatchParams &bp, int parity, uint32_t sweep
                     const float4 out = direction_update(
                         a0, ut, gen(make_uint4(direction_pair((uint32_t)eo), sweep, sw_dir, 0u)), (uint32_t)eo);
                     links[link_index(g, MU, parity, eo)] = out;
-                    if (MEAS) plaq += (double)qmul_re(out, Q.r_sp[q]);
+                    if (MEAS) plaq = __fadd_rn(plaq, qmul_re(out, Q.r_sp[q]));
                     my_trials += (unsigned int)(t + 1);
                 } else {
                     atomicAdd(&bp.flags[0], 1u);  // trial cap: the link keeps its old value
@@ -165,7 +168,7 @@ __device__ void batch_phase_kp(const BatchParams &bp, int parity, uint32_t sweep
                                         __shfl_sync(0xffffffffu, dblk.z, src), __shfl_sync(0xffffffffu, dblk.w, src));
             const float4 out = direction_update(a0, ut, wd, (uint32_t)cur);
             if (accepted) links[link_index(g, MU, parity, cur)] = out;
-            if (MEAS && accepted) plaq += (double)qmul_re(out, sp_cur);
+            if (MEAS && accepted) plaq = __fadd_rn(plaq, qmul_re(out, sp_cur));
             my_trials += accepted ? 1u : 0u;
             v_next = add_nu_terms(v_next, nl);
             if (MU == 3) sp_next = v_next;
@@ -180,29 +183,12 @@ __device__ void batch_phase_kp(const BatchParams &bp, int parity, uint32_t sweep
         }
         if (queued > 0) retry(0, queued);
         if (MEAS) {
-            const double total = warp_sum(plaq);
+            const double total = warp_sum((double)plaq);
             for (int c = chunk + lane; c < seg_end; c += 32)
                 bp.chunk_partials[(MU - 1) * bp.total_chunks + c] = c == chunk ? total : 0.0;
         }
         chunk = seg_end;
     }
-}
-
-namespace {
-template <int R>
-void *kp_for_t(int T)
-{
-    if (T == 64) return (void *)batch_sweep_kernel<R, 64, kBatchKP>;
-    if (T == 256) return (void *)batch_sweep_kernel<R, 256, kBatchKP>;
-    return (void *)batch_sweep_kernel<R, 128, kBatchKP>;
-}
-}  // namespace
-
-void *batch_kernel_kp(int R, int T)
-{
-    if (R == 2) return kp_for_t<2>(T);
-    if (R == 8) return kp_for_t<8>(T);
-    return kp_for_t<4>(T);
 }
 
 }  // namespace su2

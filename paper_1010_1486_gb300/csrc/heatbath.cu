@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
     const uint32_t sw_creutz = stream_word(kCreutz, rng_parity, MU);
     const uint32_t sw_dir = stream_word(kDirection, rng_parity, MU);
     unsigned int trials = 0;
-    double plaq = 0.0;
+    float plaq = 0.0f;  // per-thread partial in binary32; the block and grid sums are binary64
     int retry_n = 0, done_n = 0;  // warp-uniform queue lengths
 
     // Lanes that push nothing write to the last slot, which no live entry
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
             const uint4 wd = philox_rk(make_uint4(direction_pair(eo_g), sweep, sw_dir, 0u), p.rk);
             const float4 out = direction_update(deferred_a0(Q.d_val[q], Q.d_ibk[q]), Q.d_ut[q], wd, eo_g);
             p.links[link_index(p.g, MU, p.parity, eo)] = out;
-            if (MEAS) plaq += (double)qmul_re(out, Q.d_sp[q]);
+            if (MEAS) plaq = __fadd_rn(plaq, qmul_re(out, Q.d_sp[q]));
         }
         __syncwarp();
     };
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(kCrThreads, kCrMinBlocks) hb_phase_kernel(cons
                                  ((blockIdx.x * kCrWarps + (threadIdx.x >> 5)) & (kTrialSlots - 1))],
                   (unsigned long long)wsum);
     if (MEAS) {
-        const double total = block_sum(plaq);
+        const double total = block_sum((double)plaq);
         if (threadIdx.x == 0) p.plaq[blockIdx.x] = total;
     }
 }

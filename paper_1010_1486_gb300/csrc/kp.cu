@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
     const uint32_t sw_kp = stream_word(kKennedyPendleton, rng_parity, MU);
     const uint32_t sw_dir = stream_word(kDirection, rng_parity, MU);
     unsigned int trials = 0;
-    double plaq = 0.0;
+    float plaq = 0.0f;  // per-thread partial in binary32; the block and grid sums are binary64
     int queued = 0;  // warp-uniform length of the retry queue
 
     // Trials 1, 2, ... of the queue entry of this lane (lane < n), then the
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
                 const int n = heatbath_draw(ut, p.beta, p.rk, (uint32_t)eo + rng_eo, sweep, rng_parity, MU, out);
                 if (n > 0) {
                     p.links[link_index(p.g, MU, p.parity, eo)] = out;
-                    if (MEAS) plaq += (double)qmul_re(out, s_sp[MEAS ? wib : 0][q]);
+                    if (MEAS) plaq = __fadd_rn(plaq, qmul_re(out, s_sp[MEAS ? wib : 0][q]));
                     trials += (unsigned int)n;
                 } else {
                     atomicAdd(&p.flags[0], 1u);
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
                                      philox_rk(make_uint4(direction_pair((uint32_t)eo + rng_eo), sweep, sw_dir, 0u), p.rk),
                                      (uint32_t)eo + rng_eo);
                 p.links[link_index(p.g, MU, p.parity, eo)] = out;
-                if (MEAS) plaq += (double)qmul_re(out, s_sp[MEAS ? wib : 0][q]);
+                if (MEAS) plaq = __fadd_rn(plaq, qmul_re(out, s_sp[MEAS ? wib : 0][q]));
                 trials += (unsigned int)(t + 1);
             } else {
                 atomicAdd(&p.flags[0], 1u);  // trial cap: the link keeps its old value
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
                                     __shfl_sync(0xffffffffu, dblk.z, src), __shfl_sync(0xffffffffu, dblk.w, src));
         const float4 out = direction_update(a0, ut, wd, (uint32_t)cur + rng_eo);
         if (accepted) p.links[link_index(p.g, MU, p.parity, cur)] = out;
-        if (MEAS && accepted) plaq += (double)qmul_re(out, sp_cur);
+        if (MEAS && accepted) plaq = __fadd_rn(plaq, qmul_re(out, sp_cur));
         trials += accepted ? 1u : 0u;
         v_next = add_nu_terms(v_next, nl);
         if (MU == 3) sp_next = v_next;
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kKpThreads, kKpMinBlocks) kp_phase_kernel(cons
                                                                       (kTrialSlots - 1))],
                   (unsigned long long)wsum);
     if (MEAS) {
-        const double total = block_sum(plaq);
+        const double total = block_sum((double)plaq);
         if (threadIdx.x == 0) p.plaq[blockIdx.x] = total;
     }
 }

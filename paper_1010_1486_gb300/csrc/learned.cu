@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(kLearnThreads, kLearnMinBlocks) learned_phase_
     int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31);
     int cur = base + (threadIdx.x & 31);
     unsigned int acc = 0;
-    double plaq = 0.0;
+    float plaq = 0.0f;  // per-thread partial in binary32; the block and grid sums are binary64
     float4 v_cur = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     float4 sp_cur = v_cur;  // MEAS: staple terms of nu < MU (the first MU groups)
     if (base < p.g.vh) {
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kLearnThreads, kLearnMinBlocks) learned_phase_
         nl = load_nu_bases<MU, OtherDir<MU, 2>::value>(p.same, p.other, p.g, xn, en, en_p);
         const float4 out = direction_from_uniforms(r.a_new, r.d.ut, uniform01(w.z), uniform01(w.w));
         if (accept) p.links[li] = out;
-        if (MEAS && valid) plaq += (double)qmul_re(accept ? out : old, sp_cur);
+        if (MEAS && valid) plaq = __fadd_rn(plaq, qmul_re(accept ? out : old, sp_cur));
         acc += accept ? 1u : 0u;
         v_next = add_nu_terms(v_next, nl);
         if (MU == 3) sp_next = v_next;
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kLearnThreads, kLearnMinBlocks) learned_phase_
     }
     if (MEAS) {
         __syncthreads();
-        const double ptotal = block_sum(plaq);
+        const double ptotal = block_sum((double)plaq);
         if (threadIdx.x == 0) p.plaq[blockIdx.x] = ptotal;
     }
 }

@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(kReduceThreads, 4) plaquette_kernel(const floa
                                                                    double *__restrict__ dst,
                                                                    const uint32_t *__restrict__ idx)
 {
-    double acc = 0.0;
+    float acc = 0.0f;  // per-thread partial in binary32; the block and grid sums are binary64
     const int64_t vol = 2 * (int64_t)g.vh;
     // sites in lexicographic order (both parities interleaved), so the
     // neighbour links a block reads were just read by its neighbours (L2)
@@ -29,9 +29,9 @@ __global__ void __launch_bounds__(kReduceThreads, 4) plaquette_kernel(const floa
         const int eo = (int)(s >> 1);
         const int parity = (int)(s & 1) ^ (eo_to_coord(g, eo, 0).lex != 2 * eo);
         const Coord x = eo_to_coord(g, eo, parity);
-        acc += (double)site_plaquette(L, g, x, eo, parity);
+        acc = __fadd_rn(acc, site_plaquette(L, g, x, eo, parity));
     }
-    const double total = block_sum(acc);
+    const double total = block_sum((double)acc);
     finish_reduction(total, partials, ticket, idx ? dst + *idx : dst, 1.0 / (6.0 * (double)vol));
 }
 
@@ -42,10 +42,10 @@ __global__ void __launch_bounds__(kReduceThreads) polyakov_kernel(const float4 *
                                                                   double *__restrict__ dst,
                                                                   const uint32_t *__restrict__ idx)
 {
-    double acc = 0.0;
+    float acc = 0.0f;  // per-thread partial in binary32; the block and grid sums are binary64
     for (int xs = blockIdx.x * blockDim.x + threadIdx.x; xs < g.vs; xs += gridDim.x * blockDim.x)
-        acc += (double)site_polyakov(L, g, xs);
-    const double total = block_sum(acc);
+        acc = __fadd_rn(acc, site_polyakov(L, g, xs));
+    const double total = block_sum((double)acc);
     finish_reduction(total, partials, ticket, idx ? dst + *idx : dst, 1.0 / (double)g.vs);
 }
 

@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(kOrThreads, kOrMinBlocks) or_phase_kernel(cons
     const int last = p.g.vh - 1;
     int base = blockIdx.x * kOrThreads + (threadIdx.x & ~31);
     int cur = base + (threadIdx.x & 31);
-    double plaq = 0.0;
+    float plaq = 0.0f;  // per-thread partial in binary32; the block and grid sums are binary64
     float4 v_cur = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     float4 sp_cur = v_cur;  // MEAS: staple terms of nu < MU (the first MU groups)
     if (base < p.g.vh) {
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kOrThreads, kOrMinBlocks) or_phase_kernel(cons
         nl = load_nu_bases<MU, OtherDir<MU, 2>::value>(p.same, p.other, p.g, xn, en, en_p);
         const float4 out = qmul(t, ut);
         if (valid) p.links[li] = out;
-        if (MEAS && valid) plaq += (double)qmul_re(out, sp_cur);
+        if (MEAS && valid) plaq = __fadd_rn(plaq, qmul_re(out, sp_cur));
         v_next = add_nu_terms(v_next, nl);
         if (MU == 3) sp_next = v_next;
         base += stride;
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(kOrThreads, kOrMinBlocks) or_phase_kernel(cons
         sp_cur = sp_next;
     }
     if (MEAS) {
-        const double total = block_sum(plaq);
+        const double total = block_sum((double)plaq);
         if (threadIdx.x == 0) p.plaq[blockIdx.x] = total;
     }
 }

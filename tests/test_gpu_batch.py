@@ -72,7 +72,7 @@ def test_batch_matches_oracle_lattice_by_lattice(use_stream):
 def test_every_queue_depth_gives_the_same_chain():
     cfg = SMALL
     results = []
-    for depth in (2, 4, 8):
+    for depth in (1, 2, 4, 8):
         b = su2.su2_batch_create(cfg["ns"], cfg["nt"], cfg["beta"], cfg["seed"], cfg["start"])
         try:
             su2.su2_batch_set_config(b, depth, 0 if depth != 4 else 37)
@@ -92,7 +92,7 @@ def test_autotune_keeps_the_chain():
     try:
         su2.su2_batch_sweep(b, 1)
         depth, grid = su2.su2_batch_autotune(b, 2)
-        assert depth in (2, 4, 8) and grid > 0
+        assert depth in (1, 2, 4, 8) and grid > 0
         assert su2.su2_batch_info(b)["sweep"] == 1
         su2.su2_batch_sweep(b, 2)
         ref = oracle_chains(cfg, 3)
@@ -153,7 +153,7 @@ def oracle_chains_kp(cfg, sweeps):
     return out
 
 
-@pytest.mark.parametrize("depth,block", [(4, 128), (2, 256), (8, 64)])
+@pytest.mark.parametrize("depth,block", [(4, 128), (2, 256), (8, 64), (1, 128)])
 def test_kennedy_pendleton_batch_matches_the_oracle(depth, block):
     """The batch with the Kennedy-Pendleton sampler: every lattice bitwise the
     oracle's KP chain (beta k < 2 links by Creutz's method included: beta 0
