@@ -14,7 +14,9 @@ device-timed with CUDA events around K steps with the links resident in HBM
 metric through the C ABI with host buffers (configuration in from pinned host
 memory, sweep, observables, configuration out), copies inside the timed
 region.  `roofline` = algorithmic bytes of the heat-bath phase kernel over its
-CUDA-event duration (events recorded by the library on the launching stream).
+duration: CUDA events on the launching stream around K unmeasured sweeps
+replayed back to back, over their 8 K phase launches (the per-launch
+event-bracketed duration is reported beside it).
 `--impl reference` times the CPU oracle on the same workload.
 """
 from __future__ import annotations
@@ -170,6 +172,77 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(load), "power_w_max": max(r["power"] for r in rows)}
 
 
+class NvmlClockSampler:
+    """SM clock, power and clock-event reasons read through NVML (read only:
+    nvmlDeviceGetClockInfo, GetMaxClockInfo, GetPowerUsage and the current
+    clock-event reasons) every 2 ms on a thread while the timed work runs, so
+    that every sample falls inside the timed region."""
+
+    SM = 1  # NVML_CLOCK_SM
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40}
+
+    def __init__(self, uuid: str | None, index: int):
+        import ctypes
+        import threading
+
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit_v2 failed")
+        self.h = ctypes.c_void_p()
+        rc = self.lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(self.h)) if uuid else 1
+        if rc != 0:
+            rc = self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.h))
+        if rc != 0:
+            self.lib.nvmlShutdown()
+            raise OSError("no NVML handle for the device")
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        self.rows = []
+        self.done = threading.Event()
+        self.thread = threading.Thread(target=self._run, daemon=True)
+
+    def _sample(self):
+        c = self.ct
+        mhz, mx, mw, rs = c.c_uint(), c.c_uint(), c.c_uint(), c.c_ulonglong()
+        if self.lib.nvmlDeviceGetClockInfo(self.h, self.SM, c.byref(mhz)) != 0:
+            return
+        self.lib.nvmlDeviceGetMaxClockInfo(self.h, self.SM, c.byref(mx))
+        self.lib.nvmlDeviceGetPowerUsage(self.h, c.byref(mw))
+        self.reasons_fn(self.h, c.byref(rs))
+        self.rows.append({"sm": float(mhz.value), "max": float(mx.value), "power": mw.value / 1000.0,
+                          "reasons": [r for r, b in self.BITS.items() if rs.value & b]})
+
+    def _run(self):
+        while not self.done.is_set():
+            self._sample()
+            time.sleep(0.002)
+
+    def start(self):
+        self.thread.start()
+
+    def stop(self):
+        self.done.set()
+        self.thread.join()
+        self.lib.nvmlShutdown()
+        rows = self.rows
+        if not rows:
+            return None
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["max"] for r in rows),
+                "reasons": sorted({x for r in rows for x in r["reasons"]}), "samples": len(rows),
+                "power_w_max": max(r["power"] for r in rows), "source": "NVML, every 2 ms inside the timed region"}
+
+
+def clock_sampler(torch, local_rank: int, gpu_index: int, rank: int):
+    """The NVML sampler for the device, else nvidia-smi in a subprocess."""
+    try:
+        uuid = getattr(torch.cuda.get_device_properties(local_rank), "uuid", None)
+        uuid = f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else (str(uuid) if uuid else None)
+        return NvmlClockSampler(uuid, gpu_index)
+    except (OSError, AttributeError):
+        return ClockSampler(gpu_index, os.path.join(tempfile.gettempdir(), f"su2_clocks_rank{rank}.csv"))
+
+
 # ------------------------------------------------------- measured peaks etc
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -216,8 +289,7 @@ def run_ours(args, dist):
     lat = su2.su2_create(NS, NT, BETA, seed, su2.SU2_HOT, stream=stream)
     try:
         su2.su2_set_sampler(lat, sampler)
-        su2.su2_generate(lat, args.warmup, 1, 0)
-        su2.su2_set_timing(lat, True)
+        su2.su2_generate(lat, args.warmup, 1, 0)  # also captures the sweep's CUDA graph
         gpu_index = dist.local_rank
         vis = os.environ.get("CUDA_VISIBLE_DEVICES")
         if vis:
@@ -225,24 +297,31 @@ def run_ours(args, dist):
                 gpu_index = int(vis.split(",")[dist.local_rank])
             except ValueError:
                 pass
-        clocks = ClockSampler(gpu_index, os.path.join(tempfile.gettempdir(), f"su2_clocks_rank{dist.rank}.csv"))
+        clocks = clock_sampler(torch, dist.local_rank, gpu_index, dist.rank)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         dist.barrier()
         torch.cuda.synchronize()
         clocks.start()
+        # the timed steps: one counter reset, then each sweep with its
+        # measurement replayed from the lattice's CUDA graph (11 kernels: 8
+        # phases, plaquette sum, Polyakov loop, counter advance)
         ev0.record(stream)
         plaq, poly, st = su2.su2_generate(lat, args.steps, 1, 0)
         ev1.record(stream)
         ev1.synchronize()
         torch.cuda.synchronize()
-        clk = clocks.stop()
         dist.barrier()
         ms = ev0.elapsed_time(ev1)
-        su2.su2_set_timing(lat, False)
+        # the phase kernel's duration, for the roofline: the same number of
+        # sweeps without the measurement, replayed back to back from the
+        # graph (8 phase launches + the counter advance per sweep), CUDA
+        # events around them on the lattice's stream, over 8 launches a sweep
+        phase_s, phase_s_events = phase_kernel_time(su2, lat, torch, stream, args.steps)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
         ms_max = dist.reduce(ms, "max")
         updates = dist.reduce(float(st["link_updates"]), "sum")
         value = updates / (ms_max * 1e-3)
-        phase_s = st["kernel_ms"] / st["kernel_launches"] * 1e-3
         peak, peak_kind = measured_peaks()
         achieved = BYTES_PER_UPDATE * (VOL // 2) / phase_s / 1e9
         trials_per_update = sum(st["trials"]) / st["link_updates"]
@@ -276,9 +355,10 @@ def run_ours(args, dist):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": ncu_traffic_per_launch(args.sampler), "kernel": SAMPLERS[args.sampler]["kernel"],
                      "peak_source": f"{peak_kind} hbm_gbs", "bytes_per_launch": BYTES_PER_UPDATE * (VOL // 2),
-                     "avg_launch_us": phase_s * 1e6},
+                     "avg_launch_us": phase_s * 1e6, "timing": PHASE_TIMING,
+                     "event_bracketed_launch_us": phase_s_events * 1e6},
         "e2e": e2e,
-        "gpu_launches": st["kernel_launches"] + 2 * args.steps,
+        "gpu_launches": 11 * args.steps + 1,  # + the counter reset before the replays
         "clocks": clk,
         "trials_per_update": trials_per_update,
         "plaquette_last": float(plaq[-1]), "polyakov_last": float(poly[-1]),
@@ -289,6 +369,30 @@ def run_ours(args, dist):
     if forms and "value_tau_adjusted" in forms:
         result["value_tau_adjusted"] = forms["value_tau_adjusted"]
     return result
+
+
+PHASE_TIMING = ("back-to-back launches: sweeps without the measurement replayed from the graph, CUDA events around "
+                "them on the lattice's stream, divided by the 8 phase launches a sweep (the counter-advance kernel "
+                "and the gaps count against the phase)")
+
+
+def phase_kernel_time(su2, lat, torch, stream, steps):
+    """Seconds per phase launch, (1) back to back: `steps` unmeasured sweeps
+    replayed from the lattice's graph, events around them; (2) with CUDA
+    events around every launch (eager launches; includes each launch's
+    latency)."""
+    su2.su2_generate(lat, 2, 0, 0)  # the unmeasured sweep's graph, captured untimed
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    su2.su2_generate(lat, steps, 0, 0)
+    e1.record(stream)
+    e1.synchronize()
+    back_to_back = e0.elapsed_time(e1) * 1e-3 / (8 * steps)
+    su2.su2_set_timing(lat, True)
+    _, _, st = su2.su2_generate(lat, steps, 0, 0)
+    su2.su2_set_timing(lat, False)
+    return back_to_back, st["kernel_ms"] / st["kernel_launches"] * 1e-3
 
 
 def timed(stream, torch, dist, fn):
@@ -341,33 +445,43 @@ def compare_forms(args, dist, lat, su2, torch, stream, tau_int):
     su2.su2_set_proposal(lat, w, s_lo, s_hi, 256)
     peak, _ = measured_peaks()
 
-    def roof(kernel, phase_s, nbytes):
+    def roof(kernel, phase_s, nbytes, timing, events_s=None):
         a = nbytes * (VOL // 2) / phase_s / 1e9
-        return {"bound": "hbm", "kernel": kernel, "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak,
-                "avg_launch_us": phase_s * 1e6, "bytes_per_launch": nbytes * (VOL // 2)}
+        r = {"bound": "hbm", "kernel": kernel, "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak,
+             "avg_launch_us": phase_s * 1e6, "bytes_per_launch": nbytes * (VOL // 2), "timing": timing}
+        if events_s is not None:
+            r["event_bracketed_launch_us"] = events_s * 1e6
+        return r
 
-    su2.su2_set_timing(lat, True)
     out = {"lattice": f"thermalised 48^4, beta = 6.0 (after {args.therm} compound sweeps of Kennedy-Pendleton + "
                       f"{N_OR} over-relaxation)"}
+    sweep_s = {}
     for key, sampler, kernel in (("kennedy_pendleton", KP, "kp_phase_kernel"), ("creutz", CR, "hb_phase_kernel")):
         su2.su2_set_sampler(lat, sampler)
         su2.su2_generate(lat, 2, 1, 0)
         ms, (_, _, st) = timed(stream, torch, dist, lambda: su2.su2_generate(lat, args.steps, 1, 0))
-        phase_s = st["kernel_ms"] / st["kernel_launches"] * 1e-3
+        phase_s, events_s = phase_kernel_time(su2, lat, torch, stream, args.steps)
+        sweep_s[key] = 8 * phase_s
         out[key] = {"value": dist.reduce(float(st["link_updates"]), "sum") / (ms * 1e-3), "unit": UNIT,
                     "ms_per_step": ms / args.steps, "trials_per_update": sum(st["trials"]) / st["link_updates"],
-                    "roofline": roof(kernel, phase_s, BYTES_PER_UPDATE)}
+                    "roofline": roof(kernel, phase_s, BYTES_PER_UPDATE, PHASE_TIMING, events_s)}
     su2.su2_set_sampler(lat, KP)  # the learned sweeps' fallback sampler
     su2.su2_learned_generate(lat, 2, 1, 0.7)
     ms_l, (_, _, st_l) = timed(stream, torch, dist, lambda: su2.su2_learned_generate(lat, args.steps, 1, 0.7))
-    learned_phase_s = st_l["kernel_ms"] / max(1, st_l["kernel_launches"]) * 1e-3
+    # the learned sweep launches the gated plain phases too: its phase kernel
+    # is timed with events around each launch
+    su2.su2_set_timing(lat, True)
+    _, _, st_lt = su2.su2_learned_generate(lat, args.steps, 1, 0.7)
+    su2.su2_set_timing(lat, False)
+    learned_phase_s = st_lt["kernel_ms"] / max(1, st_lt["kernel_launches"]) * 1e-3
     proposals = st_l["learned_sweeps"] * 4 * VOL
     out["learned"] = {
         "value": dist.reduce(float(st_l["link_updates"]), "sum") / (ms_l * 1e-3), "unit": UNIT,
         "ms_per_step": ms_l / args.steps, "acceptance": sum(st_l["accepted"]) / max(1, proposals),
         "learned_sweeps": st_l["learned_sweeps"], "fallback_sweeps": st_l["plain_sweeps"],
         "fallback_sampler": "Kennedy-Pendleton",
-        "roofline": roof("learned_phase_kernel", learned_phase_s, BYTES_PER_LEARNED_UPDATE),
+        "roofline": roof("learned_phase_kernel", learned_phase_s, BYTES_PER_LEARNED_UPDATE,
+                         "CUDA events around every learned phase launch (each launch's latency included)"),
         "gpu_launches": st_l["kernel_launches"] * 2 + args.steps * 3,
         "training": {"pairs": args.learned_pairs, "steps": 2 * args.train_steps, "batch": TRAIN_BATCH,
                      "schedule": f"{args.train_steps} Adam steps at 3e-3, {args.train_steps} at 3e-4",
@@ -377,15 +491,25 @@ def compare_forms(args, dist, lat, su2, torch, stream, tau_int):
     su2.su2_generate(lat, 2, 1, 0)
     n_cmp = max(1, args.steps // (N_OR + 1))
     ms_o, (_, _, st_o) = timed(stream, torch, dist, lambda: su2.su2_generate(lat, n_cmp, 1, 0))
-    su2.su2_set_overrelax(lat, 0)
+    # over-relaxation phase: unmeasured compound sweeps back to back, less the
+    # Kennedy-Pendleton sweep timed the same way, over 8 N_OR launches
+    su2.su2_generate(lat, 2, 0, 0)
+    ms_c, _ = timed(stream, torch, dist, lambda: su2.su2_generate(lat, n_cmp, 0, 0))
+    su2.su2_set_timing(lat, True)
+    _, _, st_ot = su2.su2_generate(lat, n_cmp, 0, 0)
     su2.su2_set_timing(lat, False)
-    or_phase_s = st_o["overrelax_ms"] / (8 * st_o["overrelax_sweeps"]) * 1e-3
+    su2.su2_set_overrelax(lat, 0)
+    or_phase_s = (ms_c * 1e-3 / n_cmp - sweep_s["kennedy_pendleton"]) / (8 * N_OR)
+    or_events_s = st_ot["overrelax_ms"] / (8 * st_ot["overrelax_sweeps"]) * 1e-3
     compound_per_s = dist.reduce(float(n_cmp), "sum") / (ms_o * 1e-3)
     out["kp_overrelax"] = {
         "compound_sweep": f"1 Kennedy-Pendleton heat-bath sweep + {N_OR} over-relaxation sweeps",
         "compound_sweeps_per_s": compound_per_s, "ms_per_compound_sweep": ms_o / n_cmp,
         "value": compound_per_s * 4 * VOL * (N_OR + 1), "unit": UNIT + " (heat bath + over-relaxation)",
-        "roofline": roof("or_phase_kernel", or_phase_s, BYTES_PER_OR_UPDATE)}
+        "roofline": roof("or_phase_kernel", or_phase_s, BYTES_PER_OR_UPDATE,
+                         "back-to-back launches: unmeasured compound sweeps replayed from the graph less the "
+                         "Kennedy-Pendleton sweep timed the same way, over the 8 N_OR over-relaxation launches",
+                         or_events_s)}
     if args.tau_sweeps <= 0:
         return out
 
@@ -585,7 +709,10 @@ def run_e2e(args, dist, lat, su2, torch):
     lattice handle and stream, taken round robin: the copy engines move one configuration while
     another is swept.  Each handle's output is its next input, so every
     handle runs its own chain (seeds differ) through host memory.  All copies
-    of all steps are inside the timed region."""
+    of all steps are inside the timed region.  Three timed repetitions of
+    e2e_steps steps each; the value is their median (the host link of the
+    virtual machines this runs on varies from run to run), all three are
+    reported."""
     start = su2.su2_get_links(lat, NS, NT)
     hs, bufs, meas = [], [], []
     try:
@@ -611,14 +738,17 @@ def run_e2e(args, dist, lat, su2, torch):
             step(i)
         for h in hs:
             su2.su2_sync(h)
-        dist.barrier()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for k in range(args.e2e_steps):
-            step(k % args.e2e_in_flight)
-        for h in hs:
-            su2.su2_sync(h)
-        e2e_s = dist.reduce(time.perf_counter() - t0, "max")
+        reps = []
+        for _ in range(3):
+            dist.barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for k in range(args.e2e_steps):
+                step(k % args.e2e_in_flight)
+            for h in hs:
+                su2.su2_sync(h)
+            reps.append(dist.reduce(time.perf_counter() - t0, "max"))
+        e2e_s = statistics.median(reps)
     finally:
         for h in hs:
             su2.su2_destroy(h)
@@ -626,6 +756,7 @@ def run_e2e(args, dist, lat, su2, torch):
     return {"value": e2e_updates / e2e_s, "unit": UNIT, "h2d_bytes_per_step": LINKS * 16,
             "d2h_bytes_per_step": LINKS * 16 + 16, "steps": args.e2e_steps,
             "ms_per_step": e2e_s * 1e3 / args.e2e_steps,
+            "repetitions": [e2e_updates / r for r in reps], "statistic": "median of 3 timed repetitions",
             "pipeline": f"{args.e2e_in_flight} configurations in flight (own lattice handle and stream each, round "
                         "robin); host<->device copies on the copy engines overlap the other configurations' "
                         "sweeps"}

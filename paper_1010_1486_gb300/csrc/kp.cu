@@ -18,9 +18,9 @@
 
 namespace su2 {
 
-constexpr int kKpThreads = 256;
+constexpr int kKpThreads = 128;
 #ifndef SU2_KP_MIN_BLOCKS
-#define SU2_KP_MIN_BLOCKS 3
+#define SU2_KP_MIN_BLOCKS 6
 #endif
 constexpr int kKpMinBlocks = SU2_KP_MIN_BLOCKS;  // blocks per SM the register budget is set for
 

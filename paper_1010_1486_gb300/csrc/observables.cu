@@ -35,18 +35,68 @@ __global__ void __launch_bounds__(kReduceThreads, 4) plaquette_kernel(const floa
     finish_reduction(total, partials, ticket, idx ? dst + *idx : dst, 1.0 / (6.0 * (double)vol));
 }
 
-// (1/2) Tr of U_3(x,0) U_3(x,1) ... U_3(x,Nt-1), multiplied left to right.
-__global__ void __launch_bounds__(kReduceThreads) polyakov_kernel(const float4 *__restrict__ L, Geom g,
-                                                                  double *__restrict__ partials,
-                                                                  unsigned int *__restrict__ ticket,
-                                                                  double *__restrict__ dst,
-                                                                  const uint32_t *__restrict__ idx)
+// (1/2) Tr of U_3(x,0) U_3(x,1) ... U_3(x,Nt-1).  A block of kPolySeg warps
+// takes 32 consecutive spatial sites at a time; warp s multiplies, left to
+// right, the links of the s-th quarter of the time extent for each of the 32
+// sites (each load instruction reads one time slice: 32 consecutive sites,
+// two runs of 256 B), with all of a quarter's loads (up to kPolyBatch) in
+// flight at once.  Warp 0 then combines the quarters through shared memory
+// as (P0 P1)(P2 P3).  Short quarters are padded with the identity, which
+// multiplies exactly.
+constexpr int kPolySeg = 4;                  // warps per block: quarters of the time extent
+constexpr int kPolyThreads = 32 * kPolySeg;  // block size
+constexpr int kPolyBatch = 12;               // loads in flight per lane (Nt = 48: one batch)
+
+__global__ void __launch_bounds__(kPolyThreads) polyakov_kernel(const float4 *__restrict__ L, Geom g,
+                                                               double *__restrict__ partials,
+                                                               unsigned int *__restrict__ ticket,
+                                                               double *__restrict__ dst,
+                                                               const uint32_t *__restrict__ idx)
 {
+    __shared__ float4 s_part[kPolySeg][32];
     float acc = 0.0f;  // per-thread partial in binary32; the block and grid sums are binary64
-    for (int xs = blockIdx.x * blockDim.x + threadIdx.x; xs < g.vs; xs += gridDim.x * blockDim.x)
-        acc = __fadd_rn(acc, site_polyakov(L, g, xs));
-    const double total = block_sum((double)acc);
-    finish_reduction(total, partials, ticket, idx ? dst + *idx : dst, 1.0 / (double)g.vs);
+    const int lane = threadIdx.x & 31;
+    const int seg = threadIdx.x >> 5;
+    const int len = (g.nt + kPolySeg - 1) / kPolySeg;
+    const int t_begin = min(seg * len, g.nt);
+    const int t_end = min(t_begin + len, g.nt);
+    const float4 one = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+    // block-uniform loop over groups of 32 sites
+    for (int base = blockIdx.x * 32; base < g.vs; base += gridDim.x * 32) {
+        const int xs = min(base + lane, g.vs - 1);
+        const int rest = xs / g.ns;
+        const int x = xs - rest * g.ns;
+        const int y = rest % g.ns;
+        const int z = rest / g.ns;
+        const int p0 = (x + y + z) & 1;
+        // a quarter of up to kPolyBatch links (Nt <= 4 kPolyBatch) is one
+        // batch of unconditional loads (the index clamped to the quarter),
+        // all issued before the first product; longer quarters loop
+        auto batch = [&](float4 p, int t) {
+            float4 q[kPolyBatch];
+#pragma unroll
+            for (int j = 0; j < kPolyBatch; ++j) {
+                const int tj = min(t + j, t_end - 1);
+                const int64_t lex = (int64_t)tj * g.vs + xs;
+                q[j] = __ldg(L + link_index(g, 3, (p0 + tj) & 1, (int)(lex >> 1)));
+            }
+#pragma unroll
+            for (int j = 0; j < kPolyBatch; ++j) p = qmul(p, t + j < t_end ? q[j] : one);
+            return p;
+        };
+        float4 p = t_begin < t_end ? batch(one, t_begin) : one;
+        for (int t = t_begin + kPolyBatch; t < t_end; t += kPolyBatch) p = batch(p, t);
+        s_part[seg][lane] = p;
+        __syncthreads();
+        if (seg == 0) {
+            const float4 p01 = qmul(s_part[0][lane], s_part[1][lane]);
+            const float4 p23 = qmul(s_part[2][lane], s_part[3][lane]);
+            if (base + lane < g.vs) acc = __fadd_rn(acc, qmul(p01, p23).x);
+        }
+        __syncthreads();
+    }
+    const double total_sum = block_sum((double)acc);
+    finish_reduction(total_sum, partials, ticket, idx ? dst + *idx : dst, 1.0 / (double)g.vs);
 }
 
 su2_status launch_plaquette(su2_lattice *lat, double *dst)
@@ -64,13 +114,26 @@ su2_status launch_plaquette(su2_lattice *lat, double *dst)
     return SU2_OK;
 }
 
-// Ordered sum of the fused-plaquette slot region (one block).
-__global__ void __launch_bounds__(kReduceThreads) fused_plaquette_kernel(const double *__restrict__ part, int n,
-                                                                        double scale, double *__restrict__ dst,
-                                                                        const uint32_t *__restrict__ idx)
+// Sum of the fused-plaquette slot region (one block of kFusedThreads; each
+// thread issues its loads together, then adds them in index order).
+constexpr int kFusedThreads = 1024;
+constexpr int kFusedPer = (kFusedRegion + kFusedThreads - 1) / kFusedThreads;
+
+__global__ void __launch_bounds__(kFusedThreads) fused_plaquette_kernel(const double *__restrict__ part, int n,
+                                                                       double scale, double *__restrict__ dst,
+                                                                       const uint32_t *__restrict__ idx)
 {
     double v = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) v += part[i];
+    for (int i0 = 0; i0 < n; i0 += kFusedPer * kFusedThreads) {
+        double x[kFusedPer];
+#pragma unroll
+        for (int j = 0; j < kFusedPer; ++j) {
+            const int i = i0 + j * kFusedThreads + (int)threadIdx.x;
+            x[j] = i < n ? part[i] : 0.0;
+        }
+#pragma unroll
+        for (int j = 0; j < kFusedPer; ++j) v += x[j];
+    }
     v = block_sum(v);
     if (threadIdx.x == 0) *(idx ? dst + *idx : dst) = v * scale;
 }
@@ -89,7 +152,7 @@ su2_status fused_begin(su2_lattice *lat)
 su2_status fused_finish(su2_lattice *lat, double *dst)
 {
     lat->fused_part = nullptr;
-    fused_plaquette_kernel<<<1, kReduceThreads, 0, lat->stream>>>(lat->scratch.partials, kFusedRegion,
+    fused_plaquette_kernel<<<1, kFusedThreads, 0, lat->stream>>>(lat->scratch.partials, kFusedRegion,
                                                                  1.0 / (6.0 * (double)lat->vol), dst,
                                                                  lat->capturing ? lat->d_ctr + 1 : nullptr);
     SU2_CUDA(cudaGetLastError());
@@ -99,8 +162,8 @@ su2_status fused_finish(su2_lattice *lat, double *dst)
 su2_status launch_polyakov(su2_lattice *lat, double *dst)
 {
     const Geom g = geom_of(lat);
-    const int grid = grid_for(g.vs, kReduceThreads, 152 * 8);
-    polyakov_kernel<<<grid, kReduceThreads, 0, lat->stream>>>(lat->links, g, lat->scratch.partials,
+    const int grid = grid_for(g.vs, 32, std::min(lat->scratch.partials_cap, 152 * 8));
+    polyakov_kernel<<<grid, kPolyThreads, 0, lat->stream>>>(lat->links, g, lat->scratch.partials,
                                                               lat->scratch.ticket + 1, dst,
                                                               lat->capturing ? lat->d_ctr + 1 : nullptr);
     SU2_CUDA(cudaGetLastError());

@@ -68,3 +68,48 @@ def test_reference_arm_other_ranks_exit_without_work():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference"], capture_output=True,
                        text=True, timeout=120, env=env, cwd=ROOT)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_nvml_clock_sampler_summary_with_a_fake_library():
+    """The in-window clock record: median SM clock, the maximum, and the
+    clock-event reasons decoded from NVML's bit mask, from a fake NVML."""
+    import threading
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class Fake:
+        def __init__(self):
+            self.n = 0
+
+        def nvmlDeviceGetClockInfo(self, h, kind, ref):
+            self.n += 1
+            ref._obj.value = 2070 if self.n % 3 else 1980
+            return 0
+
+        def nvmlDeviceGetMaxClockInfo(self, h, kind, ref):
+            ref._obj.value = 2070
+            return 0
+
+        def nvmlDeviceGetPowerUsage(self, h, ref):
+            ref._obj.value = 950000
+            return 0
+
+        def nvmlShutdown(self):
+            return 0
+
+    fake = Fake()
+    s = object.__new__(bench.NvmlClockSampler)
+    import ctypes
+
+    s.ct, s.lib, s.h = ctypes, fake, None
+    s.reasons_fn = lambda h, ref: setattr(ref._obj, "value", 0x4 | 0x1) or 0
+    s.rows, s.done = [], threading.Event()
+    for _ in range(6):
+        s._sample()
+    s.thread = threading.Thread(target=lambda: None)
+    s.thread.start()
+    out = s.stop()
+    assert out["samples"] == 6 and out["sm_max_mhz"] == 2070.0
+    assert out["sm_mhz"] == 2070.0 and out["reasons"] == ["sw_power_cap"]
+    assert abs(out["power_w_max"] - 950.0) < 1e-9
