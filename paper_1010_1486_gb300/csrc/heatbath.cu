@@ -443,8 +443,8 @@ static su2_status sweep_and_measure(su2_lattice *lat, bool measure, bool reunit,
     }
     if (reunit && (st = launch_reunitarize(lat)) != SU2_OK) return st;
     if (measure) {
-        st = fused ? fused_finish(lat, plaq_dst) : launch_plaquette(lat, plaq_dst);
-        if (st != SU2_OK) return st;
+        if (fused) return fused_finish_with_polyakov(lat, plaq_dst, poly_dst);
+        if ((st = launch_plaquette(lat, plaq_dst)) != SU2_OK) return st;
         if ((st = launch_polyakov(lat, poly_dst)) != SU2_OK) return st;
     }
     return SU2_OK;

@@ -380,8 +380,9 @@ su2_status su2_learned_generate(su2_lattice *lat, int nsweeps, int measure_every
         SU2_CUDA(cudaGetLastError());
         lat->sweep += 1;
         if (measure) {
-            if ((st = fused_finish(lat, lat->scratch.history + m)) != SU2_OK) return st;
-            if ((st = launch_polyakov(lat, lat->scratch.history + lat->scratch.history_cap + m)) != SU2_OK) return st;
+            if ((st = fused_finish_with_polyakov(lat, lat->scratch.history + m,
+                                                 lat->scratch.history + lat->scratch.history_cap + m)) != SU2_OK)
+                return st;
             ++m;
         }
     }

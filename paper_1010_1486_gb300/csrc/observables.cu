@@ -47,11 +47,19 @@ constexpr int kPolySeg = 4;                  // warps per block: quarters of the
 constexpr int kPolyThreads = 32 * kPolySeg;  // block size
 constexpr int kPolyBatch = 12;               // loads in flight per lane (Nt = 48: one batch)
 
+// PLAQ: the kernel of a measuring sweep also sums the fused-plaquette slot
+// region `fused` (kFusedRegion doubles): block b adds its contiguous share in
+// index order, and the last block adds the block sums in block order into
+// plaq_dst (scaled by plaq_scale), beside the Polyakov loop; `partials` then
+// holds 2 gridDim.x doubles and must not overlap the slot region.
+template <bool PLAQ>
 __global__ void __launch_bounds__(kPolyThreads) polyakov_kernel(const float4 *__restrict__ L, Geom g,
                                                                double *__restrict__ partials,
                                                                unsigned int *__restrict__ ticket,
                                                                double *__restrict__ dst,
-                                                               const uint32_t *__restrict__ idx)
+                                                               const uint32_t *__restrict__ idx,
+                                                               const double *__restrict__ fused,
+                                                               double *__restrict__ plaq_dst, double plaq_scale)
 {
     __shared__ float4 s_part[kPolySeg][32];
     float acc = 0.0f;  // per-thread partial in binary32; the block and grid sums are binary64
@@ -96,7 +104,39 @@ __global__ void __launch_bounds__(kPolyThreads) polyakov_kernel(const float4 *__
         __syncthreads();
     }
     const double total_sum = block_sum((double)acc);
-    finish_reduction(total_sum, partials, ticket, idx ? dst + *idx : dst, 1.0 / (double)g.vs);
+    if (!PLAQ) {
+        finish_reduction(total_sum, partials, ticket, idx ? dst + *idx : dst, 1.0 / (double)g.vs);
+        return;
+    }
+    const int per = (kFusedRegion + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int f0 = min((int)blockIdx.x * per, kFusedRegion);
+    const int f1 = min(f0 + per, kFusedRegion);
+    double fv = 0.0;
+    for (int i = f0 + (int)threadIdx.x; i < f1; i += kPolyThreads) fv += fused[i];
+    const double fused_sum = block_sum(fv);
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = total_sum;
+        partials[gridDim.x + blockIdx.x] = fused_sum;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double vp = 0.0, vq = 0.0;
+    for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+        vp += ((volatile double *)partials)[b];
+        vq += ((volatile double *)partials)[gridDim.x + b];
+    }
+    vp = block_sum(vp);
+    vq = block_sum(vq);
+    if (threadIdx.x == 0) {
+        const uint32_t slot = idx ? *idx : 0u;
+        dst[slot] = vp * (1.0 / (double)g.vs);
+        plaq_dst[slot] = vq * plaq_scale;
+        *ticket = 0u;
+    }
 }
 
 su2_status launch_plaquette(su2_lattice *lat, double *dst)
@@ -114,30 +154,6 @@ su2_status launch_plaquette(su2_lattice *lat, double *dst)
     return SU2_OK;
 }
 
-// Sum of the fused-plaquette slot region (one block of kFusedThreads; each
-// thread issues its loads together, then adds them in index order).
-constexpr int kFusedThreads = 1024;
-constexpr int kFusedPer = (kFusedRegion + kFusedThreads - 1) / kFusedThreads;
-
-__global__ void __launch_bounds__(kFusedThreads) fused_plaquette_kernel(const double *__restrict__ part, int n,
-                                                                       double scale, double *__restrict__ dst,
-                                                                       const uint32_t *__restrict__ idx)
-{
-    double v = 0.0;
-    for (int i0 = 0; i0 < n; i0 += kFusedPer * kFusedThreads) {
-        double x[kFusedPer];
-#pragma unroll
-        for (int j = 0; j < kFusedPer; ++j) {
-            const int i = i0 + j * kFusedThreads + (int)threadIdx.x;
-            x[j] = i < n ? part[i] : 0.0;
-        }
-#pragma unroll
-        for (int j = 0; j < kFusedPer; ++j) v += x[j];
-    }
-    v = block_sum(v);
-    if (threadIdx.x == 0) *(idx ? dst + *idx : dst) = v * scale;
-}
-
 su2_status fused_begin(su2_lattice *lat)
 {
     if (lat->scratch.partials_cap < kFusedRegion) {
@@ -149,23 +165,30 @@ su2_status fused_begin(su2_lattice *lat)
     return SU2_OK;
 }
 
-su2_status fused_finish(su2_lattice *lat, double *dst)
-{
-    lat->fused_part = nullptr;
-    fused_plaquette_kernel<<<1, kFusedThreads, 0, lat->stream>>>(lat->scratch.partials, kFusedRegion,
-                                                                 1.0 / (6.0 * (double)lat->vol), dst,
-                                                                 lat->capturing ? lat->d_ctr + 1 : nullptr);
-    SU2_CUDA(cudaGetLastError());
-    return SU2_OK;
-}
-
 su2_status launch_polyakov(su2_lattice *lat, double *dst)
 {
     const Geom g = geom_of(lat);
     const int grid = grid_for(g.vs, 32, std::min(lat->scratch.partials_cap, 152 * 8));
-    polyakov_kernel<<<grid, kPolyThreads, 0, lat->stream>>>(lat->links, g, lat->scratch.partials,
-                                                              lat->scratch.ticket + 1, dst,
-                                                              lat->capturing ? lat->d_ctr + 1 : nullptr);
+    polyakov_kernel<false><<<grid, kPolyThreads, 0, lat->stream>>>(lat->links, g, lat->scratch.partials,
+                                                                     lat->scratch.ticket + 1, dst,
+                                                                     lat->capturing ? lat->d_ctr + 1 : nullptr,
+                                                                     nullptr, nullptr, 0.0);
+    SU2_CUDA(cudaGetLastError());
+    return SU2_OK;
+}
+
+su2_status fused_finish_with_polyakov(su2_lattice *lat, double *plaq_dst, double *poly_dst)
+{
+    const Geom g = geom_of(lat);
+    const int grid = grid_for(g.vs, 32, 152 * 8);
+    if (lat->scratch.partials_cap < kFusedRegion + 2 * grid) {
+        set_last_error("reduction scratch too small for the fused plaquette");
+        return SU2_E_INVAL;
+    }
+    lat->fused_part = nullptr;
+    polyakov_kernel<true><<<grid, kPolyThreads, 0, lat->stream>>>(
+        lat->links, g, lat->scratch.partials + kFusedRegion, lat->scratch.ticket + 1, poly_dst,
+        lat->capturing ? lat->d_ctr + 1 : nullptr, lat->scratch.partials, plaq_dst, 1.0 / (6.0 * (double)lat->vol));
     SU2_CUDA(cudaGetLastError());
     return SU2_OK;
 }

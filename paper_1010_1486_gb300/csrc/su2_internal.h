@@ -186,10 +186,12 @@ inline double *fused_slot(const su2_lattice *lat, int mu, int parity, int kind)
     return lat->fused_part + ((mu - 1) * 2 + kind) * kFusedSlots;
 }
 // Zero-fills the slot region and points the lattice at it (the next sweep
-// measures), or detaches it; fused_finish sums the region in index order into
-// *dst (device) scaled to the mean plaquette.
+// measures); fused_finish_with_polyakov detaches it and, in one launch, sums
+// the region (block shares in index order, then the shares in block order)
+// into *plaq_dst (device) scaled to the mean plaquette, and writes the
+// Polyakov loop to *poly_dst.
 su2_status fused_begin(su2_lattice *lat);
-su2_status fused_finish(su2_lattice *lat, double *dst);
+su2_status fused_finish_with_polyakov(su2_lattice *lat, double *plaq_dst, double *poly_dst);
 
 // Launchers (each enqueues on lat->stream and returns a status of the launch).
 su2_status launch_cold_start(su2_lattice *lat);
