@@ -33,7 +33,8 @@ def test_every_declared_symbol_is_exported(su2):
     assert ctypes.sizeof(su2.su2_stats) == 128
 
 
-@pytest.mark.parametrize("ns,nt", [(3, 4), (4, 3), (0, 4), (4, 0), (1, 2), (-2, 4), (2000, 2000), (150, 160)])
+@pytest.mark.parametrize("ns,nt", [(3, 4), (4, 3), (0, 4), (4, 0), (1, 2), (-2, 4), (2000, 2000), (150, 160),
+                                   (64, 2048)])  # 4V = 2^31 exactly: one past the largest lattice
 def test_create_rejects_bad_extents(su2, ns, nt):
     with pytest.raises(su2.SU2Error) as e:
         su2.su2_create(ns, nt, 2.3, 1)
