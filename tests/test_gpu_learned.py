@@ -155,3 +155,31 @@ def test_learned_sweep_with_the_cpu_trained_network_matches_the_oracle():
     half = ns ** 3 * nt // 2
     assert abs(int(acc.sum()) - int(net.sum())) <= 0.005 * 16 * half, (acc, net)
     assert acc.sum() > 0.85 * 16 * half
+
+
+def test_learned_sweep_full_size_48():
+    """One learned sweep of the benchmark's 48^4, beta = 6 lattice from its
+    hot start, in the benchmark's launch configuration, with the network the
+    oracle trained (tests/golden/learned_weights.txt): bitwise the oracle's
+    table chain over all 21 million links, with equal acceptance counts."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "learned_weights.txt")
+    with open(path) as f:
+        w = np.array([float(x) for x in f if not x.startswith("#")], dtype=np.float32)
+    mean, scale = float(w[1945]), float(w[1946])
+    lo, hi = float(np.float32((1.0 - mean) * scale)), float(np.float32((40.0 - mean) * scale))
+    ns = nt = 48
+    beta, seed = 6.0, 3
+    h = su2.su2_create(ns, nt, beta, seed, su2.SU2_HOT)
+    try:
+        su2.su2_set_proposal(h, w, lo, hi, 256)
+        st = su2.su2_learned_sweep(h, 1)
+        got = su2.su2_get_links(h, ns, nt)
+    finally:
+        su2.su2_destroy(h)
+    assert st["learned_sweeps"] == 1 and st["plain_sweeps"] == 0
+    links = oracle.hot_start(ns, nt, seed)
+    table = oracle.proposal_table(w, lo, hi, 256)
+    acc = oracle.learned_sweep(ns, nt, beta, seed, 0, links, table, lo, hi, mean, scale)
+    assert np.array_equal(got, links)
+    assert [int(a) for a in st["accepted"]] == [int(a) for a in acc]
+    assert acc.sum() > 0.85 * 4 * ns ** 3 * nt
