@@ -295,6 +295,39 @@ def test_full_size_48_hot_start_one_sweep(lattice):
     assert obs_close(su2.su2_polyakov(lat.h), oracle.polyakov(ns, nt, ref))
 
 
+def test_benchmark_path_full_size_48():
+    """The benchmark's own path: the PyTorch allocator, a lattice on a user
+    stream, the Kennedy-Pendleton sampler, su2_generate measuring every sweep
+    (warm-up sweeps capture the sweep's CUDA graph, the next ones replay it).
+    After 3 + 2 sweeps from the hot start the whole 48^4 lattice is bitwise
+    the oracle's, and each sweep's plaquette (fused into the sweep) and
+    Polyakov loop agree with the oracle's within 1e-6."""
+    torch = pytest.importorskip("torch")
+    ns = nt = 48
+    beta, seed = 6.0, 3
+    su2.use_torch_allocator()
+    try:
+        stream = torch.cuda.Stream()
+        h = su2.su2_create(ns, nt, beta, seed, su2.SU2_HOT, stream=stream)
+        try:
+            su2.su2_set_sampler(h, su2.SU2_SAMPLER_KP)
+            p_w, l_w, _ = su2.su2_generate(h, 3, 1, 0)
+            p_t, l_t, st = su2.su2_generate(h, 2, 1, 0)
+            got = su2.su2_get_links(h, ns, nt)
+        finally:
+            su2.su2_destroy(h)
+    finally:
+        su2.use_default_allocator()
+    plaq, poly = list(p_w) + list(p_t), list(l_w) + list(l_t)
+    ref = oracle.hot_start(ns, nt, seed)
+    for s in range(5):
+        oracle.heatbath_sweep_kp(ns, nt, beta, seed, s, ref, nthreads=nthreads())
+        assert obs_close(plaq[s], oracle.plaquette(ns, nt, ref)), s
+        assert obs_close(poly[s], oracle.polyakov(ns, nt, ref)), s
+    assert np.array_equal(got, ref)
+    assert st["link_updates"] == 2 * 4 * ns ** 3 * nt
+
+
 # ------------------------------------------------ Kennedy-Pendleton sampler
 @pytest.mark.parametrize("ns,nt,beta,start", [(8, 8, 2.3, su2.SU2_HOT), (6, 4, 6.0, su2.SU2_HOT),
                                               (4, 6, 0.4, su2.SU2_COLD), (12, 4, 2.5, su2.SU2_COLD)])
