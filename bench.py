@@ -632,7 +632,8 @@ def run_batched(args, dist, su2, torch):
             "sites": sites, "value": value, "unit": UNIT, "sweeps_per_s": args.batched_steps / (ms * 1e-3),
             "ms_per_sweep": ms / args.batched_steps,
             "autotuned": {"queue_depth": tuned[0], "threads_per_block": tuned[1], "grid_blocks": tuned[2],
-                          "search": "queue depth 1/2/4/8 x 64/128/256 threads x full or half grid, 5 sweeps each"},
+                          "search": "queue depth 1/2/4/8 x 64/128/256 threads x all co-resident blocks or 1/2, "
+                                    "1/4, 1/8, 1/16 of them, 5 sweeps each"},
             "fixed_config": {"queue_depth": fixed[0], "threads_per_block": fixed[1], "grid_blocks": fixed[2],
                              "ms_per_sweep": fixed_ms},
             "autotuned_speedup_vs_fixed": fixed_ms / (ms / args.batched_steps),
@@ -652,8 +653,9 @@ def run_small(args, dist, su2, torch):
       24^4, beta = 2.5, cold start (seed 2): 200 thermalisation sweeps, then
         1000 measured sweeps with reunitarization every 10;
       32^3 x 4, beta = 2.20 .. 2.60 in steps of 0.05, cold starts (seeds
-        100 + i): one batch of nine lattices, 500 thermalisation + 2000
-        measured sweeps, plaquette and |L| per beta (Sec. 4.2)."""
+        100 + i): one batch of nine lattices, launch shape autotuned after the
+        500 thermalisation sweeps, then 2000 measured sweeps, plaquette and
+        |L| per beta (Sec. 4.2)."""
     import numpy as np
 
     from paper_1010_1486_gb300 import workloads
@@ -692,6 +694,8 @@ def run_small(args, dist, su2, torch):
     try:
         su2.su2_batch_set_sampler(b, sampler)
         su2.su2_batch_generate(b, nb, 500, 0)
+        su2.su2_batch_autotune(b, 5)  # restores the links and the sweep counter
+        scan_launch = su2.su2_batch_launch_info(b)
         ms, (plaq, poly, _) = timed(bst, torch, dist, lambda: su2.su2_batch_generate(b, nb, 2000, 1))
     finally:
         su2.su2_batch_destroy(b)
@@ -700,6 +704,8 @@ def run_small(args, dist, su2, torch):
                     "sweeps, plaquette and Polyakov loop of every lattice every sweep",
         "sweeps_per_s": 2000 / (ms * 1e-3), "us_per_sweep_of_the_scan": ms * 1e3 / 2000,
         "link_updates_per_s": 2000 * nb * 4 * 32 ** 3 * 4 / (ms * 1e-3),
+        "autotuned": {"queue_depth": scan_launch[0], "threads_per_block": scan_launch[1],
+                      "grid_blocks": scan_launch[2]},
         "beta": list(c4["betas"]), "plaquette_mean": [float(x) for x in plaq.mean(axis=0)],
         "abs_polyakov_mean": [float(x) for x in np.abs(poly).mean(axis=0)]}
     return out

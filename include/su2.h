@@ -402,9 +402,10 @@ su2_status su2_batch_get_links(su2_batch *b, int i, float *host);
  * threads per SM for every size) and grid (<= 0 or too large = all
  * co-resident blocks).  The default is depth 4, 128 threads, all co-resident
  * blocks.  su2_batch_set_config keeps the block size.  su2_batch_autotune
- * times all 24 combinations of depth, block size and full or half grid over
- * `sweeps` sweeps each, restores the links and sweep counter, and keeps the
- * fastest (reported by su2_batch_launch_info). */
+ * times all 60 combinations of depth, block size and grid (all co-resident
+ * blocks, or 1/2, 1/4, 1/8, 1/16 of them) over `sweeps` sweeps each,
+ * restores the links and sweep counter, and keeps the fastest (reported by
+ * su2_batch_launch_info). */
 su2_status su2_batch_set_launch(su2_batch *b, int queue_depth, int threads, int grid);
 /* a0 sampler of every lattice of the batch: SU2_SAMPLER_CREUTZ (default) or
  * SU2_SAMPLER_KP, as su2_set_sampler for one lattice (each lattice's chain is

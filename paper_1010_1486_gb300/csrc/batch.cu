@@ -577,9 +577,13 @@ su2_status su2_batch_set_sampler(su2_batch *b, int sampler)
     return su2_batch_set_launch(b, b->R, b->threads, b->grid);
 }
 
-// Times each candidate (queue depth 1/2/4/8 x block size 64/128/256 x full or
-// half of the co-resident grid) over `sweeps` sweeps of the batch, then
-// restores the links and the sweep counter, and keeps the fastest.
+// Times each candidate (queue depth 1/2/4/8 x block size 64/128/256 x the
+// co-resident grid or 1/2, 1/4, 1/8, 1/16 of it: small batches run faster on
+// fewer blocks, whose grid barriers cost less) over `sweeps` sweeps of the
+// batch, then restores the links and the sweep counter, and keeps the fastest.
+constexpr int kGridFractions = 5;
+constexpr int kAutotuneCandidates = 4 * 3 * kGridFractions;
+
 su2_status su2_batch_autotune(su2_batch *b, int sweeps, int *queue_depth, int *grid)
 {
     if (!b || sweeps < 1) return SU2_E_INVAL;
@@ -596,11 +600,11 @@ su2_status su2_batch_autotune(su2_batch *b, int sweeps, int *queue_depth, int *g
         cudaMemcpyAsync(saved, b->links, bytes, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess)
         st = cuda_fail(cudaGetLastError(), "su2_batch_autotune");
     const int depths[4] = {1, 2, 4, 8};
-    for (int c = 0; c < 24 && st == SU2_OK; ++c) {
-            const int i = c / 6, j = (c / 2) % 3, half = c % 2;
+    for (int c = 0; c < kAutotuneCandidates && st == SU2_OK; ++c) {
+            const int i = c / (3 * kGridFractions), j = (c / kGridFractions) % 3, f = c % kGridFractions;
             const int R = depths[i], T = kBatchBlockSizes[j];
             const int most = b->max_grid[b->sampler][i][j];
-            const int grid = half ? std::max(1, most / 2) : most;
+            const int grid = std::max(1, most >> f);  // the co-resident grid, 1/2, 1/4, 1/8 or 1/16 of it
             if ((st = set_depth(b, R, T, grid)) != SU2_OK) break;
             if ((st = launch_sweep(b, 0)) != SU2_OK) break;  // warm-up (and graph capture)
             cudaEventRecord(e0, b->stream);
