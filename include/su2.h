@@ -176,8 +176,9 @@ su2_status su2_reunitarize(su2_lattice *lat);
 su2_status su2_plaquette(su2_lattice *lat, double *out);
 
 /* Polyakov loop (Sec. 4): (1/Ns^3) sum over spatial sites of
- * (1/2) Tr prod_{t=0}^{Nt-1} U_3(x, t), signed; binary32 products, binary64
- * sum.  Synchronous. */
+ * (1/2) Tr prod_{t=0}^{Nt-1} U_3(x, t), signed; binary32 products (each
+ * quarter of the time extent multiplied left to right, the quarters combined
+ * in order as (P0 P1)(P2 P3)), binary64 sum.  Synchronous. */
 su2_status su2_polyakov(su2_lattice *lat, double *out);
 
 /* Space-time Wilson loops (not in the paper; the observables after the
