@@ -196,6 +196,10 @@ su2_status collect_stats(su2_lattice *lat, su2_stats *stats, uint64_t sweeps)
         set_last_error("heat-bath sampler hit its trial cap");
         return SU2_E_SAMPLER;
     }
+    if (flags[2] != 0) {
+        set_last_error("a learned phase gave up waiting for its proposal-table copy");
+        return SU2_E_DEVICE_TIMEOUT;
+    }
     return SU2_OK;
 }
 

@@ -15,6 +15,7 @@
 #include "staple.cuh"
 #include "su2_device.cuh"
 #include "su2_internal.h"
+#include "tc05.cuh"
 
 namespace su2 {
 
@@ -28,6 +29,23 @@ constexpr int kLearnThreads = 768;
 #endif
 constexpr int kLearnMinBlocks = SU2_LEARN_MIN_BLOCKS;  // blocks per SM the register budget is set for
 constexpr int kAcceptSlots = 64;
+constexpr uint32_t kTableWaitPolls = 1u << 24;  // polls of the table copy's mbarrier before a block gives up
+
+// Row pairs (r_j, r_{j+1} - r_j) of the table, the form the phase kernel
+// interpolates from (one 8-byte load and one fused multiply-add per
+// parameter); the tail up to a multiple of 16 bytes is zero.
+__global__ void proposal_pairs_kernel(const float *__restrict__ table, int n_pairs, int n_padded,
+                                      float2 *__restrict__ pairs)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_padded) return;
+    if (i < n_pairs) {
+        const float r0 = table[i];
+        pairs[i] = make_float2(r0, __fsub_rn(table[i + learned::kParams], r0));
+    } else {
+        pairs[i] = make_float2(0.0f, 0.0f);
+    }
+}
 
 __global__ void proposal_table_kernel(const float *__restrict__ w, float s_lo, float s_hi, int G,
                                       float *__restrict__ table)
@@ -42,6 +60,9 @@ __global__ void proposal_table_kernel(const float *__restrict__ w, float s_lo, f
 
 struct LearnedParams {
     float4 *links;
+    const float2 *pairs;               // the proposal table's row pairs (global, 16-byte aligned)
+    unsigned int pair_bytes;           // their size, a multiple of 16 bytes
+    unsigned int *flags;               // [2]: a block gave up waiting for the table copy
     Geom g;
     RoundKeys rk;
     int parity;
@@ -86,14 +107,23 @@ __device__ __forceinline__ unsigned int block_sum_u32(unsigned int v)
 template <int MU, bool MEAS>
 __global__ void __launch_bounds__(kLearnThreads, kLearnMinBlocks) learned_phase_kernel(const LearnedParams p)
 {
-    extern __shared__ float2 s_pairs[];
+    extern __shared__ __align__(16) float2 s_pairs[];
+    __shared__ __align__(8) uint64_t s_bar;
     if (*(volatile const unsigned int *)p.gate != 1u) return;
-    const int n_pairs = (p.G - 1) * learned::kParams;
-    for (int i = threadIdx.x; i < n_pairs; i += blockDim.x) {
-        const float r0 = p.table[i];
-        s_pairs[i] = make_float2(r0, __fsub_rn(p.table[i + learned::kParams], r0));
+    // The table's row pairs come in by one bulk copy (the TMA engine) that
+    // completes on an mbarrier, while the threads load their first staple.
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&s_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_addr(&s_bar)),
+                     "r"(p.pair_bytes)
+                     : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         tc::smem_addr(s_pairs)),
+                     "l"(p.pairs), "r"(p.pair_bytes), "r"(tc::smem_addr(&s_bar))
+                     : "memory");
     }
-    __syncthreads();
+    __syncthreads();  // the barrier is initialised before anyone waits on it
     const learned::Proposal pr{s_pairs, p.G, p.s_lo, learned::table_inv_ds(p.G, p.s_lo, p.s_hi), p.mean, p.scale};
     const int stride = gridDim.x * blockDim.x;
     const uint32_t sw = stream_word(kLearned, (uint32_t)p.parity, MU);
@@ -117,6 +147,22 @@ __global__ void __launch_bounds__(kLearnThreads, kLearnMinBlocks) learned_phase_
         v_cur = add_nu_terms(v_cur, load_nu_bases<MU, OtherDir<MU, 2>::value>(p.same, p.other, p.g, x, e, e_p));
         if (MU == 3) sp_cur = v_cur;
     }
+    // Thread 0 waits for the table (bounded); a block whose wait gives up
+    // flags it, waits once more (bounded) for its copy still in flight, and
+    // leaves its links unchanged.  The others then observe the completed
+    // phase themselves, which makes the copied bytes visible to them.
+    __shared__ int s_table_ok;
+    if (threadIdx.x == 0) {
+        const bool ok = tc::mbar_wait(&s_bar, 0, kTableWaitPolls);
+        if (!ok) {
+            atomicAdd(&p.flags[2], 1u);
+            tc::mbar_wait(&s_bar, 0, kTableWaitPolls);
+        }
+        s_table_ok = ok ? 1 : 0;
+    }
+    __syncthreads();
+    if (!s_table_ok) return;  // block-uniform
+    tc::mbar_wait(&s_bar, 0, kTableWaitPolls);
     while (base < p.g.vh) {  // warp-uniform
         const bool valid = cur <= last;
         const int nxt = cur + stride;
@@ -231,6 +277,10 @@ static cudaError_t launch_persistent(Kernel kernel, const LearnedParams &p, int 
     return cudaGetLastError();
 }
 
+// Bytes of the row pairs of a G-row table, rounded up to 16 (a bulk copy
+// moves a multiple of 16 bytes).
+static size_t pair_bytes_of(int G) { return (sizeof(float2) * (size_t)(G - 1) * learned::kParams + 15) & ~(size_t)15; }
+
 static su2_status launch_learned_phase(su2_lattice *lat, int mu, int parity)
 {
     LearnedParams p;
@@ -241,6 +291,8 @@ static su2_status launch_learned_phase(su2_lattice *lat, int mu, int parity)
     p.beta = (float)lat->beta;
     p.sweep = lat->sweep;
     p.table = lat->proposal;
+    p.pairs = lat->proposal_pairs;
+    p.flags = lat->scratch.flags;
     p.G = lat->proposal_g;
     p.s_lo = lat->prop_s_lo;
     p.s_hi = lat->prop_s_hi;
@@ -251,7 +303,8 @@ static su2_status launch_learned_phase(su2_lattice *lat, int mu, int parity)
     p.sweep_slots = lat->accept_slots + 8 * kAcceptSlots;
     p.plaq = fused_slot(lat, mu, parity, 1);
     set_bases(p.same, p.other, lat, parity);
-    const size_t smem = sizeof(float2) * (size_t)(p.G - 1) * learned::kParams;
+    p.pair_bytes = (unsigned int)pair_bytes_of(p.G);
+    const size_t smem = p.pair_bytes;
     const int want = (p.g.vh + kLearnThreads - 1) / kLearnThreads;
     cudaError_t e;
     if (p.plaq) {
@@ -297,8 +350,9 @@ su2_status su2_set_proposal(su2_lattice *lat, const float *weights, int n, doubl
     const size_t w_bytes = align256(sizeof(float) * learned::kWeights);
     const size_t ctl_bytes = align256(sizeof(unsigned int) * 4);
     const size_t slot_bytes = align256(sizeof(unsigned long long) * 9 * kAcceptSlots);
+    const size_t pairs_bytes = align256(pair_bytes_of(400));
     if (!lat->learned_block) {
-        lat->learned_bytes = table_bytes + w_bytes + ctl_bytes + slot_bytes;
+        lat->learned_bytes = table_bytes + w_bytes + ctl_bytes + slot_bytes + pairs_bytes;
         lat->learned_block = device_alloc(lat->learned_bytes, lat->device, lat->stream);
         if (!lat->learned_block) {
             set_last_error("device allocation of the learned proposal failed");
@@ -308,12 +362,18 @@ su2_status su2_set_proposal(su2_lattice *lat, const float *weights, int n, doubl
         lat->proposal = (float *)q;
         lat->learned_ctl = (unsigned int *)(q + table_bytes + w_bytes);
         lat->accept_slots = (unsigned long long *)(q + table_bytes + w_bytes + ctl_bytes);
+        lat->proposal_pairs = (float2 *)(q + table_bytes + w_bytes + ctl_bytes + slot_bytes);
         SU2_CUDA(cudaMemsetAsync(lat->learned_ctl, 0, ctl_bytes + slot_bytes, lat->stream));
     }
     float *d_w = (float *)((char *)lat->learned_block + table_bytes);
     SU2_CUDA(cudaMemcpyAsync(d_w, weights, sizeof(float) * learned::kWeights, cudaMemcpyHostToDevice, lat->stream));
     proposal_table_kernel<<<(grid_points + 63) / 64, 64, 0, lat->stream>>>(d_w, (float)s_lo, (float)s_hi, grid_points,
                                                                          lat->proposal);
+    SU2_CUDA(cudaGetLastError());
+    const int n_pairs = (grid_points - 1) * learned::kParams;
+    const int n_padded = (int)(pair_bytes_of(grid_points) / sizeof(float2));
+    proposal_pairs_kernel<<<(n_padded + 255) / 256, 256, 0, lat->stream>>>(lat->proposal, n_pairs, n_padded,
+                                                                          lat->proposal_pairs);
     SU2_CUDA(cudaGetLastError());
     SU2_CUDA(cudaStreamSynchronize(lat->stream));
     lat->proposal_g = grid_points;

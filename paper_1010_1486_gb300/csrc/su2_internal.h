@@ -87,6 +87,7 @@ struct su2_lattice {
     void *learned_block = nullptr;
     size_t learned_bytes = 0;
     float *proposal = nullptr;                 // G x 27 spline parameters
+    float2 *proposal_pairs = nullptr;          // (G - 1) x 27 row pairs (r_j, r_{j+1} - r_j), padded to 16 bytes
     int proposal_g = 0;
     float prop_s_lo = 0, prop_s_hi = 1, prop_mean = 0, prop_scale = 1;
     unsigned int *learned_ctl = nullptr;       // [0] gate (1 = learned sweep), [1] plain sweeps, [2] learned sweeps
