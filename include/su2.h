@@ -423,6 +423,13 @@ su2_status su2_batch_info(su2_batch *b, int *n, uint32_t *sweep, int *queue_dept
  * timeout_ns (<= 5 s); *timed_out receives the number of blocks that did. */
 su2_status su2_selftest_barrier_timeout(int blocks, uint64_t timeout_ns, unsigned int *timed_out);
 
+/* Self-test of the bounded mbarrier wait that the learned phase uses for its
+ * proposal-table copy: in each of `blocks` blocks (1..1024) thread 0 sets up
+ * an mbarrier that expects one arrival which never comes, and waits `polls`
+ * polls (1..2^24); *timed_out receives the number of blocks whose wait gave
+ * up (all of them). */
+su2_status su2_selftest_mbar_timeout(int blocks, unsigned int polls, unsigned int *timed_out);
+
 /* ------------------------------------------------------------------------
  * Time slabs: one lattice decomposed over ranks (Sec. 4, multi-GPU part, and
  * Fig. 1).  A slab holds the time slices t0 .. t0 + nt_local - 1 of the

@@ -327,6 +327,17 @@ static su2_status launch_learned_phase(su2_lattice *lat, int mu, int parity)
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// An mbarrier that expects one arrival which never comes: the bounded wait
+// must give up (the table wait of learned_phase_kernel, made to run out).
+__global__ void mbar_timeout_kernel(uint32_t polls, unsigned int *timed_out)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    tc::mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!tc::mbar_wait(&bar, 0, polls)) atomicAdd(timed_out, 1u);
+}
+
 }  // namespace su2
 
 using namespace su2;
@@ -381,6 +392,25 @@ su2_status su2_set_proposal(su2_lattice *lat, const float *weights, int n, doubl
     lat->prop_s_hi = (float)s_hi;
     lat->prop_mean = weights[learned::kOffMean];
     lat->prop_scale = weights[learned::kOffScale];
+    return SU2_OK;
+}
+
+su2_status su2_selftest_mbar_timeout(int blocks, unsigned int polls, unsigned int *timed_out)
+{
+    if (blocks < 1 || blocks > 1024 || polls < 1 || polls > (1u << 24) || !timed_out) return SU2_E_INVAL;
+    int dev = 0;
+    SU2_CUDA(cudaGetDevice(&dev));
+    unsigned int *d = (unsigned int *)device_alloc(sizeof(unsigned int), dev, nullptr);
+    if (!d) return SU2_E_NOMEM;
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned int), nullptr);
+    if (e == cudaSuccess) {
+        mbar_timeout_kernel<<<blocks, 32>>>(polls, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(timed_out, d, sizeof(unsigned int), cudaMemcpyDeviceToHost);
+    device_free(d, sizeof(unsigned int), dev, nullptr);
+    cudaStreamSynchronize(nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "su2_selftest_mbar_timeout");
     return SU2_OK;
 }
 

@@ -123,6 +123,7 @@ _SIGS = {
     "su2_batch_info": [_P, ctypes.POINTER(_i32), ctypes.POINTER(_u32), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
                        ctypes.POINTER(_i32)],
     "su2_selftest_barrier_timeout": [_i32, _u64, ctypes.POINTER(_u32)],
+    "su2_selftest_mbar_timeout": [_i32, _u32, ctypes.POINTER(_u32)],
     "su2_selftest_mma": [_P, _P, _i32, _P],
     "su2_set_proposal": [_P, _P, _i32, _f64, _f64, _i32],
     "su2_get_proposal_table": [_P, _P],
@@ -649,6 +650,12 @@ def su2_batch_info(b: int) -> dict:
 def su2_selftest_barrier_timeout(blocks: int, timeout_ns: int) -> int:
     out = _u32()
     _check(_lib.su2_selftest_barrier_timeout(blocks, timeout_ns, ctypes.byref(out)), "su2_selftest_barrier_timeout")
+    return out.value
+
+
+def su2_selftest_mbar_timeout(blocks: int, polls: int) -> int:
+    out = _u32()
+    _check(_lib.su2_selftest_mbar_timeout(blocks, polls, ctypes.byref(out)), "su2_selftest_mbar_timeout")
     return out.value
 
 

@@ -60,6 +60,11 @@ def test_null_and_enum_arguments(su2):
     assert lib.su2_overrelax_phase(None, 0, 0) == 1
     assert lib.su2_set_overrelax(None, 1) == 1
     assert lib.su2_wilson_loops(None, 1, 1, None) == 1
+    out = ctypes.c_uint()
+    assert lib.su2_selftest_mbar_timeout(0, 100, ctypes.byref(out)) == 1
+    assert lib.su2_selftest_mbar_timeout(8, 0, ctypes.byref(out)) == 1
+    assert lib.su2_selftest_mbar_timeout(8, (1 << 24) + 1, ctypes.byref(out)) == 1
+    assert lib.su2_selftest_mbar_timeout(8, 100, None) == 1
     assert lib.su2_destroy(None) == 0
     # allocator hooks must come in pairs
     assert lib.su2_set_allocator(su2.ALLOC_FN(lambda *a: None), su2.FREE_FN(), None) == 1

@@ -1,5 +1,7 @@
 """Failure detection without a GPU fault: the sampler's trial cap (forced low
-with su2_set_trial_cap) and the link-health check (su2_check_links).  A link
+with su2_set_trial_cap), the link-health check (su2_check_links) and the
+bounded mbarrier wait of the learned phase's table copy (made to run out on
+a barrier that nothing completes).  A link
 whose draw reaches the cap keeps its old value and the status is
 SU2_E_SAMPLER; every other link equals the oracle's uncapped draw bit for bit
 (the draws are the same counters).  Non-finite links give SU2_E_NUMERIC."""
@@ -112,3 +114,15 @@ def test_check_links_counts_bad_links():
             su2.su2_check_links(h, -1.0)
     finally:
         su2.su2_destroy(h)
+
+
+def test_mbarrier_wait_gives_up_and_reports():
+    """Every block's wait on an mbarrier that nothing completes gives up
+    after its polls, and the context stays usable."""
+    assert su2.su2_selftest_mbar_timeout(8, 1000) == 8
+    assert su2.su2_selftest_mbar_timeout(152, 1 << 16) == 152
+    lat = su2.su2_create(4, 4, 2.3, 1, su2.SU2_COLD)
+    try:
+        assert su2.su2_plaquette(lat) == 1.0
+    finally:
+        su2.su2_destroy(lat)
