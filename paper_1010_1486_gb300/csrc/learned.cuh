@@ -134,7 +134,7 @@ __device__ __forceinline__ float spline_eval(const P &p, int k, float xi, float 
     const float num = __fmul_rn(h, __fmaf_rn(__fmul_rn(s, xi), xi, __fmul_rn(dk, t)));
     const float omx = __fsub_rn(1.0f, xi);
     const float m = __fmaf_rn(__fmul_rn(dk1, xi), xi, __fmaf_rn(__fmul_rn(2.0f, s), t, __fmul_rn(__fmul_rn(dk, omx), omx)));
-    const float r = __fdiv_rn(1.0f, den);
+    const float r = __frcp_rn(den);  // correctly rounded 1/den, the same number as 1.0f / den
     fprime = __fmul_rn(__fmul_rn(__fmul_rn(s, s), m), __fmul_rn(r, r));
     return __fadd_rn(yk, __fmul_rn(num, r));
 }
@@ -146,7 +146,7 @@ __device__ __forceinline__ float spline_forward(const P &p, float z, float &fpri
     constexpr int Y = kBins + 1;
     const int k = bin_of(p, 0, z);
     const float xk = p(k);
-    const float iw = __fdiv_rn(1.0f, __fsub_rn(p(k + 1), xk));
+    const float iw = __frcp_rn(__fsub_rn(p(k + 1), xk));  // correctly rounded 1/w
     const float s = __fmul_rn(__fsub_rn(p(Y + k + 1), p(Y + k)), iw);
     float xi = __fmul_rn(__fsub_rn(z, xk), iw);
     xi = xi < 0.0f ? 0.0f : (xi > 1.0f ? 1.0f : xi);
