@@ -328,6 +328,7 @@ def run_ours(args, dist):
         peak, peak_kind = measured_peaks()
         achieved = BYTES_PER_UPDATE * (VOL // 2) / phase_s / 1e9
         trials_per_update = sum(st["trials"]) / st["link_updates"]
+        traffic = ncu_traffic_per_launch(args.sampler)
 
         # end to end through the C ABI with host buffers
         e2e = None
@@ -357,7 +358,9 @@ def run_ours(args, dist):
                    "parallelism": "independent replicas" if dist.world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (340 MB of links vs 129 MB L2), no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": ncu_traffic_per_launch(args.sampler), "kernel": SAMPLERS[args.sampler]["kernel"],
+                     "traffic": traffic, "kernel": SAMPLERS[args.sampler]["kernel"],
+                     # ncu's DRAM bytes of one launch over the live launch duration
+                     "traffic_gbs": traffic / phase_s / 1e9 if traffic else None,
                      "peak_source": f"{peak_kind} hbm_gbs", "bytes_per_launch": BYTES_PER_UPDATE * (VOL // 2),
                      "avg_launch_us": phase_s * 1e6, "timing": PHASE_TIMING,
                      "event_bracketed_launch_us": phase_s_events * 1e6},
