@@ -756,7 +756,54 @@ def run_small(args, dist, su2, torch):
                       "grid_blocks": scan_launch[2]},
         "beta": list(c4["betas"]), "plaquette_mean": [float(x) for x in plaq.mean(axis=0)],
         "abs_polyakov_mean": [float(x) for x in np.abs(poly).mean(axis=0)]}
+    out["32^3x4_beta_scan_learned"] = run_scan_learned(args, dist, su2, torch, c4,
+                                                       out["32^3x4_beta_scan"]["plaquette_mean"])
     return out
+
+
+def run_scan_learned(args, dist, su2, torch, c4, plain_plaquette):
+    """The beta scan with the learned proposal and its plain fallback: the
+    nine 32^3 x 4 lattices (cold, seeds 100 + i) thermalised by 500
+    Kennedy-Pendleton sweeps each, one network trained on (beta k, a0) pairs
+    pooled over the scan (10^5 per lattice, 1500 + 1500 Adam steps), then
+    2000 measured sweeps per lattice with the proposal (fallback below 0.7
+    acceptance), the lattices one after another on one stream."""
+    import numpy as np
+
+    from paper_1010_1486_gb300 import learn
+
+    nb = len(c4["betas"])
+    ns, nt = c4["ns"], c4["nt"]
+    st_ = torch.cuda.Stream()
+    lats = [su2.su2_create(ns, nt, b, c4["seed0"] + i + dist.rank, c4["start"], stream=st_)
+            for i, b in enumerate(c4["betas"])]
+    try:
+        for h in lats:
+            su2.su2_set_sampler(h, su2.SU2_SAMPLER_KP)
+            su2.su2_generate(h, 500, 0, 0)
+        pairs = torch.cat([learn.collect(h, ns, nt, 100_000) for h in lats])
+        w, _, s_lo, s_hi = learn.train(pairs, steps=1500, batch=8192, lr=3e-3, seed=4, tail_steps=1500, tail_lr=3e-4)
+        del pairs
+        for h in lats:
+            su2.su2_set_proposal(h, w, s_lo, s_hi, 256)
+            su2.su2_learned_generate(h, 3, 1, 0.7)
+        res = []
+        ms, _ = timed(st_, torch, dist, lambda: [res.append(su2.su2_learned_generate(h, 2000, 1, 0.7)) for h in lats])
+    finally:
+        for h in lats:
+            su2.su2_destroy(h)
+    acc = [sum(r[2]["accepted"]) / max(1, r[2]["learned_sweeps"] * 4 * ns ** 3 * nt) for r in res]
+    return {"workload": "nine 32^3 x 4 lattices, beta 2.20 .. 2.60, cold, 500 Kennedy-Pendleton sweeps each, one "
+                        "network trained on pairs pooled over the scan, then 2000 learned sweeps (fallback below "
+                        "0.7 acceptance) per lattice, one after another, plaquette and Polyakov loop every sweep",
+            "sweeps_per_s": 2000 * nb / (ms * 1e-3), "us_per_sweep": ms * 1e3 / (2000 * nb),
+            "sweeps_of_the_scan_per_s": 2000 / (ms * 1e-3),
+            "acceptance": [float(a) for a in acc],
+            "learned_sweeps": [int(r[2]["learned_sweeps"]) for r in res],
+            "fallback_sweeps": [int(r[2]["plain_sweeps"]) for r in res],
+            "plaquette_mean": [float(np.mean(r[0])) for r in res],
+            "plaquette_minus_plain_batch": [float(np.mean(r[0])) - float(p) for r, p in zip(res, plain_plaquette)],
+            "abs_polyakov_mean": [float(np.mean(np.abs(r[1]))) for r in res]}
 
 
 def run_e2e(args, dist, lat, su2, torch):
