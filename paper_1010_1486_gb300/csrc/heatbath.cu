@@ -468,7 +468,21 @@ __global__ void advance_kernel(uint32_t *ctr, int measured)
     }
 }
 
-static uint64_t generation_signature(const su2_lattice *lat)
+su2_status enqueue_set_counters(su2_lattice *lat)
+{
+    set_counters_kernel<<<1, 1, 0, lat->stream>>>(lat->d_ctr, lat->sweep);
+    SU2_CUDA(cudaGetLastError());
+    return SU2_OK;
+}
+
+su2_status enqueue_advance(su2_lattice *lat, bool measured)
+{
+    advance_kernel<<<1, 32, 0, lat->stream>>>(lat->d_ctr, measured ? 1 : 0);
+    SU2_CUDA(cudaGetLastError());
+    return SU2_OK;
+}
+
+uint64_t generation_signature(const su2_lattice *lat)
 {
     uint64_t h = 1469598103934665603ull;  // FNV-1a over the settings a captured sweep depends on
     auto mix = [&](uint64_t v) {

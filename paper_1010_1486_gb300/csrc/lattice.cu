@@ -385,6 +385,8 @@ su2_status su2_destroy(su2_lattice *lat)
     DeviceGuard guard(lat->device);
     for (cudaEvent_t e : lat->hb_log.events) cudaEventDestroy(e);
     for (cudaEvent_t e : lat->or_log.events) cudaEventDestroy(e);
+    for (GenGraph &gg : lat->learned_graph)
+        if (gg.exec) cudaGraphExecDestroy(gg.exec);
     for (GenGraph &gg : lat->gen_graph)
         if (gg.exec) cudaGraphExecDestroy(gg.exec);
     device_free(lat->staging, lat->staging_bytes, lat->device, lat->stream);

@@ -63,6 +63,7 @@ struct LearnedParams {
     const float2 *pairs;               // the proposal table's row pairs (global, 16-byte aligned)
     unsigned int pair_bytes;           // their size, a multiple of 16 bytes
     unsigned int *flags;               // [2]: a block gave up waiting for the table copy
+    const uint32_t *sweep_dev;         // if non-NULL the sweep counter is read here (graph replays)
     Geom g;
     RoundKeys rk;
     int parity;
@@ -126,6 +127,7 @@ __global__ void __launch_bounds__(kLearnThreads, kLearnMinBlocks) learned_phase_
     __syncthreads();  // the barrier is initialised before anyone waits on it
     const learned::Proposal pr{s_pairs, p.G, p.s_lo, learned::table_inv_ds(p.G, p.s_lo, p.s_hi), p.mean, p.scale};
     const int stride = gridDim.x * blockDim.x;
+    const uint32_t sweep = p.sweep_dev ? *p.sweep_dev : p.sweep;
     const uint32_t sw = stream_word(kLearned, (uint32_t)p.parity, MU);
     const int last = p.g.vh - 1;
     // Lanes past the end work on a clamped index and drop their results, so
@@ -173,7 +175,7 @@ __global__ void __launch_bounds__(kLearnThreads, kLearnMinBlocks) learned_phase_
         NuLinks nl = load_nu_bases<MU, OtherDir<MU, 0>::value>(p.same, p.other, p.g, xn, en, en_p);
         const uint32_t li = link_index(p.g, MU, p.parity, min(cur, last));
         const float4 old = p.links[li];
-        const uint4 w = philox_rk(make_uint4((uint32_t)cur, p.sweep, sw, 0u), p.rk);
+        const uint4 w = philox_rk(make_uint4((uint32_t)cur, sweep, sw, 0u), p.rk);
         const learned::LearnedDraw r = learned::learned_propose(pr, p.beta, v_cur, uniform01(w.x));
         float4 v_next = add_nu_terms(make_float4(0.0f, 0.0f, 0.0f, 0.0f), nl);
         float4 sp_next = v_next;
@@ -290,6 +292,7 @@ static su2_status launch_learned_phase(su2_lattice *lat, int mu, int parity)
     p.parity = parity;
     p.beta = (float)lat->beta;
     p.sweep = lat->sweep;
+    p.sweep_dev = lat->capturing ? lat->d_ctr : nullptr;
     p.table = lat->proposal;
     p.pairs = lat->proposal_pairs;
     p.flags = lat->scratch.flags;
@@ -336,6 +339,96 @@ __global__ void mbar_timeout_kernel(uint32_t polls, unsigned int *timed_out)
     tc::mbar_init(&bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     if (!tc::mbar_wait(&bar, 0, polls)) atomicAdd(timed_out, 1u);
+}
+
+// One learned sweep: the eight learned phases, each followed by the plain
+// phase gated off while the sweep is learned (it runs when the previous
+// sweep's acceptance fell below min_acceptance), the fallback decision, and
+// the measurement if due (plaq_dst / poly_dst: the slots, or when capturing
+// the bases to which the kernels add the device slot index).
+static su2_status learned_sweep_body(su2_lattice *lat, bool measure, double min_acceptance, double *plaq_dst,
+                                     double *poly_dst)
+{
+    su2_status st;
+    if (measure && (st = fused_begin(lat)) != SU2_OK) return st;
+    for (int mu = 0; mu < 4; ++mu)
+        for (int parity = 0; parity < 2; ++parity) {
+            if ((st = timing_begin(lat, lat->hb_log)) == SU2_OK) st = launch_learned_phase(lat, mu, parity);
+            if (st == SU2_OK) st = timing_end(lat, lat->hb_log);
+            if (st == SU2_OK) st = launch_hb_phase(lat, mu, parity, lat->sweep, lat->learned_ctl);
+            if (st != SU2_OK) {
+                lat->fused_part = nullptr;
+                return st;
+            }
+        }
+    learned_decide_kernel<<<1, 32, 0, lat->stream>>>(lat->learned_ctl, lat->accept_slots + 8 * kAcceptSlots,
+                                                     4.0 * (double)lat->vol, min_acceptance);
+    SU2_CUDA(cudaGetLastError());
+    if (measure) return fused_finish_with_polyakov(lat, plaq_dst, poly_dst);
+    return SU2_OK;
+}
+
+// The captured learned sweep of this variant (captured on first use or after
+// a settings change); *exec = NULL if the stream refused the capture.
+static su2_status learned_graph(su2_lattice *lat, bool measure, double min_acceptance, cudaGraphExec_t *exec)
+{
+    GenGraph &gg = lat->learned_graph[measure ? 1 : 0];
+    uint64_t sig = generation_signature(lat);
+    auto mix = [&](uint64_t v) {
+        for (int i = 0; i < 8; ++i) {
+            sig ^= (v >> (8 * i)) & 0xffu;
+            sig *= 1099511628211ull;
+        }
+    };
+    uint32_t b[5];
+    memcpy(&b[0], &lat->prop_s_lo, 4);
+    memcpy(&b[1], &lat->prop_s_hi, 4);
+    memcpy(&b[2], &lat->prop_mean, 4);
+    memcpy(&b[3], &lat->prop_scale, 4);
+    b[4] = (uint32_t)lat->proposal_g;
+    for (uint32_t x : b) mix(x);
+    uint64_t ma;
+    memcpy(&ma, &min_acceptance, 8);
+    mix(ma);
+    sig |= 1ull;
+    if (gg.exec && gg.sig == sig) {
+        *exec = gg.exec;
+        return SU2_OK;
+    }
+    if (gg.exec) {
+        cudaGraphExecDestroy(gg.exec);
+        gg.exec = nullptr;
+    }
+    *exec = nullptr;
+    if (cudaStreamBeginCapture(lat->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        lat->graphs_off = true;
+        return SU2_OK;
+    }
+    lat->capturing = true;
+    su2_status st = learned_sweep_body(lat, measure, min_acceptance, lat->scratch.history,
+                                       lat->scratch.history + lat->scratch.history_cap);
+    if (st == SU2_OK) st = enqueue_advance(lat, measure);
+    lat->capturing = false;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(lat->stream, &graph);
+    if (st != SU2_OK || e != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        lat->graphs_off = true;
+        return st == SU2_E_CUDA ? SU2_OK : st;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&gg.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        gg.exec = nullptr;
+        cudaGetLastError();
+        lat->graphs_off = true;
+        return SU2_OK;
+    }
+    gg.sig = sig;
+    *exec = gg.exec;
+    return SU2_OK;
 }
 
 }  // namespace su2
@@ -452,33 +545,30 @@ su2_status su2_learned_generate(su2_lattice *lat, int nsweeps, int measure_every
     SU2_CUDA(cudaMemcpyAsync(lat->learned_ctl, ctl0, sizeof ctl0, cudaMemcpyHostToDevice, lat->stream));
     SU2_CUDA(cudaMemsetAsync(lat->accept_slots, 0, sizeof(unsigned long long) * 9 * kAcceptSlots, lat->stream));
     lat->hb_log.used = 0;
-    const double links = 4.0 * (double)lat->vol;
     int m = 0;
+    // Graph replays need a stream that can be captured and no per-launch events.
+    bool graphs = lat->stream != nullptr && !lat->timing && !lat->graphs_off && nsweeps >= 1;
+    if (graphs && (st = enqueue_set_counters(lat)) != SU2_OK) return st;
     for (int s = 1; s <= nsweeps; ++s) {
         // a measured sweep adds the plaquette through whichever kernel runs
         // each phase (learned, or the plain fallback)
         const bool measure = measure_every > 0 && s % measure_every == 0;
-        if (measure && (st = fused_begin(lat)) != SU2_OK) return st;
-        for (int mu = 0; mu < 4; ++mu)
-            for (int parity = 0; parity < 2; ++parity) {
-                if ((st = timing_begin(lat, lat->hb_log)) == SU2_OK) st = launch_learned_phase(lat, mu, parity);
-                if (st == SU2_OK) st = timing_end(lat, lat->hb_log);
-                if (st == SU2_OK) st = launch_hb_phase(lat, mu, parity, lat->sweep, lat->learned_ctl);
-                if (st != SU2_OK) {
-                    lat->fused_part = nullptr;
-                    return st;
-                }
+        if (graphs) {
+            cudaGraphExec_t exec = nullptr;
+            if ((st = learned_graph(lat, measure, min_acceptance, &exec)) != SU2_OK) return st;
+            if (exec) {
+                SU2_CUDA(cudaGraphLaunch(exec, lat->stream));
+                lat->sweep += 1;
+                if (measure) ++m;
+                continue;
             }
-        learned_decide_kernel<<<1, 32, 0, lat->stream>>>(lat->learned_ctl, lat->accept_slots + 8 * kAcceptSlots,
-                                                         links, min_acceptance);
-        SU2_CUDA(cudaGetLastError());
-        lat->sweep += 1;
-        if (measure) {
-            if ((st = fused_finish_with_polyakov(lat, lat->scratch.history + m,
-                                                 lat->scratch.history + lat->scratch.history_cap + m)) != SU2_OK)
-                return st;
-            ++m;
+            graphs = false;  // capture refused: run the rest eagerly
         }
+        if ((st = learned_sweep_body(lat, measure, min_acceptance, lat->scratch.history + m,
+                                     lat->scratch.history + lat->scratch.history_cap + m)) != SU2_OK)
+            return st;
+        lat->sweep += 1;
+        if (measure) ++m;
     }
     if (nmeas > 0 && plaq)
         SU2_CUDA(cudaMemcpyAsync(plaq, lat->scratch.history, sizeof(double) * nmeas, cudaMemcpyDeviceToHost,

@@ -78,6 +78,7 @@ struct su2_lattice {
     bool graphs_off = false;       // a capture failed once: generate eagerly
     uint32_t *d_ctr = nullptr;     // device: [0] sweep counter, [1] measurement slot (graph replays)
     su2::GenGraph gen_graph[4];    // captured sweeps, variant = (measured) | (reunitarized) << 1
+    su2::GenGraph learned_graph[2];  // captured learned sweeps, [measured]
 
     bool timing = false;
     su2::EventLog hb_log;  // heat-bath (and learned) phase launches
@@ -192,6 +193,12 @@ inline double *fused_slot(const su2_lattice *lat, int mu, int parity, int kind)
 // into *plaq_dst (device) scaled to the mean plaquette, and writes the
 // Polyakov loop to *poly_dst.
 su2_status fused_begin(su2_lattice *lat);
+// Graph replays of generation loops: the device sweep counter and measurement
+// slot set from the host state (one-thread kernel), advanced at the end of a
+// captured sweep; and the hash of the settings a captured sweep depends on.
+su2_status enqueue_set_counters(su2_lattice *lat);
+su2_status enqueue_advance(su2_lattice *lat, bool measured);
+uint64_t generation_signature(const su2_lattice *lat);
 su2_status fused_finish_with_polyakov(su2_lattice *lat, double *plaq_dst, double *poly_dst);
 
 // Launchers (each enqueues on lat->stream and returns a status of the launch).

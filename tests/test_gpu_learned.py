@@ -183,3 +183,34 @@ def test_learned_sweep_full_size_48():
     assert np.array_equal(got, links)
     assert [int(a) for a in st["accepted"]] == [int(a) for a in acc]
     assert acc.sum() > 0.85 * 4 * ns ** 3 * nt
+
+
+@pytest.mark.parametrize("min_acceptance", [0.7, 0.999])
+def test_graph_replayed_learned_sweeps_equal_eager_sweeps(min_acceptance):
+    """su2_learned_generate on a lattice with a stream replays each sweep
+    (learned phases, gated plain phases, fallback decision, measurement) from
+    a CUDA graph; the chain, the acceptance counts, the fallback alternation
+    (forced at min_acceptance 0.999) and the measurements equal the eager
+    path's bit for bit."""
+    torch = pytest.importorskip("torch")
+    ns, nt, beta, seed = 8, 8, 2.4, 23
+    w = weights(7, 0.2, mean=beta * 3.0, inv_sd=0.6)
+    out = []
+    for stream in (None, torch.cuda.Stream()):
+        h = su2.su2_create(ns, nt, beta, seed, su2.SU2_HOT, stream=stream)
+        try:
+            su2.su2_heatbath_sweep(h, 2)
+            su2.su2_set_proposal(h, w, -3.0, 3.0, 128)
+            plaq, poly, st = su2.su2_learned_generate(h, 6, 2, min_acceptance)
+            plaq2, poly2, st2 = su2.su2_learned_generate(h, 3, 1, min_acceptance)
+            out.append((su2.su2_get_links(h, ns, nt), plaq.copy(), poly.copy(), st, plaq2.copy(), st2))
+        finally:
+            su2.su2_destroy(h)
+    (l0, p0, q0, s0, r0, t0), (l1, p1, q1, s1, r1, t1) = out
+    assert np.array_equal(l0, l1)
+    assert np.array_equal(p0, p1) and np.array_equal(q0, q1) and np.array_equal(r0, r1)
+    for a, b in ((s0, s1), (t0, t1)):
+        assert a["accepted"] == b["accepted"]
+        assert a["learned_sweeps"] == b["learned_sweeps"] and a["plain_sweeps"] == b["plain_sweeps"]
+    if min_acceptance > 0.9:
+        assert s0["plain_sweeps"] > 0
